@@ -1,0 +1,171 @@
+"""Python handle on the oracle (pes_oracle.c): test infrastructure only.
+
+The oracle is the plain CPU restatement of what the library computes (Verschelde
+2021, Eq. (eqconvform) for the truncated series product and Eq. (eqpolynomial)
+for the polynomial and its gradient).  Only tests/, __graft_entry__.smoke() and
+bench.py's CPU-baseline and reference legs use it; the product path never does.
+
+Arrays follow the library's limb-major layout: a series array is float64 of
+shape (k, n_series, d+1); a single series is (k, d+1); a multiple double scalar
+is (k,).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pes_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: Dekker's TwoProduct and Knuth's TwoSum must not be fused
+# into multiply-adds by the compiler.
+CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fopenmp"]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to this file (gcc, a second or two)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            c_int = ctypes.c_int
+            for name, args in {
+                "orc_md_add": [c_int, dp, dp, dp],
+                "orc_md_mul": [c_int, dp, dp, dp],
+                "orc_round_sum": [c_int, c_int, dp, dp],
+                "orc_conv": [c_int, c_int, dp, dp, dp],
+                "orc_corr": [c_int, c_int, dp, dp, dp],
+                "orc_eval_grad": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, c_int],
+                "orc_vjp": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, dp, c_int],
+                "orc_threads": [c_int],
+            }.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def md_add(x, y):
+    x, y = _f64(x), _f64(y)
+    k = x.shape[0]
+    out = np.empty(k)
+    _check(_load().orc_md_add(k, _dp(x), _dp(y), _dp(out)), "md_add")
+    return out
+
+
+def md_mul(x, y):
+    x, y = _f64(x), _f64(y)
+    k = x.shape[0]
+    out = np.empty(k)
+    _check(_load().orc_md_mul(k, _dp(x), _dp(y), _dp(out)), "md_mul")
+    return out
+
+
+def round_sum(values, k):
+    """round_k of the exact sum of a list of doubles."""
+    v = _f64(values).ravel()
+    out = np.empty(k)
+    _check(_load().orc_round_sum(k, v.size, _dp(v), _dp(out)), "round_sum")
+    return out
+
+
+def conv(x, y):
+    """Truncated product of two series, (k, d+1) each."""
+    x, y = _f64(x), _f64(y)
+    k, s = x.shape
+    z = np.empty_like(x)
+    _check(_load().orc_conv(k, s - 1, _dp(x), _dp(y), _dp(z)), "conv")
+    return z
+
+
+def corr(u, s):
+    """Truncated correlation r_j = sum_{l>=j} u_l s_{l-j}, (k, d+1) each."""
+    u, s = _f64(u), _f64(s)
+    k, n = u.shape
+    r = np.empty_like(u)
+    _check(_load().orc_corr(k, n - 1, _dp(u), _dp(s), _dp(r)), "corr")
+    return r
+
+
+def _supports(supports):
+    ptr = np.zeros(len(supports) + 1, dtype=np.int32)
+    idx = []
+    for m, s in enumerate(supports):
+        idx.extend(int(v) for v in s)
+        ptr[m + 1] = len(idx)
+    return ptr, np.asarray(idx, dtype=np.int32)
+
+
+def eval_grad(supports, n, coeff, inputs, nthreads: int = 0, grad: bool = True):
+    """Value (k, d+1) and gradient (k, n, d+1) of the polynomial at the series.
+
+    supports: list of increasing 0-based variable index lists, one per monomial.
+    coeff: (k, N+1, d+1) with index 0 the constant term; inputs: (k, n, d+1).
+    """
+    coeff, inputs = _f64(coeff), _f64(inputs)
+    k, n1, s = coeff.shape
+    N = len(supports)
+    assert n1 == N + 1 and inputs.shape == (k, n, s)
+    ptr, idx = _supports(supports)
+    value = np.empty((k, s))
+    g = np.empty((k, n, s)) if grad else None
+    gp = _dp(g) if grad else ctypes.POINTER(ctypes.c_double)()
+    _check(_load().orc_eval_grad(k, s - 1, N, n, _ip(ptr), _ip(idx), _dp(coeff), _dp(inputs),
+                                 _dp(value), gp, nthreads), "eval_grad")
+    return (value, g) if grad else value
+
+
+def vjp(supports, n, coeff, inputs, upstream, nthreads: int = 0):
+    """(grad_input (k, n, d+1), grad_coeff (k, N+1, d+1)) of <upstream, value>."""
+    coeff, inputs, upstream = _f64(coeff), _f64(inputs), _f64(upstream)
+    k, n1, s = coeff.shape
+    N = len(supports)
+    ptr, idx = _supports(supports)
+    gi = np.empty((k, n, s))
+    gc = np.empty((k, N + 1, s))
+    _check(_load().orc_vjp(k, s - 1, N, n, _ip(ptr), _ip(idx), _dp(coeff), _dp(inputs),
+                           _dp(upstream), _dp(gi), _dp(gc), nthreads), "vjp")
+    return gi, gc
+
+
+def threads(nthreads: int = 0) -> int:
+    return int(_load().orc_threads(nthreads))

@@ -1,0 +1,147 @@
+"""Exact arithmetic helpers for the tests (independent of both the oracle and
+the CUDA path): k-limb values collapsed to exact integers or Fractions, the
+normwise error measure, and a Fraction evaluator of the polynomial, its gradient
+and its vector-Jacobian product for tiny cases.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+
+# normwise relative tolerance per number of limbs k
+TOL = {1: 1e-13, 2: 1e-29, 3: 1e-44, 4: 1e-60, 5: 1e-76, 8: 1e-123, 10: 1e-150}
+
+
+def to_fraction(limbs) -> Fraction:
+    return sum((Fraction(float(x)) for x in limbs), Fraction(0))
+
+
+def series_fractions(a):
+    """(k, ..., S) float array -> nested lists of Fractions over the trailing axes."""
+    a = np.asarray(a, dtype=np.float64)
+    k = a.shape[0]
+    flat = a.reshape(k, -1)
+    vals = [to_fraction(flat[:, i]) for i in range(flat.shape[1])]
+    return np.array(vals, dtype=object).reshape(a.shape[1:])
+
+
+def exact_ints(arrs):
+    """Collapse several (k, ...) float arrays to exact Python ints at one common
+    binary scale.  Returns (list of object arrays of ints, scale exponent)."""
+    mants, exps = [], []
+    for a in arrs:
+        a = np.asarray(a, dtype=np.float64)
+        m, e = np.frexp(a)
+        mi = np.ldexp(m, 53).astype(np.int64)
+        ex = e.astype(np.int64) - 53
+        mants.append(mi)
+        exps.append(ex)
+    emin = None
+    for mi, ex in zip(mants, exps):
+        nz = mi != 0
+        if nz.any():
+            v = int(ex[nz].min())
+            emin = v if emin is None else min(emin, v)
+    if emin is None:
+        emin = 0
+    outs = []
+    for mi, ex in zip(mants, exps):
+        k = mi.shape[0]
+        fm = mi.reshape(k, -1)
+        fe = ex.reshape(k, -1)
+        vals = np.empty(fm.shape[1], dtype=object)
+        for i in range(fm.shape[1]):
+            v = 0
+            for l in range(k):
+                mm = int(fm[l, i])
+                if mm:
+                    v += mm << (int(fe[l, i]) - emin)
+            vals[i] = v
+        outs.append(vals.reshape(mi.shape[1:]))
+    return outs, emin
+
+
+def normwise_err(s, r) -> float:
+    """max over series of max_j |s_j - r_j| / max_j |r_j|, exact.
+
+    s, r: (k, ..., S) arrays (limb-major), the last axis indexing coefficients.
+    A series whose reference is identically zero must be exactly zero (error
+    0.0), else the error is reported as inf.
+    """
+    (si, ri), _ = exact_ints([s, r])
+    si = si.reshape(-1, si.shape[-1]) if si.ndim > 1 else si.reshape(1, -1)
+    ri = ri.reshape(-1, ri.shape[-1]) if ri.ndim > 1 else ri.reshape(1, -1)
+    worst = 0.0
+    for a, b in zip(si, ri):
+        num = max(abs(int(x) - int(y)) for x, y in zip(a, b))
+        den = max(abs(int(y)) for y in b)
+        if den == 0:
+            err = 0.0 if num == 0 else float("inf")
+        else:
+            err = num / den
+        worst = max(worst, err)
+    return worst
+
+
+def normwise_err_fr(s, ref_fr) -> float:
+    """Like normwise_err but against exact Fractions ref_fr (shape (..., S))."""
+    sf = series_fractions(s)
+    sf = sf.reshape(-1, sf.shape[-1])
+    rf = np.asarray(ref_fr, dtype=object).reshape(-1, sf.shape[-1])
+    worst = 0.0
+    for a, b in zip(sf, rf):
+        num = max(abs(x - y) for x, y in zip(a, b))
+        den = max(abs(y) for y in b)
+        if den == 0:
+            err = 0.0 if num == 0 else float("inf")
+        else:
+            err = float(num / den)
+        worst = max(worst, err)
+    return worst
+
+
+# ---------------------------------------------------------------------------
+# Fraction evaluator (tiny cases only)
+# ---------------------------------------------------------------------------
+
+def conv_fr(x, y):
+    d = len(x) - 1
+    return [sum((x[i] * y[j - i] for i in range(j + 1)), Fraction(0)) for j in range(d + 1)]
+
+
+def corr_fr(u, s):
+    d = len(u) - 1
+    return [sum((u[l] * s[l - j] for l in range(j, d + 1)), Fraction(0)) for j in range(d + 1)]
+
+
+def eval_grad_fr(supports, n, coeff_fr, input_fr):
+    """coeff_fr: (N+1, S) Fractions, input_fr: (n, S) Fractions."""
+    S = len(coeff_fr[0])
+    value = list(coeff_fr[0])
+    grad = [[Fraction(0)] * S for _ in range(n)]
+    for m, supp in enumerate(supports):
+        t = list(coeff_fr[m + 1])
+        for v in supp:
+            t = conv_fr(t, input_fr[v])
+        value = [a + b for a, b in zip(value, t)]
+        for i in supp:
+            g = list(coeff_fr[m + 1])
+            for v in supp:
+                if v != i:
+                    g = conv_fr(g, input_fr[v])
+            grad[i] = [a + b for a, b in zip(grad[i], g)]
+    return value, grad
+
+
+def vjp_fr(supports, n, coeff_fr, input_fr, u_fr):
+    S = len(coeff_fr[0])
+    _, grad = eval_grad_fr(supports, n, coeff_fr, input_fr)
+    gin = [corr_fr(u_fr, grad[i]) for i in range(n)]
+    gco = [list(u_fr)]
+    for supp in supports:
+        mono = list(input_fr[supp[0]])
+        for v in supp[1:]:
+            mono = conv_fr(mono, input_fr[v])
+        gco.append(corr_fr(u_fr, mono))
+    return gin, gco
