@@ -1,0 +1,230 @@
+/*
+ * pes.h -- C-ABI of libpes: evaluation and differentiation of a polynomial at
+ * power series in multiple double precision, on one GB300 GPU (sm_103a).
+ *
+ * Method: J. Verschelde, "Accelerated Polynomial Evaluation and Differentiation
+ * at Power Series in Multiple Double Precision" (2021).
+ *   - A series is truncated at degree d: d+1 coefficients (Sec. 2).
+ *   - A coefficient is a multiple double: an unevaluated sum of k doubles,
+ *     k in {1, 2, 3, 4, 5, 8, 10} (Sec. 1, "Contributions").
+ *   - The polynomial is p = a_0 + sum_{m=1..N} a_m x_{i_1} ... x_{i_{n_m}}
+ *     (Eq. eqpolynomial) with coefficient series a_m and variable supports
+ *     i_1 < ... < i_{n_m}; it is evaluated, with all n partial derivatives, at
+ *     n input series z_1..z_n (problem statement of Sec. 5).
+ *   - The work is the reverse mode of Sec. 3 (forward, backward and cross
+ *     products of every monomial) as layered convolution jobs (Sec. 5), followed
+ *     by the addition of the monomial contributions.
+ *
+ * Layout of every series buffer: limb-major, float64, contiguous:
+ *   buffer[l][s][j] at ((l * n_series) + s) * (d + 1) + j,
+ * limb l in [0, k), series s, coefficient j in [0, d].  Limb 0 holds the leading
+ * double of every coefficient; outputs are normalised (nonoverlapping limbs,
+ * each limb at most half an ulp of the previous one).
+ *
+ * Ownership: the caller owns every data buffer (device memory of the current
+ * device).  A plan owns its job tables and its workspace in device memory.
+ * Calls taking a stream are asynchronous on that stream (a cudaStream_t, NULL
+ * for the legacy default stream); device-side failures (a bounded wait that
+ * gave up) are recorded in the plan and returned by pes_check.  Calls on one
+ * plan must not overlap in time (they share the plan's workspace).
+ *
+ * Every function returns PES_OK or an error code; nothing traps or aborts.
+ */
+#ifndef PES_H
+#define PES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PES_OK = 0,
+  PES_EINVAL = 1,            /* invalid argument (message in pes_last_error) */
+  PES_EUNSUPPORTED_K = 2,    /* k not in {1,2,3,4,5,8,10} */
+  PES_ENOMEM = 3,            /* device or host allocation failed */
+  PES_ECUDA = 4,             /* a CUDA runtime call failed */
+  PES_ETIMEOUT = 5,          /* a device-side wait gave up (see pes_check) */
+  PES_EINTERNAL = 6,         /* inconsistent internal state */
+  PES_EUNSUPPORTED_SIZE = 7  /* degree too large for the shared-memory staging */
+} pes_status;
+
+typedef struct pes_plan_s* pes_plan_t;
+typedef struct pes_batch_s* pes_batch_t;
+
+/* Arithmetic of the convolution multiply-accumulate loop.  Both give the same
+ * values: every output coefficient is the exact sum of its terms' digit
+ * products, rounded once to k limbs. */
+enum { PES_ARITH_FP64 = 0, PES_ARITH_INT = 1 };
+
+typedef struct {
+  int32_t arith;       /* PES_ARITH_FP64 (default) or PES_ARITH_INT */
+  int32_t threads;     /* threads per CTA of the convolution kernel: 128 or 256; 0 = default (128) */
+  int32_t ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit */
+  int32_t with_vjp;    /* 1: also build the tables of pes_vjp (default 1) */
+  int64_t timeout_ms;  /* bound on every device-side wait; 0 = default (60000) */
+} pes_options;
+
+/* Fill *opt with the defaults. */
+void pes_default_options(pes_options* opt);
+
+/* ---- plans ------------------------------------------------------------------ */
+
+/* Compile the job tables of one polynomial (Sec. 5, data staging) and allocate
+ * its workspace.
+ *   supp_ptr: N+1 row pointers into supp_idx (supp_ptr[0] == 0);
+ *   supp_idx: 0-based variable indices of monomials 1..N, strictly increasing
+ *             within a monomial (the paper's i_1 < ... < i_{n_k}, 1-based);
+ *   N >= 0 monomials (a_0 is implicit), n >= 1 variables, d >= 0, k as above.
+ * Errors: PES_EINVAL (bad sizes, empty monomial, index out of range, unsorted or
+ * repeated index), PES_EUNSUPPORTED_K, PES_EUNSUPPORTED_SIZE, PES_ENOMEM,
+ * PES_ECUDA.  The supports are copied; the caller keeps ownership. */
+pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
+                    int32_t k, pes_plan_t* out);
+pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
+                       int32_t k, const pes_options* opt, pes_plan_t* out);
+void pes_plan_destroy(pes_plan_t plan);
+
+/* Value and gradient of the polynomial at the input series (Sec. 4 and 5).
+ *   coeff: device, [k][N+1][d+1], index 0 is a_0;
+ *   input: device, [k][n][d+1];
+ *   value: device, [k][d+1]          (written);
+ *   grad:  device, [k][n][d+1]       (written; series i is d p / d x_i).
+ * Asynchronous on `stream`. */
+pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const double* input, double* value, double* grad,
+                         void* stream);
+
+/* Vector-Jacobian product of the value series with an upstream series u:
+ * for L = sum_j u_j v_j (v the value series),
+ *   grad_coeff[0]  = u,
+ *   grad_coeff[m]_j = sum_{l=j..d} u_l M_m[l-j],  M_m = prod_{i in S_m} z_i,
+ *   grad_input[i]_j = sum_{l=j..d} u_l g_i[l-j],  g_i = d p / d x_i,
+ * i.e. truncated correlations (transposed convolutions) of u with the monomial
+ * products and with the gradient series; exact because every variable has
+ * exponent 1, so v is affine in each input series and each coefficient series.
+ *   upstream:   device, [k][d+1];
+ *   grad_input: device, [k][n][d+1] (written);
+ *   grad_coeff: device, [k][N+1][d+1] (written).
+ * reuse_forward = 1: the plan's workspace still holds the forward, backward and
+ * cross products of the last pes_eval_grad call on this plan with the same
+ * coeff and input (no other call in between); only the correlations and the
+ * monomial products are computed.  reuse_forward = 0: everything is recomputed.
+ * Needs a plan built with with_vjp = 1.  Asynchronous on `stream`. */
+pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double* input, const double* upstream,
+                   double* grad_input, double* grad_coeff, int32_t reuse_forward, void* stream);
+
+/* Copy the plan's workspace (the forward, backward and cross products of the
+ * last call) to a caller buffer (to_buffer = 1) or back from it (to_buffer = 0),
+ * asynchronously on `stream`.  buffer: device, pes_plan_info.workspace_bytes
+ * bytes.  Lets a caller keep the products of one call alive under its own
+ * memory budget and reuse them later with pes_vjp(..., reuse_forward = 1). */
+pes_status pes_workspace_io(pes_plan_t plan, void* buffer, int32_t to_buffer, void* stream);
+
+/* Synchronise `stream`, then return (and clear) the device status of the plan:
+ * PES_OK, or PES_ETIMEOUT when a bounded wait gave up during a call. */
+pes_status pes_check(pes_plan_t plan, void* stream);
+
+typedef struct {
+  int64_t conv_jobs;       /* convolution jobs of pes_eval_grad (3n-3 per monomial of n >= 2 variables) */
+  int64_t layers;          /* number of layers (largest monomial size) */
+  int64_t add_terms;       /* series contributions summed by the addition stage */
+  int64_t add_jobs;        /* pairwise additions of the paper's tree: add_terms - outputs with >=1 term */
+  int64_t workspace_bytes; /* device workspace owned by the plan */
+  int64_t vjp_conv_jobs;   /* extra convolutions of pes_vjp (monomial products) */
+  int64_t vjp_corr_jobs;   /* correlations of pes_vjp (N + n) */
+  int32_t digits;          /* digits per coefficient of the exact dot product */
+  int32_t grid;            /* persistent CTAs of the convolution kernel */
+  int32_t threads;         /* threads per CTA */
+  int32_t smem_bytes;      /* dynamic shared memory per CTA */
+} pes_plan_info;
+
+pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);
+
+/* ---- batches: many polynomials in one persistent launch (CUDA graph) ---------- */
+
+/* count instances; instance b has n[b] variables, N[b] monomials and degree
+ * d[b]; its supports are rows supp_ptr[P_b .. P_b + N[b]] (each instance's row
+ * pointers start at 0) with P_b = sum_{c<b} (N[c] + 1), indexing supp_idx from
+ * Q_b = sum_{c<b} supp_ptr[P_c + N[c]].  All instances share k.
+ * The buffers of pes_eval_grad_batch concatenate the instances' buffers in
+ * order, each laid out as for pes_eval_grad; pes_batch_offsets gives where each
+ * instance starts. */
+pes_status pes_plan_batch(int32_t count, const int32_t* n, const int32_t* N, const int32_t* d,
+                          const int32_t* supp_ptr, const int32_t* supp_idx, int32_t k, const pes_options* opt,
+                          pes_batch_t* out);
+void pes_batch_destroy(pes_batch_t batch);
+
+/* Offsets (in doubles) of instance b in the concatenated buffers, arrays of
+ * count+1 entries (the last is the total length).  Any pointer may be NULL. */
+pes_status pes_batch_offsets(pes_batch_t batch, int64_t* coeff_off, int64_t* input_off, int64_t* value_off,
+                             int64_t* grad_off);
+
+/* All instances at once: one pack, one persistent convolution launch over the
+ * concatenated job tables, one addition launch, replayed as a CUDA graph. */
+pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff, const double* input, double* value,
+                               double* grad, void* stream);
+pes_status pes_batch_check(pes_batch_t batch, void* stream);
+pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info);
+
+/* ---- multiple double numbers --------------------------------------------------- */
+
+/* Elementwise out = x + y (op 0) or x * y (op 1) of `count` k-double numbers,
+ * limb-major [k][count], device buffers (Sec. 1 arithmetic: FMA TwoSum/TwoProd
+ * with renormalisation). */
+pes_status pes_md_binary(int32_t op, int32_t k, const double* x, const double* y, double* out, int64_t count,
+                         void* stream);
+
+/* Double-precision-equivalent cost of one k-double multiplication and addition
+ * (Sec. 6.2 gives 3089 and 397 for k = 10; other k use the FP64 operation
+ * counts of this library's md_mul and md_add). */
+pes_status pes_md_costs(int32_t k, double* mul_ops, double* add_ops);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops per
+ * FMA), best of `repeats` timed launches over all SMs. */
+pes_status pes_fp64_peak(int32_t repeats, double* tflops);
+
+/* ---- job compiler introspection (host only; no GPU needed) --------------------- */
+
+/* stats[0] conv jobs, [1] layers, [2] add terms, [3] paper add jobs,
+ * [4] slots of the data array, [5] add levels of the paper's tree, [6] vjp extra
+ * convolutions, [7] correlations.  layer_sizes[0..cap) receives the number of
+ * jobs per layer.  paper_layout = 1 counts the data array of Eq. (eqcountnum). */
+pes_status pes_jobc_stats(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                          int32_t paper_layout, int64_t* stats, int32_t* layer_sizes, int32_t cap);
+
+/* Convolution jobs in dispatch order: jobs[4 t + 0..3] = (input 1, input 2,
+ * output, layer), inputs and outputs as slots of the data array (multiply by
+ * d+1 for the paper's offsets of Sec. 5); at most cap jobs. */
+pes_status pes_jobc_jobs(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                         int32_t paper_layout, int32_t* jobs, int64_t cap);
+
+/* Sizes of the levels of the paper's pairwise addition tree (Sec. 5 and the
+ * launch counts of Sec. 6.1); at most cap levels, *nlevels receives the count. */
+pes_status pes_jobc_add_levels(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                               int64_t* levels, int32_t cap, int32_t* nlevels);
+
+/* Series summed by the addition stage: output 0 is the value, output 1+i the
+ * partial derivative d p / d x_i; its terms are the slots
+ * add_src[add_ptr[o] .. add_ptr[o+1]) of the data array (a coefficient slot a_m
+ * for a monomial of one variable, else a forward, backward or cross product).
+ * add_ptr: n+2 entries; at most cap terms are written. */
+pes_status pes_jobc_add_terms(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                              int32_t* add_ptr, int32_t* add_src, int64_t cap);
+
+/* Self-test of the failure path: runs the convolution kernel on one job that
+ * waits for a completion flag nobody sets, with the given bound (ms).  Returns
+ * PES_OK when the kernel gave up on its own and reported PES_ETIMEOUT through
+ * the status word (written to *device_status), leaving the context usable. */
+pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status);
+
+/* Human-readable name of a status code; never NULL. */
+const char* pes_status_string(pes_status s);
+/* Message of the last PES_EINVAL / PES_ECUDA on this thread ("" if none). */
+const char* pes_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PES_H */

@@ -59,6 +59,7 @@ def _load():
                 "orc_eval_grad": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, c_int],
                 "orc_vjp": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, dp, c_int],
                 "orc_threads": [c_int],
+                "orc_conv_many": [c_int, c_int, c_int, dp, dp, dp, c_int],
             }.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
@@ -114,6 +115,15 @@ def conv(x, y):
     k, s = x.shape
     z = np.empty_like(x)
     _check(_load().orc_conv(k, s - 1, _dp(x), _dp(y), _dp(z)), "conv")
+    return z
+
+
+def conv_many(x, y, nthreads: int = 0):
+    """Independent truncated products of (k, count, d+1) arrays, pairwise."""
+    x, y = _f64(x), _f64(y)
+    k, count, s = x.shape
+    z = np.empty_like(x)
+    _check(_load().orc_conv_many(k, s - 1, count, _dp(x), _dp(y), _dp(z), nthreads), "conv_many")
     return z
 
 

@@ -618,3 +618,41 @@ int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *
 
 /* number of threads the oracle would use for nthreads (for reporting) */
 int orc_threads(int nthreads) { return used_threads(nthreads); }
+
+/* count independent truncated products Z[c] = X[c] * Y[c] (Eq. eqconvform),
+ * arrays [k][count][d+1]; the pairs are spread over threads. */
+int orc_conv_many(int k, int d, int count, const double *X, const double *Y, double *Z, int nthreads)
+{
+    if (!valid_k(k) || d < 0 || count < 0)
+        return 1;
+    const size_t S = (size_t)d + 1;
+    const size_t ls = (size_t)count * S;
+    int fail = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(used_threads(nthreads))
+#endif
+    {
+        expn e;
+        int ok = expn_init(&e, 4 * k * k + 64);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int c = 0; c < count; ++c) {
+            if (!ok)
+                continue;
+            cser x = {X + (size_t)c * S, ls}, y = {Y + (size_t)c * S, ls};
+            ser z = {Z + (size_t)c * S, ls};
+            conv(k, d, x, y, z, &e);
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        {
+            if (!ok)
+                fail = 1;
+        }
+        if (ok)
+            expn_free(&e);
+    }
+    return fail ? 3 : 0;
+}

@@ -1,0 +1,218 @@
+// digits.cuh -- exact fixed-point digits for multiple double dot products.
+//
+// A k-double number x (limbs x[0..k-1], nonoverlapping, |x[0]| largest) is
+// written on a grid g (an integer) as
+//     x ~= 2^(B g) * sum_{p=0..L-1} X_p 2^(-B (p+1)),   |X_p| <= 2^(B-1),
+// with B = 24-bit balanced digits X_p.  Products of two digits are at most 2^46
+// in magnitude, so they are exact in a double and in an int64, and sums of up to
+// 128 of them stay exact in a double (2^53), which is what makes the
+// multiply-accumulate loop of a truncated series product (Eq. eqconvform) an
+// error-free transformation: every term x_i y_{j-i} is accumulated exactly into
+// digit positions, and the sum is rounded once to k limbs at the end.
+//
+// The number of digits L per k is chosen so that the dropped tail of every term
+// is below 2^-(53k+12) of the largest term (see digits_for_k).
+//
+// All conversions (limbs -> digits, digits -> limbs) use integer operations only;
+// the FP64 pipe is left to the multiply-accumulate loop.
+#pragma once
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#if defined(__CUDACC__)
+#define PES_HD __host__ __device__ __forceinline__
+#define PES_HDC __host__ __device__ constexpr
+#else
+#define PES_HD inline
+#define PES_HDC constexpr
+#endif
+
+namespace pes {
+
+PES_HD uint64_t dbits(double x) {
+#if defined(__CUDA_ARCH__)
+  return static_cast<uint64_t>(__double_as_longlong(x));
+#else
+  uint64_t u;
+  std::memcpy(&u, &x, sizeof(u));
+  return u;
+#endif
+}
+
+PES_HD int clz64(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+  return __clzll(static_cast<long long>(x));
+#else
+  return __builtin_clzll(x);
+#endif
+}
+
+constexpr int DIGIT_BITS = 24;
+constexpr int64_t DIGIT_BASE = int64_t(1) << DIGIT_BITS;
+constexpr int64_t DIGIT_HALF = int64_t(1) << (DIGIT_BITS - 1);
+constexpr int64_t DIGIT_MASK = DIGIT_BASE - 1;
+// grid of a zero coefficient: far below any real grid so that every term with
+// it is skipped
+constexpr int32_t GRID_ZERO = -(1 << 28);
+
+// L: smallest number of digits with B (L - 1) >= 53 k + 28 (12 guard bits plus
+// log2 of (1024 terms x 40 digit products)), see the error budget above.
+PES_HDC int digits_for_k(int k) {
+  return (53 * k + 28 + DIGIT_BITS - 1) / DIGIT_BITS + 1;
+}
+
+PES_HD int32_t floordiv(int32_t a, int32_t b) {
+  int32_t q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+// Decode a double into sign, 53-bit integer mantissa and exponent of its lsb:
+// x = sign * mant * 2^lsb.  Returns false for zero.
+PES_HD bool decode(double x, int& neg, uint64_t& mant, int32_t& lsb) {
+  uint64_t bits = dbits(x);
+  uint32_t be = static_cast<uint32_t>((bits >> 52) & 0x7FF);
+  uint64_t frac = bits & ((uint64_t(1) << 52) - 1);
+  neg = static_cast<int>(bits >> 63);
+  if (be == 0) {
+    if (frac == 0) return false;
+    mant = frac;
+    lsb = -1074;
+  } else {
+    mant = frac | (uint64_t(1) << 52);
+    lsb = static_cast<int32_t>(be) - 1075;
+  }
+  return true;
+}
+
+// Grid of a k-double whose leading limb is x0: g = ceil((e + 2) / B) where
+// |x| <= 2^e, so that |x| <= 2^(B g - 2).
+PES_HD int32_t grid_of(double x0) {
+  uint64_t bits = dbits(x0);
+  uint32_t be = static_cast<uint32_t>((bits >> 52) & 0x7FF);
+  if ((bits << 1) == 0) return GRID_ZERO;
+  int32_t e = (be == 0 ? 1 : static_cast<int32_t>(be)) - 1022;  // |x0| < 2^e
+  return floordiv(e + 2 + DIGIT_BITS - 1, DIGIT_BITS);
+}
+
+// Signed piece of limb (neg, mant, lsb) inside the digit window whose lsb is at
+// absolute bit position P (bits [P, P + B)), truncated toward zero.
+PES_HD int64_t window(int neg, uint64_t mant, int32_t lsb, int32_t P) {
+  int32_t sh = P - lsb;
+  uint64_t v;
+  if (sh >= 0)
+    v = sh >= 64 ? 0 : (mant >> sh);
+  else
+    v = (-sh) >= DIGIT_BITS ? 0 : (mant << (-sh));
+  int64_t piece = static_cast<int64_t>(v & static_cast<uint64_t>(DIGIT_MASK));
+  return neg ? -piece : piece;
+}
+
+// Digits of a k-double on grid g into D[0..L-1] (registers), balanced.
+// x: limb l at x[l * ls].  Bits below the last digit are dropped.
+template <int K, int L>
+PES_HD void to_digits(const double* x, int ls, int32_t g, int64_t (&D)[L]) {
+#pragma unroll
+  for (int p = 0; p < L; ++p) D[p] = 0;
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    int neg;
+    uint64_t mant;
+    int32_t lsb;
+    if (!decode(x[l * ls], neg, mant, lsb)) continue;
+#pragma unroll
+    for (int p = 0; p < L; ++p) {
+      int32_t P = DIGIT_BITS * g - DIGIT_BITS * (p + 1);
+      D[p] += window(neg, mant, lsb, P);
+    }
+  }
+  // balanced digits: carry from the bottom up
+#pragma unroll
+  for (int p = L - 1; p >= 1; --p) {
+    int64_t c = (D[p] + DIGIT_HALF) >> DIGIT_BITS;
+    D[p] -= c << DIGIT_BITS;
+    D[p - 1] += c;
+  }
+}
+
+// Round the exact fixed-point sum V = sum_{a=0..L} E[a] 2^(B (L - a)) times
+// 2^(B gs - B (L + 1)) to K nonoverlapping limbs (round to nearest, ties away),
+// written to out[l * ls].  E is destroyed.
+template <int K, int L>
+PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long ls) {
+  constexpr int NA = L + 1;
+  // floor-normalise: E[1..L] in [0, 2^B), E[0] carries the sign
+  auto normalise = [&]() {
+#pragma unroll
+    for (int a = NA - 1; a >= 1; --a) {
+      int64_t c = E[a] >> DIGIT_BITS;
+      E[a] -= c << DIGIT_BITS;
+      E[a - 1] += c;
+    }
+  };
+  normalise();
+  double sign = 1.0;
+  if (E[0] < 0) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) E[a] = -E[a];
+    normalise();
+    sign = -1.0;
+  }
+  const int32_t base_exp = DIGIT_BITS * gs - DIGIT_BITS * (L + 1);
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    // highest set bit of the magnitude
+    int top = -1;
+    int32_t h = 0;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      if (top < 0 && E[a] != 0) {
+        top = a;
+        h = DIGIT_BITS * (L - a) + (63 - clz64(static_cast<uint64_t>(E[a])));
+      }
+    }
+    if (top < 0) {
+#pragma unroll
+      for (int r = l; r < K; ++r) out[r * ls] = 0.0;
+      return;
+    }
+    // 64-bit window W = floor(V / 2^(h - 63))
+    uint64_t W = 0;
+    const int32_t wlo = h - 63;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      int32_t pos = DIGIT_BITS * (L - a) - wlo;  // shift of digit a inside the window
+      uint64_t dv = static_cast<uint64_t>(E[a]);
+      if (pos >= 0) {
+        if (pos < 64) W |= dv << pos;
+      } else if (pos > -64) {
+        W |= dv >> (-pos);
+      }
+    }
+    uint64_t m = (W >> 11) + ((W >> 10) & 1);  // 53 bits, rounded
+    int32_t mexp = h - 52;                      // weight of the mantissa lsb
+    out[l * ls] = sign * ldexp(static_cast<double>(m), mexp + base_exp);
+    // V -= m * 2^mexp (exact): digit a receives the bits of m 2^mexp in its
+    // window [B (L - a), B (L - a) + B); digit 0 receives everything above.
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      int32_t sh = mexp - DIGIT_BITS * (L - a);
+      uint64_t piece;
+      if (sh >= 0)
+        piece = sh >= 64 ? 0 : (m << sh);
+      else
+        piece = (-sh) >= 64 ? 0 : (m >> (-sh));
+      if (a > 0) piece &= static_cast<uint64_t>(DIGIT_MASK);
+      E[a] -= static_cast<int64_t>(piece);
+    }
+    normalise();
+    if (E[0] < 0) {
+#pragma unroll
+      for (int a = 0; a < NA; ++a) E[a] = -E[a];
+      normalise();
+      sign = -sign;
+    }
+  }
+}
+
+}  // namespace pes

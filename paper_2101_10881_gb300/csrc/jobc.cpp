@@ -1,0 +1,220 @@
+// jobc.cpp -- host job-table compiler.  See jobc.hpp.
+//
+// Reverse mode of one monomial a x_{i_1} ... x_{i_n} (Sec. 3), with the index
+// readings that the paper's own counts confirm:
+//   f_1 = a * z_{i_1},  f_l = f_{l-1} * z_{i_l}                (layer l)
+//   b_1 = z_{i_n} * z_{i_{n-1}},  b_l = b_{l-1} * z_{i_{n-l}}   (layer l, l <= n-2)
+//   bA  = b_{n-2} * a                                          (layer n-1)
+//   c_j = f_j * b_{n-2-j}, j = 1..n-3        (layer max(j, n-2-j) + 1)
+//   c_{n-2} = f_{n-2} * z_{i_n}                                (layer n-1)
+// giving 3n-3 products; the value term is f_n and the partials are
+//   d/dx_{i_1} = bA, d/dx_{i_{j+1}} = c_j (j = 1..n-2), d/dx_{i_n} = f_{n-1}.
+// Small monomials (the paper assumes n > 2): n = 2 uses f_1, f_2 and
+// b_1 = z_{i_2} * a (3 products); n = 1 uses f_1 = a * z_{i_1} and its partial
+// is the coefficient series a itself.
+// bA is kept in its own slot (the paper updates b_{n-2} in place) so that the
+// product of the variables alone stays available to the VJP.
+#include "jobc.hpp"
+
+#include <algorithm>
+#include <numeric>
+
+namespace pes {
+
+std::string validate(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t n) {
+  if (N < 0) return "N must be >= 0";
+  if (n < 1) return "n must be >= 1";
+  if (N > 0 && (ptr == nullptr || idx == nullptr)) return "null support arrays";
+  if (N > 0 && ptr[0] != 0) return "supp_ptr[0] must be 0";
+  for (int32_t m = 0; m < N; ++m) {
+    if (ptr[m + 1] <= ptr[m]) return "empty or decreasing monomial row " + std::to_string(m);
+    for (int32_t t = ptr[m]; t < ptr[m + 1]; ++t) {
+      if (idx[t] < 0 || idx[t] >= n) return "variable index out of range in monomial " + std::to_string(m);
+      if (t > ptr[m] && idx[t] <= idx[t - 1])
+        return "indices not strictly increasing in monomial " + std::to_string(m);
+    }
+  }
+  return "";
+}
+
+namespace {
+
+struct Builder {
+  std::vector<ConvJob> jobs;
+  void add(int32_t in1, int32_t in2, int32_t out, int32_t layer, int32_t kind = JOB_CONV) {
+    jobs.push_back(ConvJob{in1, in2, out, -1, -1, 0, kind, layer});
+  }
+};
+
+// Stable sort by layer, then resolve producer jobs of every operand slot.
+void finalize(std::vector<ConvJob>& jobs, int32_t n_slots) {
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [](const ConvJob& a, const ConvJob& b) { return a.layer < b.layer; });
+  std::vector<int32_t> producer(static_cast<size_t>(n_slots), -1);
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    ConvJob& jb = jobs[j];
+    jb.dep1 = producer[static_cast<size_t>(jb.in1)];
+    jb.dep2 = producer[static_cast<size_t>(jb.in2)];
+    producer[static_cast<size_t>(jb.out)] = static_cast<int32_t>(j);
+  }
+}
+
+}  // namespace
+
+Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp) {
+  Program1 P;
+  P.N = s.N;
+  P.n = s.n;
+  P.d = d;
+  const int32_t N = s.N, n = s.n;
+  auto A = [](int32_t k) { return k; };                 // coefficient a_k, k = 1..N
+  auto Z = [N](int32_t v) { return 1 + N + v; };         // input z_v, v 0-based
+  P.n_input_slots = 1 + N + n;
+
+  // ---- slot layout (Eq. eqcountnum order: inputs, all f, all b, all c) ----
+  P.mono.resize(static_cast<size_t>(N));
+  int32_t next = P.n_input_slots;
+  for (int32_t m = 0; m < N; ++m) {
+    MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    ms.nk = s.ptr[m + 1] - s.ptr[m];
+    ms.f0 = next;
+    next += ms.nk;
+  }
+  for (int32_t m = 0; m < N; ++m) {
+    MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    ms.nb = paper_layout ? std::max(1, ms.nk - 2) : (ms.nk >= 2 ? std::max(1, ms.nk - 2) : 0);
+    ms.b0 = next;
+    next += ms.nb;
+  }
+  for (int32_t m = 0; m < N; ++m) {
+    MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    ms.nc = std::max(0, ms.nk - 2);
+    ms.c0 = next;
+    next += ms.nc;
+  }
+  for (int32_t m = 0; m < N; ++m) {
+    MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    if (ms.nk >= 3) {
+      if (paper_layout) {
+        ms.bA = ms.b0 + ms.nk - 3;  // in place: b_{k,nk-2}
+      } else {
+        ms.bA = next++;
+      }
+    } else {
+      ms.bA = -1;
+    }
+  }
+  P.n_slots = next;
+
+  // ---- convolution jobs ----
+  Builder B;
+  int32_t max_layer = 0;
+  for (int32_t m = 0; m < N; ++m) {
+    const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    const int32_t* v = s.idx.data() + s.ptr[m];
+    const int32_t nk = ms.nk, k = m + 1;
+    auto f = [&](int32_t l) { return ms.f0 + l - 1; };  // f_{k,l}, l = 1..nk
+    auto b = [&](int32_t l) { return ms.b0 + l - 1; };  // b_{k,l}
+    auto c = [&](int32_t l) { return ms.c0 + l - 1; };  // c_{k,l}
+    B.add(A(k), Z(v[0]), f(1), 1);
+    for (int32_t l = 2; l <= nk; ++l) B.add(f(l - 1), Z(v[l - 1]), f(l), l);
+    if (nk == 2) {
+      B.add(Z(v[1]), A(k), b(1), 1);
+    } else if (nk >= 3) {
+      B.add(Z(v[nk - 1]), Z(v[nk - 2]), b(1), 1);
+      for (int32_t l = 2; l <= nk - 2; ++l) B.add(b(l - 1), Z(v[nk - 1 - l]), b(l), l);
+      B.add(b(nk - 2), A(k), ms.bA, nk - 1);
+      for (int32_t j = 1; j <= nk - 3; ++j) B.add(f(j), b(nk - 2 - j), c(j), std::max(j, nk - 2 - j) + 1);
+      B.add(f(nk - 2), Z(v[nk - 1]), c(nk - 2), nk - 1);
+    }
+    max_layer = std::max(max_layer, nk);
+  }
+  P.jobs = B.jobs;
+  finalize(P.jobs, P.n_slots);
+  P.n_layers = max_layer;
+  P.layer_ptr.assign(static_cast<size_t>(max_layer) + 1, 0);
+  for (const ConvJob& j : P.jobs) P.layer_ptr[static_cast<size_t>(j.layer)]++;
+  for (int32_t L = 1; L <= max_layer; ++L) P.layer_ptr[static_cast<size_t>(L)] += P.layer_ptr[static_cast<size_t>(L) - 1];
+
+  // ---- addition stage: value and gradient contributions, monomial order ----
+  std::vector<std::vector<int32_t>> contrib(static_cast<size_t>(n) + 1);
+  contrib[0].push_back(0);  // a_0
+  for (int32_t m = 0; m < N; ++m) {
+    const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    const int32_t* v = s.idx.data() + s.ptr[m];
+    const int32_t nk = ms.nk, k = m + 1;
+    contrib[0].push_back(ms.f0 + nk - 1);
+    if (nk == 1) {
+      contrib[1 + static_cast<size_t>(v[0])].push_back(A(k));
+    } else if (nk == 2) {
+      contrib[1 + static_cast<size_t>(v[0])].push_back(ms.b0);  // b_1 = z_{i_2} a
+      contrib[1 + static_cast<size_t>(v[1])].push_back(ms.f0);  // f_1 = a z_{i_1}
+    } else {
+      contrib[1 + static_cast<size_t>(v[0])].push_back(ms.bA);
+      for (int32_t j = 1; j <= nk - 2; ++j) contrib[1 + static_cast<size_t>(v[j])].push_back(ms.c0 + j - 1);
+      contrib[1 + static_cast<size_t>(v[nk - 1])].push_back(ms.f0 + nk - 2);
+    }
+  }
+  P.add_ptr.assign(static_cast<size_t>(n) + 2, 0);
+  for (size_t o = 0; o < contrib.size(); ++o) P.add_ptr[o + 1] = P.add_ptr[o] + static_cast<int32_t>(contrib[o].size());
+  P.add_src.reserve(static_cast<size_t>(P.add_ptr.back()));
+  for (const auto& cl : contrib) P.add_src.insert(P.add_src.end(), cl.begin(), cl.end());
+
+  if (!with_vjp || paper_layout) return P;
+
+  // ---- VJP extras: M_k (product of the variables), gradient series, correlations ----
+  int32_t nx = P.n_slots;
+  P.slot_u = nx++;
+  P.mslot.assign(static_cast<size_t>(N), -1);
+  Builder V;
+  V.jobs = P.jobs;  // forward products first
+  for (ConvJob& j : V.jobs) j.dep1 = j.dep2 = -1;
+  P.slot_M0 = nx;
+  for (int32_t m = 0; m < N; ++m) {
+    const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
+    const int32_t* v = s.idx.data() + s.ptr[m];
+    if (ms.nk == 1) {
+      P.mslot[static_cast<size_t>(m)] = Z(v[0]);
+    } else if (ms.nk == 2) {
+      P.mslot[static_cast<size_t>(m)] = nx;
+      V.add(Z(v[0]), Z(v[1]), nx++, 1);
+    } else {
+      P.mslot[static_cast<size_t>(m)] = nx;
+      V.add(ms.b0 + ms.nk - 3, Z(v[0]), nx++, ms.nk - 1);  // b_{k,nk-2} * z_{i_1}
+    }
+  }
+  P.slot_g0 = nx;
+  nx += n;
+  P.slot_r0 = nx;
+  nx += N + n;
+  P.n_slots_vjp = nx;
+  finalize(V.jobs, nx);
+  P.vjp_fwd_jobs = static_cast<int32_t>(V.jobs.size());
+  for (int32_t m = 0; m < N; ++m)
+    V.jobs.push_back(ConvJob{P.slot_u, P.mslot[static_cast<size_t>(m)], P.slot_r0 + m, -1, -1, 0, JOB_CORR, 1});
+  for (int32_t i = 0; i < n; ++i)
+    V.jobs.push_back(ConvJob{P.slot_u, P.slot_g0 + i, P.slot_r0 + N + i, -1, -1, 0, JOB_CORR, 1});
+  P.vjp_jobs = V.jobs;
+  return P;
+}
+
+std::vector<int64_t> paper_add_levels(const Supports& s) {
+  std::vector<int64_t> sizes;
+  sizes.push_back(static_cast<int64_t>(s.N) + 1);  // value: a_0 and N forward products
+  std::vector<int64_t> deg(static_cast<size_t>(s.n), 0);
+  for (int32_t t = 0; t < (s.N > 0 ? s.ptr[static_cast<size_t>(s.N)] : 0); ++t) deg[static_cast<size_t>(s.idx[static_cast<size_t>(t)])]++;
+  for (int64_t g : deg) sizes.push_back(g);
+  std::vector<int64_t> levels;
+  for (;;) {
+    int64_t adds = 0;
+    for (int64_t& m : sizes) {
+      adds += m / 2;
+      m -= m / 2;
+    }
+    if (adds == 0) break;
+    levels.push_back(adds);
+  }
+  return levels;
+}
+
+}  // namespace pes

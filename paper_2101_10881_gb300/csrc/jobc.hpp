@@ -1,0 +1,118 @@
+// jobc.hpp -- host job-table compiler (integer only, no CUDA).
+//
+// Turns monomial supports into the convolution jobs of the reverse mode of
+// Sec. 3 (forward products f, backward products b, cross products c) placed in
+// layers (Sec. 5, "Jobs are placed in layers"), and into the addition work of
+// the second stage (Sec. 5, pairs of the tree summation).  The same tables drive
+// one polynomial or a batch of them: a batch is the concatenation of the
+// instances' tables, each instance with its own workspace region and degree.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pes {
+
+// Job kinds.
+enum : int32_t { JOB_CONV = 0, JOB_CORR = 1 };
+
+// Where instance `inst` keeps series slot s, limb l, coefficient j (in doubles,
+// from the workspace base): ws_base + l * ws_lstride + s * S + j.
+struct InstInfo {
+  int64_t ws_base;
+  int64_t ws_lstride;
+  int32_t S;  // padded series stride (multiple of 8 doubles)
+  int32_t d;  // truncation degree
+};
+
+// One convolution (or correlation) job: out := in1 * in2 (slots of one instance).
+// dep1/dep2: index of the job that produces in1/in2 in the same job list, or -1
+// when the operand is an input series.
+struct ConvJob {
+  int32_t in1, in2, out;
+  int32_t dep1, dep2;
+  int32_t inst;
+  int32_t kind;
+  int32_t layer;
+};
+
+// One output series of the addition stage: the exact sum of the series in
+// contrib[cbeg, cend) (slots of instance `inst`), written to destination buffer
+// `dst_sel` at dst_off + l * dst_lstride + j.
+struct AddOut {
+  int64_t dst_off;
+  int64_t dst_lstride;
+  int32_t dst_sel;
+  int32_t inst;
+  int32_t cbeg, cend;
+};
+
+// One series copy between a caller buffer and the workspace.  For a pack (caller
+// to workspace) src is the caller buffer `sel`; for an unpack it is the target.
+struct CopyRow {
+  int64_t off;      // caller-buffer offset of coefficient 0, limb 0 (doubles)
+  int64_t lstride;  // caller-buffer limb stride (doubles)
+  int32_t sel;      // which caller buffer
+  int32_t inst;
+  int32_t slot;     // workspace slot
+  int32_t pad;
+};
+
+// Slots of one monomial in the product layout.
+struct MonoSlots {
+  int32_t nk;
+  int32_t f0;   // f_{k,1}..f_{k,nk}: f0 .. f0+nk-1
+  int32_t b0;   // b_{k,1}..: b0 ..
+  int32_t nb;   // number of b slots (max(1, nk-2) for nk>=2, 0 for nk==1)
+  int32_t bA;   // slot of b_{k,nk-2} * a_k (nk >= 3), else -1
+  int32_t c0;   // c_{k,1}..c_{k,nk-2}
+  int32_t nc;
+};
+
+// Parsed, validated supports of one polynomial.
+struct Supports {
+  int32_t N = 0, n = 0;
+  std::vector<int32_t> ptr, idx;  // CSR, 0-based, increasing per row
+};
+
+// Returns "" if valid, else a message.  Rules: N >= 0, n >= 1, every monomial
+// non-empty, indices in [0, n), strictly increasing within a monomial.
+std::string validate(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t n);
+
+// Layout and jobs of one polynomial (slot numbering local to the instance).
+struct Program1 {
+  int32_t N = 0, n = 0, d = 0;
+  int32_t n_input_slots = 0;   // 1 + N + n (a_0, a_1..a_N, z_1..z_n)
+  int32_t n_slots = 0;         // total slots of the eval+grad layout
+  int32_t n_layers = 0;
+  std::vector<MonoSlots> mono;
+  std::vector<ConvJob> jobs;   // sorted by layer (stable in monomial order)
+  std::vector<int32_t> layer_ptr;      // jobs of layer L (1-based) at [layer_ptr[L-1], layer_ptr[L])
+  // addition stage: output 0 = value, output 1+i = d p / d x_i
+  std::vector<int32_t> add_ptr;        // n+2 entries
+  std::vector<int32_t> add_src;        // contributing slots
+  // VJP extras (slots after the eval+grad layout)
+  int32_t slot_u = -1;                 // upstream series
+  int32_t slot_M0 = -1;                // M_k (k = 1..N) at slot_M0 + k - 1 (or an input slot, see mslot)
+  std::vector<int32_t> mslot;          // slot holding M_k (input slot when nk == 1)
+  int32_t slot_g0 = -1;                // gradient series g_i at slot_g0 + i
+  int32_t slot_r0 = -1;                // correlation outputs: N coefficient + n input series
+  int32_t n_slots_vjp = 0;
+  std::vector<ConvJob> vjp_jobs;       // forward jobs + M jobs (topological), then correlation jobs
+  int32_t vjp_fwd_jobs = 0;            // number of conv jobs before the correlations
+};
+
+// Build the eval+grad layout and jobs.  paper_layout=true reproduces the data
+// array of Eq. (eqcountnum) (b_{k,nk-2} updated in place, no VJP extras); it is
+// used for the offset/count checks against the paper only.
+Program1 compile(const Supports& s, int32_t d, bool paper_layout = false, bool with_vjp = false);
+
+// Addition-tree level sizes of the paper's pairwise summation (Sec. 5, read with
+// a_0 as one more term of the value sum): each level pairs floor(m/2) of a list
+// of m terms, for the value and for every gradient sum.
+std::vector<int64_t> paper_add_levels(const Supports& s);
+
+// Padded series stride for degree d (multiple of 8 doubles, 64 bytes).
+inline int32_t series_stride(int32_t d) { return ((d + 1) + 7) / 8 * 8; }
+
+}  // namespace pes

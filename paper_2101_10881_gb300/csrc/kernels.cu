@@ -1,0 +1,614 @@
+// kernels.cu -- the CUDA kernels of the evaluation and differentiation path.
+//
+//   pack      caller series -> workspace (padded limb planes)        (Sec. 2, data layout)
+//   dag       all convolution jobs of all layers in one persistent launch (Sec. 5):
+//             operands staged into shared memory by TMA bulk copies, converted
+//             to exact digits, every output coefficient the exact sum of its
+//             terms (Eq. eqconvform) rounded once to k limbs
+//   add       value and gradient sums (Sec. 5, addition jobs): one warp per
+//             output coefficient, contributions spread over the lanes, exact
+//             digit sums reduced with warp shuffles
+//   unpack    workspace -> caller series
+//   md_binary elementwise k-double add / mul (Sec. 1 arithmetic)
+//   fp64_peak DFMA throughput microbenchmark (the roofline of the FP64 variant)
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "digits.cuh"
+#include "kernels.hpp"
+#include "md.cuh"
+
+namespace pes {
+
+namespace {
+
+constexpr int kStatusTimeout = 5;  // PES_ETIMEOUT
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Plain (non-tensor, non-multicast) bulk copy global -> this CTA's shared memory.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long timeout_ns) {
+  if (mbar_try_wait(bar, phase)) return true;
+  unsigned long long t0 = global_timer();
+  for (;;) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if (static_cast<long long>(global_timer() - t0) > timeout_ns) return false;
+  }
+}
+
+__device__ __forceinline__ long long mac(int32_t x, int32_t y, long long acc) {
+  long long r;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(r) : "r"(x), "r"(y), "l"(acc));
+  return r;
+}
+
+__device__ __forceinline__ double mac(double x, double y, double acc) { return __fma_rn(x, y, acc); }
+
+__device__ __forceinline__ void set_error(Ctrl* ctrl, int code, long long d0, long long d1) {
+  if (atomicCAS(&ctrl->status, 0, code) == 0) {
+    ctrl->diag[0] = d0;
+    ctrl->diag[1] = d1;
+  }
+  atomicExch(&ctrl->abort, 1);
+}
+
+// Bounded wait until job `dep` of this call has completed.
+__device__ bool wait_done(const DagArgs& a, int dep, int epoch, int job) {
+  if (dep < 0) return true;
+  if (ld_acquire(a.flags + dep) == epoch) return true;
+  unsigned long long t0 = global_timer();
+  for (;;) {
+    if (ld_acquire(a.flags + dep) == epoch) return true;
+    if (*reinterpret_cast<volatile int32_t*>(&a.ctrl->abort)) return false;
+    if (static_cast<long long>(global_timer() - t0) > a.timeout_ns) {
+      set_error(a.ctrl, kStatusTimeout, dep, job);
+      return false;
+    }
+    __nanosleep(200);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DAG kernel shared-memory layout
+// ---------------------------------------------------------------------------
+
+struct DagLayout {
+  size_t raw, xdig, ydig, gx, gy, gs, bar, misc, total;
+};
+
+__host__ __device__ inline DagLayout dag_layout(int K, int L, int digit_bytes, int smax, int dmax) {
+  const int LP = L | 1;
+  DagLayout o;
+  size_t raw_bytes = size_t(2) * K * smax * sizeof(double);
+  size_t exch_bytes = size_t(dmax + 1) * (L + 1) * sizeof(unsigned long long);
+  o.raw = 0;
+  size_t off = align_up(raw_bytes > exch_bytes ? raw_bytes : exch_bytes, 128);
+  o.xdig = off;
+  off = align_up(off + size_t(smax) * LP * digit_bytes, 16);
+  o.ydig = off;
+  off = align_up(off + size_t(smax) * LP * digit_bytes, 16);
+  o.gx = off;
+  off += size_t(smax) * 4;
+  o.gy = off;
+  off += size_t(smax) * 4;
+  o.gs = off;
+  off = align_up(off + size_t(smax) * 4, 16);
+  o.bar = off;
+  off += 16;
+  o.misc = off;
+  off += 64;
+  o.total = align_up(off, 128);
+  return o;
+}
+
+// first coefficient j with start(j) > g, minus one
+__device__ __forceinline__ long long conv_start(long long j) { return j * (j + 1) / 2; }
+__device__ __forceinline__ long long corr_start(long long j, long long d) { return j * (d + 1) - j * (j - 1) / 2; }
+
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
+  using DigitT = typename std::conditional<INTV, int32_t, double>::type;
+  using AccT = typename std::conditional<INTV, long long, double>::type;
+  constexpr int L = digits_for_k(K);
+  constexpr int LP = L | 1;
+  constexpr int R = 128 / L;  // FP64 accumulators stay exact for R terms
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const DagLayout lay = dag_layout(K, L, sizeof(DigitT), a.smax, a.dmax);
+  double* raw = reinterpret_cast<double*>(smem + lay.raw);
+  unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.raw);
+  DigitT* xdig = reinterpret_cast<DigitT*>(smem + lay.xdig);
+  DigitT* ydig = reinterpret_cast<DigitT*>(smem + lay.ydig);
+  int32_t* gx = reinterpret_cast<int32_t*>(smem + lay.gx);
+  int32_t* gy = reinterpret_cast<int32_t*>(smem + lay.gy);
+  int32_t* gs = reinterpret_cast<int32_t*>(smem + lay.gs);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
+  int32_t* misc = reinterpret_cast<int32_t*>(smem + lay.misc);
+
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const uint32_t bar_addr = smem_u32(bar);
+  if (tid == 0) {
+    mbar_init(bar_addr, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int epoch = *reinterpret_cast<volatile int32_t*>(&a.ctrl->epoch);
+  uint32_t phase = 0;
+
+  for (;;) {
+    if (tid == 0) {
+      int job = atomicAdd(&a.ctrl->next[a.counter], 1);
+      int bad = 0;
+      if (job < a.njobs) {
+        const ConvJob jb = a.jobs[job];
+        if (!wait_done(a, jb.dep1, epoch, job) || !wait_done(a, jb.dep2, epoch, job)) bad = 1;
+      }
+      misc[0] = job;
+      misc[1] = bad;
+    }
+    __syncthreads();
+    const int job = misc[0];
+    if (job >= a.njobs || misc[1]) break;
+    const ConvJob jb = a.jobs[job];
+    const InstInfo in = a.inst[jb.inst];
+    const int d = in.d;
+    const int S = in.S;
+    const long long ls = in.ws_lstride;
+    const double* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * S;
+    const double* ys = a.ws + in.ws_base + static_cast<long long>(jb.in2) * S;
+    double* zs = a.ws + in.ws_base + static_cast<long long>(jb.out) * S;
+
+    // ---- stage both operand series (k limb planes each) with TMA bulk copies ----
+    if (tid == 0) {
+      fence_proxy_async_global();
+      fence_proxy_async_shared();
+      const uint32_t bytes = static_cast<uint32_t>(S) * sizeof(double);
+      mbar_expect_tx(bar_addr, 2u * K * bytes);
+      const uint32_t raw_addr = smem_u32(raw);
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        bulk_g2s(raw_addr + static_cast<uint32_t>(l) * bytes, xs + l * ls, bytes, bar_addr);
+        bulk_g2s(raw_addr + static_cast<uint32_t>(K + l) * bytes, ys + l * ls, bytes, bar_addr);
+      }
+    }
+    const bool landed = mbar_wait(bar_addr, phase, a.timeout_ns);
+    if (!__syncthreads_and(landed)) {
+      if (tid == 0) set_error(a.ctrl, kStatusTimeout, job, -2);
+      mbar_wait(bar_addr, phase, a.timeout_ns);  // let copies in flight land before exit
+      break;
+    }
+    phase ^= 1u;
+
+    // ---- exact digits of every staged coefficient ----
+    for (int c = tid; c <= d; c += T) {
+      int64_t D[L];
+      const int32_t g1 = grid_of(raw[c]);
+      to_digits<K, L>(raw + c, S, g1, D);
+      gx[c] = g1;
+#pragma unroll
+      for (int p = 0; p < L; ++p) xdig[c * LP + p] = static_cast<DigitT>(D[p]);
+      const int32_t g2 = grid_of(raw[K * S + c]);
+      to_digits<K, L>(raw + K * S + c, S, g2, D);
+      gy[c] = g2;
+#pragma unroll
+      for (int p = 0; p < L; ++p) ydig[c * LP + p] = static_cast<DigitT>(D[p]);
+    }
+    __syncthreads();
+
+    // ---- zero the exchange rows, reference grid of every output coefficient ----
+    const int rows = (d + 1) * (L + 1);
+    for (int t = tid; t < rows; t += T) exch[t] = 0ull;
+    for (int j = tid; j <= d; j += T) {
+      int32_t m = 2 * GRID_ZERO;
+      if (jb.kind == JOB_CONV) {
+        for (int i = 0; i <= j; ++i) m = max(m, gx[i] + gy[j - i]);
+      } else {
+        for (int i = 0; i <= d - j; ++i) m = max(m, gx[j + i] + gy[i]);
+      }
+      gs[j] = m;
+    }
+    __syncthreads();
+
+    // ---- multiply-accumulate: every thread runs the same number of terms ----
+    {
+      const bool conv = jb.kind == JOB_CONV;
+      const long long W = static_cast<long long>(d + 1) * (d + 2) / 2;
+      const long long g0 = W * tid / T;
+      const long long g1 = W * (tid + 1) / T;
+      const int cnt = static_cast<int>(g1 - g0);
+      int j = 0, i = 0;
+      if (cnt > 0) {
+        int lo = 0, hi = d;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          const long long st = conv ? conv_start(mid) : corr_start(mid, d);
+          if (st <= g0) lo = mid; else hi = mid - 1;
+        }
+        j = lo;
+        i = static_cast<int>(g0 - (conv ? conv_start(j) : corr_start(j, d)));
+      }
+      int nt = conv ? j + 1 : d - j + 1;
+      int gsj = cnt > 0 ? gs[j] : 0;
+      AccT A[L];
+#pragma unroll
+      for (int t = 0; t < L; ++t) A[t] = 0;
+      auto flush = [&](int jj) {
+        unsigned long long* row = exch + jj * (L + 1) + 1;
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+          long long v;
+          if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
+          if (v != 0) atomicAdd(row + t, static_cast<unsigned long long>(v));
+          A[t] = 0;
+        }
+      };
+      for (int s = 0; s < cnt; ++s) {
+        const int ix = conv ? i : j + i;
+        const int iy = conv ? j - i : i;
+        const int delta = gsj - gx[ix] - gy[iy];
+        if (delta < L) {
+          const DigitT* yr = ydig + iy * LP;
+          const DigitT* xr = xdig + ix * LP;
+          DigitT Y[L];
+#pragma unroll
+          for (int q = 0; q < L; ++q) Y[q] = yr[q];
+#pragma unroll
+          for (int p = 0; p < L; ++p) {
+            const int id = p - delta;
+            DigitT xv = xr[id < 0 ? 0 : id];
+            xv = id < 0 ? DigitT(0) : xv;
+#pragma unroll
+            for (int q = 0; q < L - p; ++q) A[p + q] = mac(xv, Y[q], A[p + q]);
+          }
+        }
+        ++i;
+        const bool end_coef = (i == nt);
+        bool do_flush = end_coef;
+        if constexpr (!INTV) do_flush = do_flush || ((s + 1) % R == 0);
+        if (do_flush) flush(j);
+        if (end_coef) {
+          ++j;
+          i = 0;
+          if (j <= d) {
+            nt = conv ? j + 1 : d - j + 1;
+            gsj = gs[j];
+          }
+        }
+      }
+      if (i > 0) flush(j);
+    }
+    __syncthreads();
+
+    // ---- one output coefficient per thread: round the exact sum to k limbs ----
+    for (int j = tid; j <= d; j += T) {
+      const int32_t g = gs[j];
+      if (g < -100000) {
+#pragma unroll
+        for (int l = 0; l < K; ++l) zs[l * ls + j] = 0.0;
+        continue;
+      }
+      int64_t E[L + 1];
+#pragma unroll
+      for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
+      from_digits<K, L>(E, g, zs + j, ls);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      fence_proxy_async_global();
+      st_release(a.flags + job, epoch);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pack / unpack
+// ---------------------------------------------------------------------------
+
+__global__ void pack_kernel(CopyArgs a, int K) {
+  const long long item = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (item >= static_cast<long long>(a.nrows) * K) return;
+  const int row = static_cast<int>(item / K);
+  const int l = static_cast<int>(item % K);
+  const CopyRow r = a.rows[row];
+  const InstInfo in = a.inst[r.inst];
+  const double* src = a.src[r.sel] + r.off + l * r.lstride;
+  double* dst = a.ws + in.ws_base + l * in.ws_lstride + static_cast<long long>(r.slot) * in.S;
+  for (int j = lane; j < in.S; j += 32) dst[j] = j <= in.d ? src[j] : 0.0;
+}
+
+__global__ void unpack_kernel(CopyArgs a, int K) {
+  const long long item = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (item >= static_cast<long long>(a.nrows) * K) return;
+  const int row = static_cast<int>(item / K);
+  const int l = static_cast<int>(item % K);
+  const CopyRow r = a.rows[row];
+  const InstInfo in = a.inst[r.inst];
+  double* dst = a.dst[r.sel] + r.off + l * r.lstride;
+  const double* src = a.ws + in.ws_base + l * in.ws_lstride + static_cast<long long>(r.slot) * in.S;
+  for (int j = lane; j <= in.d; j += 32) dst[j] = src[j];
+}
+
+__global__ void prologue_kernel(Ctrl* ctrl) {
+  if (threadIdx.x == 0) {
+    ctrl->epoch += 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ctrl->next[c] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// addition stage: warp per output coefficient, exact digit sums, warp shuffles
+// ---------------------------------------------------------------------------
+
+template <int K>
+__global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
+  constexpr int L = digits_for_k(K);
+  const long long w = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= items) return;
+  int lo = 0, hi = a.nouts - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.item_ptr[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  const AddOut ao = a.outs[lo];
+  const int j = static_cast<int>(w - a.item_ptr[lo]);
+  const InstInfo in = a.inst[ao.inst];
+  const long long ls = in.ws_lstride;
+  const double* base = a.ws + in.ws_base + j;
+
+  int32_t gmax = 2 * GRID_ZERO;
+  for (int c = ao.cbeg + lane; c < ao.cend; c += 32)
+    gmax = max(gmax, grid_of(base[static_cast<long long>(a.contrib[c]) * in.S]));
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+
+  double* dst = a.dst[ao.dst_sel] + ao.dst_off + j;
+  if (gmax < -100000) {
+    if (lane < K) dst[lane * ao.dst_lstride] = 0.0;
+    return;
+  }
+  int64_t acc[L];
+#pragma unroll
+  for (int p = 0; p < L; ++p) acc[p] = 0;
+  for (int c = ao.cbeg + lane; c < ao.cend; c += 32) {
+    int64_t D[L];
+    const double* x = base + static_cast<long long>(a.contrib[c]) * in.S;
+    double limbs[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) limbs[l] = x[l * ls];
+    to_digits<K, L>(limbs, 1, gmax, D);
+#pragma unroll
+    for (int p = 0; p < L; ++p) acc[p] += D[p];
+  }
+#pragma unroll
+  for (int p = 0; p < L; ++p) {
+    long long v = acc[p];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    acc[p] = v;
+  }
+  if (lane == 0) {
+    int64_t E[L + 1];
+#pragma unroll
+    for (int p = 0; p < L; ++p) E[p] = acc[p];
+    E[L] = 0;
+    from_digits<K, L>(E, gmax, dst, ao.dst_lstride);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise multiple double operations
+// ---------------------------------------------------------------------------
+
+template <int K>
+__global__ void md_binary_kernel(int op, const double* x, const double* y, double* out, long long count) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double a[K], b[K], r[K];
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    a[l] = x[l * count + i];
+    b[l] = y[l * count + i];
+  }
+  if (op == 0)
+    md::md_add<K>(a, b, r);
+  else
+    md::md_mul<K>(a, b, r);
+#pragma unroll
+  for (int l = 0; l < K; ++l) out[l * count + i] = r[l];
+}
+
+// DFMA throughput: 8 independent FMA chains per thread.
+__global__ void fp64_peak_kernel(double* sink, int iters, double a, double b) {
+  double acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = __fma_rn(acc[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += acc[i];
+  if (s == 12345.678) sink[blockIdx.x] = s;  // keeps the chains alive
+}
+
+template <int K, bool INTV>
+void* dag_fn() {
+  return reinterpret_cast<void*>(&dag_kernel<K, INTV>);
+}
+
+void* dag_kernel_ptr(int k, int arith) {
+  const bool iv = arith == ARITH_INT;
+  switch (k) {
+    case 1: return iv ? dag_fn<1, true>() : dag_fn<1, false>();
+    case 2: return iv ? dag_fn<2, true>() : dag_fn<2, false>();
+    case 3: return iv ? dag_fn<3, true>() : dag_fn<3, false>();
+    case 4: return iv ? dag_fn<4, true>() : dag_fn<4, false>();
+    case 5: return iv ? dag_fn<5, true>() : dag_fn<5, false>();
+    case 8: return iv ? dag_fn<8, true>() : dag_fn<8, false>();
+    case 10: return iv ? dag_fn<10, true>() : dag_fn<10, false>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+int digits_of_k(int k) { return digits_for_k(k); }
+
+size_t dag_smem_bytes(int k, int arith, int smax, int dmax) {
+  const int digit_bytes = arith == ARITH_INT ? 4 : 8;
+  return dag_layout(k, digits_for_k(k), digit_bytes, smax, dmax).total;
+}
+
+cudaError_t dag_prepare(int k, int arith, size_t smem) {
+  void* fn = dag_kernel_ptr(k, arith);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
+cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm) {
+  void* fn = dag_kernel_ptr(k, arith);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
+}
+
+cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st) {
+  void* fn = dag_kernel_ptr(k, arith);
+  if (!fn) return cudaErrorInvalidValue;
+  const size_t smem = dag_smem_bytes(k, arith, a.smax, a.dmax);
+  DagArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);
+}
+
+cudaError_t launch_prologue(Ctrl* ctrl, cudaStream_t st) {
+  prologue_kernel<<<1, 32, 0, st>>>(ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const CopyArgs& a, int k, cudaStream_t st) {
+  const long long items = static_cast<long long>(a.nrows) * k;
+  if (items == 0) return cudaSuccess;
+  const int warps = 8;
+  pack_kernel<<<static_cast<unsigned>((items + warps - 1) / warps), warps * 32, 0, st>>>(a, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const CopyArgs& a, int k, cudaStream_t st) {
+  const long long items = static_cast<long long>(a.nrows) * k;
+  if (items == 0) return cudaSuccess;
+  const int warps = 8;
+  unpack_kernel<<<static_cast<unsigned>((items + warps - 1) / warps), warps * 32, 0, st>>>(a, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(const AddArgs& a, int k, int64_t items, cudaStream_t st) {
+  if (items == 0) return cudaSuccess;
+  const int warps = 8;
+  const unsigned grid = static_cast<unsigned>((items + warps - 1) / warps);
+  switch (k) {
+    case 1: add_kernel<1><<<grid, warps * 32, 0, st>>>(a, items); break;
+    case 2: add_kernel<2><<<grid, warps * 32, 0, st>>>(a, items); break;
+    case 3: add_kernel<3><<<grid, warps * 32, 0, st>>>(a, items); break;
+    case 4: add_kernel<4><<<grid, warps * 32, 0, st>>>(a, items); break;
+    case 5: add_kernel<5><<<grid, warps * 32, 0, st>>>(a, items); break;
+    case 8: add_kernel<8><<<grid, warps * 32, 0, st>>>(a, items); break;
+    case 10: add_kernel<10><<<grid, warps * 32, 0, st>>>(a, items); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out, int64_t count,
+                             cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((count + 127) / 128);
+  switch (k) {
+    case 1: md_binary_kernel<1><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    case 2: md_binary_kernel<2><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    case 3: md_binary_kernel<3><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    case 4: md_binary_kernel<4><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    case 5: md_binary_kernel<5><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    case 8: md_binary_kernel<8><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    case 10: md_binary_kernel<10><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters, cudaStream_t st) {
+  fp64_peak_kernel<<<blocks, threads, 0, st>>>(sink, iters, 0.999999999, 1e-9);
+  return cudaGetLastError();
+}
+
+}  // namespace pes

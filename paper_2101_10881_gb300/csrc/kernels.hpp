@@ -1,0 +1,76 @@
+// kernels.hpp -- launch interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "jobc.hpp"
+
+namespace pes {
+
+// Arithmetic of the convolution multiply-accumulate loop.
+enum : int32_t {
+  ARITH_FP64 = 0,  // digit products accumulated with FP64 FMA (exact, flushed every R terms)
+  ARITH_INT = 1,   // digit products accumulated with 32x32->64-bit integer multiply-add
+};
+
+// Per-plan control block in device memory.
+struct Ctrl {
+  int32_t epoch;      // incremented once per call by the prologue kernel
+  int32_t abort;      // set when any wait gives up
+  int32_t status;     // first error code (pes_status), 0 when fine
+  int32_t pad0;
+  int32_t next[4];    // job dispatch counters (one per DAG launch of a call)
+  long long diag[4];  // diagnostics: [0] job that timed out, [1] waiting job
+};
+
+struct DagArgs {
+  const ConvJob* jobs;
+  int32_t njobs;
+  int32_t counter;          // which Ctrl::next
+  int32_t* flags;           // per job: epoch when done
+  const InstInfo* inst;
+  double* ws;
+  Ctrl* ctrl;
+  int32_t smax;             // largest padded stride of the instances
+  int32_t dmax;             // largest degree
+  long long timeout_ns;     // bound on every wait
+};
+
+struct AddArgs {
+  const AddOut* outs;
+  int32_t nouts;
+  const int64_t* item_ptr;  // nouts + 1 prefix sums of (d + 1) over outputs
+  const int32_t* contrib;
+  const InstInfo* inst;
+  const double* ws;
+  double* dst[2];
+};
+
+struct CopyArgs {
+  const CopyRow* rows;
+  int32_t nrows;
+  const InstInfo* inst;
+  double* ws;
+  const double* src[4];  // pack: caller buffers by selector
+  double* dst[4];        // unpack: caller buffers by selector
+};
+
+// Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax).
+size_t dag_smem_bytes(int k, int arith, int smax, int dmax);
+int digits_of_k(int k);
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_prologue(Ctrl* ctrl, cudaStream_t st);
+cudaError_t launch_pack(const CopyArgs& a, int k, cudaStream_t st);
+cudaError_t launch_unpack(const CopyArgs& a, int k, cudaStream_t st);
+cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st);
+cudaError_t launch_add(const AddArgs& a, int k, int64_t items, cudaStream_t st);
+cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t dag_prepare(int k, int arith, size_t smem);
+cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out,
+                             int64_t count, cudaStream_t st);
+cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters, cudaStream_t st);
+
+}  // namespace pes

@@ -1,0 +1,817 @@
+// pes_api.cu -- the C-ABI of include/pes.h: plans, batches and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pes.h"
+#include "jobc.hpp"
+#include "kernels.hpp"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pes_status fail(pes_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+pes_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return PES_ECUDA;
+}
+
+#define PES_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+bool valid_k(int32_t k) { return k == 1 || k == 2 || k == 3 || k == 4 || k == 5 || k == 8 || k == 10; }
+
+template <class T>
+pes_status upload(T** dptr, const std::vector<T>& v) {
+  *dptr = nullptr;
+  if (v.empty()) return PES_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), v.size() * sizeof(T));
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(PES_ENOMEM, "device tables") : cuda_fail(e, "cudaMalloc");
+  e = cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return PES_OK;
+}
+
+// One list of convolution jobs with its completion flags.
+struct JobList {
+  pes::ConvJob* jobs = nullptr;
+  int32_t* flags = nullptr;
+  int32_t n = 0;
+  int32_t grid = 0;
+};
+
+struct AddTable {
+  pes::AddOut* outs = nullptr;
+  int64_t* item_ptr = nullptr;
+  int32_t* contrib = nullptr;
+  int32_t nouts = 0;
+  int64_t items = 0;
+};
+
+struct CopyTable {
+  pes::CopyRow* rows = nullptr;
+  int32_t n = 0;
+};
+
+// Device state shared by single plans and batches.
+struct Exec {
+  int32_t k = 0, arith = 0, threads = 128, ctas_per_sm = 0;
+  int32_t smax = 0, dmax = 0;
+  size_t smem = 0;
+  int32_t blocks_per_sm = 0, nsm = 0;
+  long long timeout_ns = 0;
+  pes::InstInfo* inst = nullptr;
+  pes::Ctrl* ctrl = nullptr;
+  double* ws = nullptr;
+  size_t ws_doubles = 0;
+  std::vector<void*> owned;
+
+  ~Exec() {
+    for (void* p : owned) cudaFree(p);
+    cudaFree(inst);
+    cudaFree(ctrl);
+    cudaFree(ws);
+  }
+
+  template <class T>
+  pes_status put(T** dptr, const std::vector<T>& v) {
+    pes_status s = upload(dptr, v);
+    if (s == PES_OK && *dptr) owned.push_back(*dptr);
+    return s;
+  }
+
+  pes_status make_joblist(JobList& L, const std::vector<pes::ConvJob>& jobs) {
+    L.n = static_cast<int32_t>(jobs.size());
+    pes_status s = put(&L.jobs, jobs);
+    if (s != PES_OK) return s;
+    if (L.n > 0) {
+      cudaError_t e = cudaMalloc(&L.flags, sizeof(int32_t) * static_cast<size_t>(L.n));
+      if (e != cudaSuccess) return fail(PES_ENOMEM, "job flags");
+      owned.push_back(L.flags);
+      PES_CUDA(cudaMemset(L.flags, 0, sizeof(int32_t) * static_cast<size_t>(L.n)));
+    }
+    long long cap = static_cast<long long>(blocks_per_sm) * nsm;
+    L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(cap, L.n)));
+    return PES_OK;
+  }
+
+  pes_status make_add(AddTable& A, const std::vector<pes::AddOut>& outs, const std::vector<int32_t>& contrib,
+                      const std::vector<pes::InstInfo>& insts) {
+    A.nouts = static_cast<int32_t>(outs.size());
+    std::vector<int64_t> ip(outs.size() + 1, 0);
+    for (size_t o = 0; o < outs.size(); ++o) ip[o + 1] = ip[o] + insts[static_cast<size_t>(outs[o].inst)].d + 1;
+    A.items = ip.back();
+    pes_status s = put(&A.outs, outs);
+    if (s == PES_OK) s = put(&A.item_ptr, ip);
+    if (s == PES_OK) s = put(&A.contrib, contrib);
+    return s;
+  }
+
+  pes_status init(int32_t k_, const pes_options& o, const std::vector<pes::InstInfo>& insts, size_t ws_doubles_) {
+    k = k_;
+    arith = o.arith;
+    threads = o.threads;
+    ctas_per_sm = o.ctas_per_sm;
+    timeout_ns = (o.timeout_ms > 0 ? o.timeout_ms : 60000) * 1000000LL;
+    smax = 8;
+    dmax = 0;
+    for (const auto& in : insts) {
+      smax = std::max(smax, in.S);
+      dmax = std::max(dmax, in.d);
+    }
+    int dev = 0;
+    PES_CUDA(cudaGetDevice(&dev));
+    PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int optin = 0;
+    PES_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    smem = pes::dag_smem_bytes(k, arith, smax, dmax);
+    if (smem > static_cast<size_t>(optin))
+      return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(smem) +
+                                             " bytes of shared memory at k=" + std::to_string(k));
+    PES_CUDA(pes::dag_prepare(k, arith, smem));
+    PES_CUDA(pes::dag_occupancy(k, arith, threads, smem, &blocks_per_sm));
+    if (blocks_per_sm < 1) return fail(PES_EUNSUPPORTED_SIZE, "convolution kernel does not fit on an SM");
+    if (ctas_per_sm > 0) blocks_per_sm = std::min(blocks_per_sm, ctas_per_sm);
+    pes_status s = upload(&inst, insts);
+    if (s != PES_OK) return s;
+    cudaError_t e = cudaMalloc(&ctrl, sizeof(pes::Ctrl));
+    if (e != cudaSuccess) return fail(PES_ENOMEM, "control block");
+    PES_CUDA(cudaMemset(ctrl, 0, sizeof(pes::Ctrl)));
+    ws_doubles = std::max<size_t>(ws_doubles_, 8);
+    e = cudaMalloc(&ws, ws_doubles * sizeof(double));
+    if (e != cudaSuccess) return fail(PES_ENOMEM, "workspace of " + std::to_string(ws_doubles * 8) + " bytes");
+    PES_CUDA(cudaMemset(ws, 0, ws_doubles * sizeof(double)));
+    return PES_OK;
+  }
+
+  pes::DagArgs dag_args(const JobList& L, int counter) const {
+    pes::DagArgs a{};
+    a.jobs = L.jobs;
+    a.njobs = L.n;
+    a.counter = counter;
+    a.flags = L.flags;
+    a.inst = inst;
+    a.ws = ws;
+    a.ctrl = ctrl;
+    a.smax = smax;
+    a.dmax = dmax;
+    a.timeout_ns = timeout_ns;
+    return a;
+  }
+
+  cudaError_t run_dag(const JobList& L, int counter, cudaStream_t st) const {
+    if (L.n == 0) return cudaSuccess;
+    return pes::launch_dag(dag_args(L, counter), k, arith, threads, L.grid, st);
+  }
+
+  cudaError_t run_add(const AddTable& A, double* dst0, double* dst1, cudaStream_t st) const {
+    pes::AddArgs a{};
+    a.outs = A.outs;
+    a.nouts = A.nouts;
+    a.item_ptr = A.item_ptr;
+    a.contrib = A.contrib;
+    a.inst = inst;
+    a.ws = ws;
+    a.dst[0] = dst0;
+    a.dst[1] = dst1;
+    return pes::launch_add(a, k, A.items, st);
+  }
+
+  cudaError_t run_pack(const CopyTable& C, const double* s0, const double* s1, const double* s2,
+                       cudaStream_t st) const {
+    pes::CopyArgs a{};
+    a.rows = C.rows;
+    a.nrows = C.n;
+    a.inst = inst;
+    a.ws = ws;
+    a.src[0] = s0;
+    a.src[1] = s1;
+    a.src[2] = s2;
+    return pes::launch_pack(a, k, st);
+  }
+
+  cudaError_t run_unpack(const CopyTable& C, double* d0, double* d1, cudaStream_t st) const {
+    pes::CopyArgs a{};
+    a.rows = C.rows;
+    a.nrows = C.n;
+    a.inst = inst;
+    a.ws = ws;
+    a.dst[0] = d0;
+    a.dst[1] = d1;
+    return pes::launch_unpack(a, k, st);
+  }
+
+  pes_status check(cudaStream_t st) {
+    PES_CUDA(cudaStreamSynchronize(st));
+    pes::Ctrl h{};
+    PES_CUDA(cudaMemcpy(&h, ctrl, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.status != 0) {
+      int32_t zero[3] = {h.epoch, 0, 0};
+      PES_CUDA(cudaMemcpy(ctrl, zero, sizeof(zero), cudaMemcpyHostToDevice));
+      g_last_error = "device wait gave up: job " + std::to_string(h.diag[1]) + " waiting on " +
+                     std::to_string(h.diag[0]);
+      return static_cast<pes_status>(h.status);
+    }
+    return PES_OK;
+  }
+};
+
+pes_status parse_options(const pes_options* opt, pes_options& o) {
+  pes_default_options(&o);
+  if (opt) o = *opt;
+  if (o.arith != PES_ARITH_FP64 && o.arith != PES_ARITH_INT) return fail(PES_EINVAL, "arith must be 0 or 1");
+  if (o.threads == 0) o.threads = 128;
+  if (o.threads != 128 && o.threads != 256) return fail(PES_EINVAL, "threads must be 128 or 256");
+  if (o.ctas_per_sm < 0) return fail(PES_EINVAL, "ctas_per_sm must be >= 0");
+  return PES_OK;
+}
+
+pes_status build_supports(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t n, pes::Supports& s) {
+  std::string msg = pes::validate(ptr, idx, N, n);
+  if (!msg.empty()) return fail(PES_EINVAL, msg);
+  s.N = N;
+  s.n = n;
+  if (N == 0) {
+    s.ptr.assign(1, 0);
+    s.idx.clear();
+  } else {
+    s.ptr.assign(ptr, ptr + (N + 1));
+    s.idx.assign(idx, idx + s.ptr.back());
+  }
+  return PES_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// single plans
+// ---------------------------------------------------------------------------
+
+struct pes_plan_s {
+  pes::Program1 prog;
+  Exec ex;
+  JobList fwd, vjp_fwd, vjp_m, vjp_corr;
+  AddTable add, add_g;
+  CopyTable pack, pack_u, unpack;
+  bool with_vjp = false;
+  int64_t ws_bytes = 0;
+};
+
+extern "C" void pes_default_options(pes_options* opt) {
+  if (!opt) return;
+  opt->arith = PES_ARITH_FP64;
+  opt->threads = 128;
+  opt->ctas_per_sm = 0;
+  opt->with_vjp = 1;
+  opt->timeout_ms = 60000;
+}
+
+extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
+                               int32_t k, pes_plan_t* out) {
+  return pes_plan_ex(supp_ptr, supp_idx, N, n, d, k, nullptr, out);
+}
+
+extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
+                                  int32_t k, const pes_options* opt, pes_plan_t* out) {
+  if (!out) return fail(PES_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
+  if (d < 0) return fail(PES_EINVAL, "d must be >= 0");
+  if (d > 1023) return fail(PES_EUNSUPPORTED_SIZE, "d must be <= 1023");
+  pes_options o;
+  pes_status s = parse_options(opt, o);
+  if (s != PES_OK) return s;
+  pes::Supports sup;
+  s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  if (s != PES_OK) return s;
+
+  std::unique_ptr<pes_plan_s> P(new (std::nothrow) pes_plan_s());
+  if (!P) return fail(PES_ENOMEM, "plan");
+  P->with_vjp = o.with_vjp != 0;
+  P->prog = pes::compile(sup, d, false, P->with_vjp);
+  const pes::Program1& G = P->prog;
+  const int32_t S = pes::series_stride(d);
+  const int32_t slots = P->with_vjp ? G.n_slots_vjp : G.n_slots;
+  std::vector<pes::InstInfo> insts{{0, static_cast<int64_t>(slots) * S, S, d}};
+  const size_t ws = static_cast<size_t>(k) * static_cast<size_t>(slots) * static_cast<size_t>(S);
+  s = P->ex.init(k, o, insts, ws);
+  if (s != PES_OK) return s;
+  P->ws_bytes = static_cast<int64_t>(P->ex.ws_doubles * sizeof(double));
+
+  // forward jobs
+  s = P->ex.make_joblist(P->fwd, G.jobs);
+  if (s != PES_OK) return s;
+
+  // pack rows: coefficients (buffer 0), inputs (buffer 1)
+  const int64_t D1 = d + 1;
+  std::vector<pes::CopyRow> rows;
+  for (int32_t m = 0; m <= N; ++m) rows.push_back({m * D1, (N + 1) * D1, 0, 0, m, 0});
+  for (int32_t i = 0; i < n; ++i) rows.push_back({i * D1, n * D1, 1, 0, 1 + N + i, 0});
+  P->pack.n = static_cast<int32_t>(rows.size());
+  s = P->ex.put(&P->pack.rows, rows);
+  if (s != PES_OK) return s;
+
+  // addition: value (buffer 0) and gradients (buffer 1)
+  std::vector<pes::AddOut> outs;
+  outs.push_back({0, D1, 0, 0, G.add_ptr[0], G.add_ptr[1]});
+  for (int32_t i = 0; i < n; ++i) outs.push_back({i * D1, n * D1, 1, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+  s = P->ex.make_add(P->add, outs, G.add_src, insts);
+  if (s != PES_OK) return s;
+
+  if (P->with_vjp) {
+    std::vector<pes::ConvJob> fwdm(G.vjp_jobs.begin(), G.vjp_jobs.begin() + G.vjp_fwd_jobs);
+    std::vector<pes::ConvJob> corr(G.vjp_jobs.begin() + G.vjp_fwd_jobs, G.vjp_jobs.end());
+    std::vector<pes::ConvJob> monly;
+    for (const auto& j : fwdm)
+      if (j.out >= G.slot_M0 && j.out < G.slot_g0) monly.push_back(pes::ConvJob{j.in1, j.in2, j.out, -1, -1, 0, j.kind, j.layer});
+    s = P->ex.make_joblist(P->vjp_fwd, fwdm);
+    if (s == PES_OK) s = P->ex.make_joblist(P->vjp_m, monly);
+    if (s == PES_OK) s = P->ex.make_joblist(P->vjp_corr, corr);
+    if (s != PES_OK) return s;
+    // gradient series into the workspace (buffer 0 = workspace itself)
+    std::vector<pes::AddOut> gouts;
+    const int64_t lsw = static_cast<int64_t>(slots) * S;
+    for (int32_t i = 0; i < n; ++i)
+      gouts.push_back({static_cast<int64_t>(G.slot_g0 + i) * S, lsw, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+    s = P->ex.make_add(P->add_g, gouts, G.add_src, insts);
+    if (s != PES_OK) return s;
+    std::vector<pes::CopyRow> urow{{0, D1, 2, 0, G.slot_u, 0}};
+    P->pack_u.n = 1;
+    s = P->ex.put(&P->pack_u.rows, urow);
+    if (s != PES_OK) return s;
+    // unpack: grad_coeff (buffer 0) <- u, r_m ; grad_input (buffer 1) <- r_{N+i}
+    std::vector<pes::CopyRow> un;
+    un.push_back({0, (N + 1) * D1, 0, 0, G.slot_u, 0});
+    for (int32_t m = 1; m <= N; ++m) un.push_back({m * D1, (N + 1) * D1, 0, 0, G.slot_r0 + m - 1, 0});
+    for (int32_t i = 0; i < n; ++i) un.push_back({i * D1, n * D1, 1, 0, G.slot_r0 + N + i, 0});
+    P->unpack.n = static_cast<int32_t>(un.size());
+    s = P->ex.put(&P->unpack.rows, un);
+    if (s != PES_OK) return s;
+  }
+  *out = P.release();
+  return PES_OK;
+}
+
+extern "C" void pes_plan_destroy(pes_plan_t plan) { delete plan; }
+
+extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const double* input, double* value,
+                                    double* grad, void* stream) {
+  if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  if (!coeff || !input || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Exec& E = plan->ex;
+  PES_CUDA(pes::launch_prologue(E.ctrl, st));
+  PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
+  PES_CUDA(E.run_dag(plan->fwd, 0, st));
+  PES_CUDA(E.run_add(plan->add, value, grad, st));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double* input, const double* upstream,
+                              double* grad_input, double* grad_coeff, int32_t reuse_forward, void* stream) {
+  if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  if (!plan->with_vjp) return fail(PES_EINVAL, "plan was built without with_vjp");
+  if (!upstream || !grad_input || !grad_coeff || (!reuse_forward && (!coeff || !input)))
+    return fail(PES_EINVAL, "NULL buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Exec& E = plan->ex;
+  PES_CUDA(pes::launch_prologue(E.ctrl, st));
+  if (reuse_forward) {
+    PES_CUDA(E.run_pack(plan->pack_u, nullptr, nullptr, upstream, st));
+    PES_CUDA(E.run_dag(plan->vjp_m, 0, st));
+  } else {
+    PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
+    PES_CUDA(E.run_pack(plan->pack_u, nullptr, nullptr, upstream, st));
+    PES_CUDA(E.run_dag(plan->vjp_fwd, 0, st));
+  }
+  PES_CUDA(E.run_add(plan->add_g, E.ws, nullptr, st));
+  PES_CUDA(E.run_dag(plan->vjp_corr, 1, st));
+  PES_CUDA(E.run_unpack(plan->unpack, grad_coeff, grad_input, st));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_workspace_io(pes_plan_t plan, void* buffer, int32_t to_buffer, void* stream) {
+  if (!plan || !buffer) return fail(PES_EINVAL, "NULL argument");
+  const size_t bytes = plan->ex.ws_doubles * sizeof(double);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (to_buffer)
+    PES_CUDA(cudaMemcpyAsync(buffer, plan->ex.ws, bytes, cudaMemcpyDeviceToDevice, st));
+  else
+    PES_CUDA(cudaMemcpyAsync(plan->ex.ws, buffer, bytes, cudaMemcpyDeviceToDevice, st));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_check(pes_plan_t plan, void* stream) {
+  if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  return plan->ex.check(static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
+  if (!plan || !info) return fail(PES_EINVAL, "NULL argument");
+  const pes::Program1& G = plan->prog;
+  std::memset(info, 0, sizeof(*info));
+  info->conv_jobs = static_cast<int64_t>(G.jobs.size());
+  info->layers = G.n_layers;
+  info->add_terms = static_cast<int64_t>(G.add_src.size());
+  int64_t nonempty = 0;
+  for (size_t o = 0; o + 1 < G.add_ptr.size(); ++o) nonempty += G.add_ptr[o + 1] > G.add_ptr[o];
+  info->add_jobs = info->add_terms - nonempty;
+  info->workspace_bytes = plan->ws_bytes;
+  info->vjp_conv_jobs = plan->with_vjp ? G.vjp_fwd_jobs - static_cast<int64_t>(G.jobs.size()) : 0;
+  info->vjp_corr_jobs = plan->with_vjp ? static_cast<int64_t>(G.vjp_jobs.size()) - G.vjp_fwd_jobs : 0;
+  info->digits = pes::digits_of_k(plan->ex.k);
+  info->grid = plan->fwd.grid;
+  info->threads = plan->ex.threads;
+  info->smem_bytes = static_cast<int32_t>(plan->ex.smem);
+  return PES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+struct pes_batch_s {
+  Exec ex;
+  JobList fwd;
+  AddTable add;
+  CopyTable pack;
+  int32_t count = 0;
+  std::vector<int64_t> coeff_off, input_off, value_off, grad_off;
+  int64_t conv_jobs = 0, layers = 0, add_terms = 0, add_jobs = 0;
+  // CUDA graph of one call, re-instantiated when the caller's buffers change
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
+  ~pes_batch_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+  }
+};
+
+extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int32_t* N, const int32_t* d,
+                                     const int32_t* supp_ptr, const int32_t* supp_idx, int32_t k,
+                                     const pes_options* opt, pes_batch_t* out) {
+  if (!out) return fail(PES_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !n || !N || !d || !supp_ptr) return fail(PES_EINVAL, "bad batch arguments");
+  if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
+  pes_options o;
+  pes_status s = parse_options(opt, o);
+  if (s != PES_OK) return s;
+  std::unique_ptr<pes_batch_s> B(new (std::nothrow) pes_batch_s());
+  if (!B) return fail(PES_ENOMEM, "batch");
+  B->count = count;
+
+  std::vector<pes::Program1> progs(static_cast<size_t>(count));
+  std::vector<pes::InstInfo> insts(static_cast<size_t>(count));
+  B->coeff_off.assign(static_cast<size_t>(count) + 1, 0);
+  B->input_off.assign(static_cast<size_t>(count) + 1, 0);
+  B->value_off.assign(static_cast<size_t>(count) + 1, 0);
+  B->grad_off.assign(static_cast<size_t>(count) + 1, 0);
+  int64_t prow = 0, qidx = 0, wsbase = 0;
+  for (int32_t b = 0; b < count; ++b) {
+    if (d[b] < 0 || d[b] > 1023) return fail(PES_EINVAL, "instance " + std::to_string(b) + ": bad degree");
+    pes::Supports sup;
+    const int32_t* bp = supp_ptr + prow;
+    const int32_t* bi = supp_idx ? supp_idx + qidx : nullptr;
+    s = build_supports(bp, bi, N[b], n[b], sup);
+    if (s != PES_OK) return fail(s, "instance " + std::to_string(b) + ": " + g_last_error);
+    progs[static_cast<size_t>(b)] = pes::compile(sup, d[b], false, false);
+    const int32_t S = pes::series_stride(d[b]);
+    const int64_t slots = progs[static_cast<size_t>(b)].n_slots;
+    insts[static_cast<size_t>(b)] = pes::InstInfo{wsbase, slots * S, S, d[b]};
+    wsbase += static_cast<int64_t>(k) * slots * S;
+    const int64_t D1 = d[b] + 1;
+    B->coeff_off[static_cast<size_t>(b) + 1] = B->coeff_off[static_cast<size_t>(b)] + k * (N[b] + 1) * D1;
+    B->input_off[static_cast<size_t>(b) + 1] = B->input_off[static_cast<size_t>(b)] + k * n[b] * D1;
+    B->value_off[static_cast<size_t>(b) + 1] = B->value_off[static_cast<size_t>(b)] + k * D1;
+    B->grad_off[static_cast<size_t>(b) + 1] = B->grad_off[static_cast<size_t>(b)] + k * n[b] * D1;
+    prow += N[b] + 1;
+    qidx += sup.ptr.back();
+  }
+  s = B->ex.init(k, o, insts, static_cast<size_t>(wsbase));
+  if (s != PES_OK) return s;
+
+  // concatenate: all jobs sorted by layer, larger degree first inside a layer
+  struct Ref {
+    int32_t layer, d, inst, local;
+  };
+  std::vector<Ref> refs;
+  for (int32_t b = 0; b < count; ++b)
+    for (size_t t = 0; t < progs[static_cast<size_t>(b)].jobs.size(); ++t)
+      refs.push_back({progs[static_cast<size_t>(b)].jobs[t].layer, d[b], b, static_cast<int32_t>(t)});
+  std::stable_sort(refs.begin(), refs.end(), [](const Ref& a, const Ref& b) {
+    if (a.layer != b.layer) return a.layer < b.layer;
+    return a.d > b.d;
+  });
+  std::vector<std::vector<int32_t>> gidx(static_cast<size_t>(count));
+  for (int32_t b = 0; b < count; ++b) gidx[static_cast<size_t>(b)].assign(progs[static_cast<size_t>(b)].jobs.size(), -1);
+  for (size_t g = 0; g < refs.size(); ++g) gidx[static_cast<size_t>(refs[g].inst)][static_cast<size_t>(refs[g].local)] = static_cast<int32_t>(g);
+  std::vector<pes::ConvJob> jobs(refs.size());
+  for (size_t g = 0; g < refs.size(); ++g) {
+    const auto& gi = gidx[static_cast<size_t>(refs[g].inst)];
+    pes::ConvJob j = progs[static_cast<size_t>(refs[g].inst)].jobs[static_cast<size_t>(refs[g].local)];
+    j.dep1 = j.dep1 >= 0 ? gi[static_cast<size_t>(j.dep1)] : -1;
+    j.dep2 = j.dep2 >= 0 ? gi[static_cast<size_t>(j.dep2)] : -1;
+    j.inst = refs[g].inst;
+    jobs[g] = j;
+    B->layers = std::max<int64_t>(B->layers, j.layer);
+  }
+  B->conv_jobs = static_cast<int64_t>(jobs.size());
+  s = B->ex.make_joblist(B->fwd, jobs);
+  if (s != PES_OK) return s;
+
+  std::vector<pes::CopyRow> rows;
+  std::vector<pes::AddOut> outs;
+  std::vector<int32_t> contrib;
+  for (int32_t b = 0; b < count; ++b) {
+    const pes::Program1& G = progs[static_cast<size_t>(b)];
+    const int64_t D1 = d[b] + 1;
+    const int64_t co = B->coeff_off[static_cast<size_t>(b)], io = B->input_off[static_cast<size_t>(b)];
+    for (int32_t m = 0; m <= N[b]; ++m) rows.push_back({co + m * D1, (N[b] + 1) * D1, 0, b, m, 0});
+    for (int32_t i = 0; i < n[b]; ++i) rows.push_back({io + i * D1, n[b] * D1, 1, b, 1 + N[b] + i, 0});
+    const int32_t c0 = static_cast<int32_t>(contrib.size());
+    contrib.insert(contrib.end(), G.add_src.begin(), G.add_src.end());
+    outs.push_back({B->value_off[static_cast<size_t>(b)], D1, 0, b, c0 + G.add_ptr[0], c0 + G.add_ptr[1]});
+    for (int32_t i = 0; i < n[b]; ++i)
+      outs.push_back({B->grad_off[static_cast<size_t>(b)] + i * D1, n[b] * D1, 1, b, c0 + G.add_ptr[1 + i],
+                      c0 + G.add_ptr[2 + i]});
+    B->add_terms += static_cast<int64_t>(G.add_src.size());
+    for (size_t oo = 0; oo + 1 < G.add_ptr.size(); ++oo)
+      B->add_jobs += std::max(0, G.add_ptr[oo + 1] - G.add_ptr[oo] - 1);
+  }
+  B->pack.n = static_cast<int32_t>(rows.size());
+  s = B->ex.put(&B->pack.rows, rows);
+  if (s == PES_OK) s = B->ex.make_add(B->add, outs, contrib, insts);
+  if (s != PES_OK) return s;
+  PES_CUDA(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
+  *out = B.release();
+  return PES_OK;
+}
+
+extern "C" void pes_batch_destroy(pes_batch_t batch) { delete batch; }
+
+extern "C" pes_status pes_batch_offsets(pes_batch_t batch, int64_t* coeff_off, int64_t* input_off,
+                                        int64_t* value_off, int64_t* grad_off) {
+  if (!batch) return fail(PES_EINVAL, "batch is NULL");
+  const size_t n = batch->coeff_off.size();
+  if (coeff_off) std::memcpy(coeff_off, batch->coeff_off.data(), n * sizeof(int64_t));
+  if (input_off) std::memcpy(input_off, batch->input_off.data(), n * sizeof(int64_t));
+  if (value_off) std::memcpy(value_off, batch->value_off.data(), n * sizeof(int64_t));
+  if (grad_off) std::memcpy(grad_off, batch->grad_off.data(), n * sizeof(int64_t));
+  return PES_OK;
+}
+
+static pes_status batch_record(pes_batch_t B, const double* coeff, const double* input, double* value,
+                               double* grad, cudaStream_t st) {
+  Exec& E = B->ex;
+  PES_CUDA(pes::launch_prologue(E.ctrl, st));
+  PES_CUDA(E.run_pack(B->pack, coeff, input, nullptr, st));
+  PES_CUDA(E.run_dag(B->fwd, 0, st));
+  PES_CUDA(E.run_add(B->add, value, grad, st));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff, const double* input, double* value,
+                                          double* grad, void* stream) {
+  if (!batch) return fail(PES_EINVAL, "batch is NULL");
+  if (!coeff || !input || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void* key[4] = {coeff, input, value, grad};
+  if (!batch->gexec || std::memcmp(key, batch->gkey, sizeof(key)) != 0) {
+    if (batch->gexec) {
+      cudaGraphExecDestroy(batch->gexec);
+      batch->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    PES_CUDA(cudaStreamBeginCapture(batch->capture_stream, cudaStreamCaptureModeThreadLocal));
+    pes_status s = batch_record(batch, coeff, input, value, grad, batch->capture_stream);
+    cudaError_t e = cudaStreamEndCapture(batch->capture_stream, &graph);
+    if (s != PES_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&batch->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    std::memcpy(batch->gkey, key, sizeof(key));
+  }
+  PES_CUDA(cudaGraphLaunch(batch->gexec, st));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_batch_check(pes_batch_t batch, void* stream) {
+  if (!batch) return fail(PES_EINVAL, "batch is NULL");
+  return batch->ex.check(static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info) {
+  if (!batch || !info) return fail(PES_EINVAL, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->conv_jobs = batch->conv_jobs;
+  info->layers = batch->layers;
+  info->add_terms = batch->add_terms;
+  info->add_jobs = batch->add_jobs;
+  info->workspace_bytes = static_cast<int64_t>(batch->ex.ws_doubles * sizeof(double));
+  info->digits = pes::digits_of_k(batch->ex.k);
+  info->grid = batch->fwd.grid;
+  info->threads = batch->ex.threads;
+  info->smem_bytes = static_cast<int32_t>(batch->ex.smem);
+  return PES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// multiple double numbers, costs, FP64 peak
+// ---------------------------------------------------------------------------
+
+extern "C" pes_status pes_md_binary(int32_t op, int32_t k, const double* x, const double* y, double* out,
+                                    int64_t count, void* stream) {
+  if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
+  if (op != 0 && op != 1) return fail(PES_EINVAL, "op must be 0 (add) or 1 (mul)");
+  if (count < 0 || (count > 0 && (!x || !y || !out))) return fail(PES_EINVAL, "bad buffers");
+  PES_CUDA(pes::launch_md_binary(op, k, x, y, out, count, static_cast<cudaStream_t>(stream)));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_md_costs(int32_t k, double* mul_ops, double* add_ops) {
+  if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
+  double mul, add;
+  if (k == 10) {
+    mul = 3089.0;  // Sec. 6.2: 952 additions, 1743 subtractions, 394 multiplications
+    add = 397.0;   // Sec. 6.2: 139 additions, 258 subtractions
+  } else if (k == 1) {
+    mul = 1.0;
+    add = 1.0;
+  } else {
+    // FP64 operations of md.cuh: md_mul = TwoProd (2) for orders <= k-2, each
+    // deposit at order s costs 6 (k - s) + 1, then renorm<k+1,k> (9 k);
+    // md_add = renorm<2k,k> (9 (2k - 1)).
+    double m = 0.0;
+    for (int s = 0; s < k; ++s)
+      for (int p = 0; p <= s; ++p) {
+        if (s < k - 1)
+          m += 2.0 + (6.0 * (k - s) + 1.0) + (6.0 * (k - s - 1) + 1.0);
+        else
+          m += 1.0 + (6.0 * (k - s) + 1.0);
+      }
+    mul = m + 9.0 * k;
+    add = 9.0 * (2 * k - 1);
+  }
+  if (mul_ops) *mul_ops = mul;
+  if (add_ops) *add_ops = add;
+  return PES_OK;
+}
+
+extern "C" pes_status pes_fp64_peak(int32_t repeats, double* tflops) {
+  if (!tflops) return fail(PES_EINVAL, "tflops is NULL");
+  int dev = 0, nsm = 0;
+  PES_CUDA(cudaGetDevice(&dev));
+  PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  const int threads = 256, blocks = nsm * 4, iters = 4096;
+  PES_CUDA(cudaMalloc(&sink, sizeof(double) * static_cast<size_t>(blocks)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  pes::launch_fp64_peak(sink, blocks, threads, iters / 8, nullptr);  // warm-up
+  for (int r = 0; r < std::max(1, repeats); ++r) {
+    cudaEventRecord(e0, nullptr);
+    pes::launch_fp64_peak(sink, blocks, threads, iters, nullptr);
+    cudaEventRecord(e1, nullptr);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 peak kernel");
+  const double fmas = static_cast<double>(blocks) * threads * iters * 8.0;
+  *tflops = 2.0 * fmas / (static_cast<double>(best) * 1e-3) / 1e12;
+  return PES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// job compiler introspection
+// ---------------------------------------------------------------------------
+
+extern "C" pes_status pes_jobc_stats(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                                     int32_t paper_layout, int64_t* stats, int32_t* layer_sizes, int32_t cap) {
+  pes::Supports sup;
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  if (s != PES_OK) return s;
+  pes::Program1 G = pes::compile(sup, 0, paper_layout != 0, paper_layout == 0);
+  std::vector<int64_t> lv = pes::paper_add_levels(sup);
+  if (stats) {
+    int64_t paper_adds = 0;
+    for (int64_t v : lv) paper_adds += v;
+    stats[0] = static_cast<int64_t>(G.jobs.size());
+    stats[1] = G.n_layers;
+    stats[2] = static_cast<int64_t>(G.add_src.size());
+    stats[3] = paper_adds;
+    stats[4] = G.n_slots;
+    stats[5] = static_cast<int64_t>(lv.size());
+    stats[6] = paper_layout ? 0 : G.vjp_fwd_jobs - static_cast<int64_t>(G.jobs.size());
+    stats[7] = paper_layout ? 0 : static_cast<int64_t>(G.vjp_jobs.size()) - G.vjp_fwd_jobs;
+  }
+  if (layer_sizes)
+    for (int32_t L = 1; L <= G.n_layers && L <= cap; ++L)
+      layer_sizes[L - 1] = G.layer_ptr[static_cast<size_t>(L)] - G.layer_ptr[static_cast<size_t>(L) - 1];
+  return PES_OK;
+}
+
+extern "C" pes_status pes_jobc_jobs(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                                    int32_t paper_layout, int32_t* jobs, int64_t cap) {
+  pes::Supports sup;
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  if (s != PES_OK) return s;
+  pes::Program1 G = pes::compile(sup, 0, paper_layout != 0, false);
+  for (size_t t = 0; t < G.jobs.size() && static_cast<int64_t>(t) < cap; ++t) {
+    jobs[4 * t + 0] = G.jobs[t].in1;
+    jobs[4 * t + 1] = G.jobs[t].in2;
+    jobs[4 * t + 2] = G.jobs[t].out;
+    jobs[4 * t + 3] = G.jobs[t].layer;
+  }
+  return PES_OK;
+}
+
+extern "C" pes_status pes_jobc_add_levels(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                                          int64_t* levels, int32_t cap, int32_t* nlevels) {
+  pes::Supports sup;
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  if (s != PES_OK) return s;
+  std::vector<int64_t> lv = pes::paper_add_levels(sup);
+  if (nlevels) *nlevels = static_cast<int32_t>(lv.size());
+  for (size_t t = 0; t < lv.size() && static_cast<int32_t>(t) < cap; ++t) levels[t] = lv[t];
+  return PES_OK;
+}
+
+extern "C" pes_status pes_jobc_add_terms(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
+                                         int32_t* add_ptr, int32_t* add_src, int64_t cap) {
+  pes::Supports sup;
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  if (s != PES_OK) return s;
+  pes::Program1 G = pes::compile(sup, 0, false, false);
+  if (add_ptr) std::memcpy(add_ptr, G.add_ptr.data(), G.add_ptr.size() * sizeof(int32_t));
+  if (add_src)
+    for (size_t t = 0; t < G.add_src.size() && static_cast<int64_t>(t) < cap; ++t) add_src[t] = G.add_src[t];
+  return PES_OK;
+}
+
+extern "C" pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status) {
+  if (timeout_ms <= 0 || timeout_ms > 60000) return fail(PES_EINVAL, "timeout_ms must be in (0, 60000]");
+  // one monomial x_0 of degree 0: a single job, made to wait on its own flag
+  const int32_t ptr[2] = {0, 1}, idx[1] = {0};
+  pes_options o;
+  pes_default_options(&o);
+  o.with_vjp = 0;
+  o.timeout_ms = timeout_ms;
+  pes_plan_t P = nullptr;
+  pes_status s = pes_plan_ex(ptr, idx, 1, 1, 0, 1, &o, &P);
+  if (s != PES_OK) return s;
+  std::unique_ptr<pes_plan_s> guard(P);
+  std::vector<pes::ConvJob> jobs = P->prog.jobs;
+  jobs[0].dep1 = 0;  // the job waits for itself: the flag is never set
+  JobList L;
+  s = P->ex.make_joblist(L, jobs);
+  if (s != PES_OK) return s;
+  PES_CUDA(pes::launch_prologue(P->ex.ctrl, nullptr));
+  PES_CUDA(P->ex.run_dag(L, 0, nullptr));
+  pes_status st = P->ex.check(nullptr);
+  if (device_status) *device_status = static_cast<int32_t>(st);
+  return st == PES_ETIMEOUT ? PES_OK : fail(PES_EINTERNAL, "the wait did not report a timeout");
+}
+
+extern "C" const char* pes_status_string(pes_status s) {
+  switch (s) {
+    case PES_OK: return "PES_OK";
+    case PES_EINVAL: return "PES_EINVAL: invalid argument";
+    case PES_EUNSUPPORTED_K: return "PES_EUNSUPPORTED_K: k must be 1,2,3,4,5,8 or 10";
+    case PES_ENOMEM: return "PES_ENOMEM: allocation failed";
+    case PES_ECUDA: return "PES_ECUDA: CUDA runtime error";
+    case PES_ETIMEOUT: return "PES_ETIMEOUT: a device-side wait gave up";
+    case PES_EINTERNAL: return "PES_EINTERNAL: internal error";
+    case PES_EUNSUPPORTED_SIZE: return "PES_EUNSUPPORTED_SIZE: degree too large";
+    default: return "unknown pes_status";
+  }
+}
+
+extern "C" const char* pes_last_error(void) { return g_last_error.c_str(); }

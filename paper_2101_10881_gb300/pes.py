@@ -1,0 +1,355 @@
+"""Thin Python binding of libpes (include/pes.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch is
+used for device memory and streams.  The library is loaded on first use and a
+missing library raises immediately: there is no CPU path.
+
+Tensors are float64, contiguous, on the current CUDA device, in the library's
+limb-major layout: coefficient series (k, N+1, d+1) with index 0 the constant
+term, input series (k, n, d+1), value (k, d+1), gradient (k, n, d+1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpes.so")
+
+PES_OK = 0
+STATUS = {0: "PES_OK", 1: "PES_EINVAL", 2: "PES_EUNSUPPORTED_K", 3: "PES_ENOMEM", 4: "PES_ECUDA",
+          5: "PES_ETIMEOUT", 6: "PES_EINTERNAL", 7: "PES_EUNSUPPORTED_SIZE"}
+ARITH = {"fp64": 0, "int": 1}
+
+# every symbol that include/pes.h declares
+EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_destroy", "pes_eval_grad", "pes_vjp",
+           "pes_workspace_io", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
+           "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
+           "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_jobc_stats", "pes_jobc_jobs",
+           "pes_jobc_add_levels", "pes_jobc_add_terms", "pes_selftest_timeout", "pes_status_string",
+           "pes_last_error")
+
+
+class PesError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} {msg}".strip())
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("arith", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("with_vjp", ctypes.c_int32), ("timeout_ms", ctypes.c_int64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("conv_jobs", ctypes.c_int64), ("layers", ctypes.c_int64), ("add_terms", ctypes.c_int64),
+                ("add_jobs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("vjp_conv_jobs", ctypes.c_int64), ("vjp_corr_jobs", ctypes.c_int64),
+                ("digits", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import build as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """The loaded libpes (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpes.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+            ip32 = ctypes.POINTER(ctypes.c_int32)
+            ip64 = ctypes.POINTER(ctypes.c_int64)
+            dp = ctypes.POINTER(ctypes.c_double)
+            sig = {
+                "pes_default_options": (None, [ctypes.POINTER(Options)]),
+                "pes_plan_ex": (i32, [ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
+                "pes_plan_destroy": (None, [vp]),
+                "pes_eval_grad": (i32, [vp, vp, vp, vp, vp, vp]),
+                "pes_vjp": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
+                "pes_workspace_io": (i32, [vp, vp, i32, vp]),
+                "pes_check": (i32, [vp, vp]),
+                "pes_get_plan_info": (i32, [vp, ctypes.POINTER(PlanInfo)]),
+                "pes_plan_batch": (i32, [i32, ip32, ip32, ip32, ip32, ip32, i32, ctypes.POINTER(Options),
+                                         ctypes.POINTER(vp)]),
+                "pes_batch_destroy": (None, [vp]),
+                "pes_batch_offsets": (i32, [vp, ip64, ip64, ip64, ip64]),
+                "pes_eval_grad_batch": (i32, [vp, vp, vp, vp, vp, vp]),
+                "pes_batch_check": (i32, [vp, vp]),
+                "pes_get_batch_info": (i32, [vp, ctypes.POINTER(PlanInfo)]),
+                "pes_md_binary": (i32, [i32, i32, vp, vp, vp, i64, vp]),
+                "pes_md_costs": (i32, [i32, dp, dp]),
+                "pes_fp64_peak": (i32, [i32, dp]),
+                "pes_jobc_stats": (i32, [ip32, ip32, i32, i32, i32, ip64, ip32, i32]),
+                "pes_jobc_jobs": (i32, [ip32, ip32, i32, i32, i32, ip32, i64]),
+                "pes_jobc_add_levels": (i32, [ip32, ip32, i32, i32, ip64, i32, ip32]),
+                "pes_jobc_add_terms": (i32, [ip32, ip32, i32, i32, ip32, ip32, i64]),
+                "pes_selftest_timeout": (i32, [i64, ip32]),
+                "pes_status_string": (ctypes.c_char_p, [i32]),
+                "pes_last_error": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != PES_OK:
+        msg = lib().pes_last_error().decode(errors="replace")
+        raise PesError(rc, where, msg)
+
+
+def csr(supports):
+    ptr = np.zeros(len(supports) + 1, dtype=np.int32)
+    idx = []
+    for m, s in enumerate(supports):
+        idx.extend(int(v) for v in s)
+        ptr[m + 1] = len(idx)
+    return ptr, np.asarray(idx if idx else [0], dtype=np.int32)
+
+
+def _ip32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_options(arith="fp64", threads=128, ctas_per_sm=0, with_vjp=True, timeout_ms=60000):
+    o = Options()
+    lib().pes_default_options(ctypes.byref(o))
+    o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
+    o.threads = int(threads)
+    o.ctas_per_sm = int(ctas_per_sm)
+    o.with_vjp = int(bool(with_vjp))
+    o.timeout_ms = int(timeout_ms)
+    return o
+
+
+class Plan:
+    """pes_plan: job tables and workspace of one polynomial on the current device."""
+
+    def __init__(self, supports, n, d, k, **opts):
+        self.supports = [list(s) for s in supports]
+        self.n, self.d, self.k = int(n), int(d), int(k)
+        self.N = len(self.supports)
+        ptr, idx = csr(self.supports)
+        o = make_options(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().pes_plan_ex(_ip32(ptr), _ip32(idx), self.N, self.n, self.d, self.k, ctypes.byref(o),
+                                 ctypes.byref(h)), "pes_plan")
+        self._h = h
+        self.generation = 0  # bumped by every call that overwrites the workspace
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pes_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shapes(self):
+        k, N, n, S = self.k, self.N, self.n, self.d + 1
+        return {"coeff": (k, N + 1, S), "input": (k, n, S), "value": (k, S), "grad": (k, n, S)}
+
+    def eval_grad(self, coeff, inputs, value=None, grad=None, stream=None):
+        import torch
+        sh = self.shapes()
+        if value is None:
+            value = torch.empty(sh["value"], dtype=torch.float64, device=coeff.device)
+        if grad is None:
+            grad = torch.empty(sh["grad"], dtype=torch.float64, device=coeff.device)
+        _check(lib().pes_eval_grad(self._h, _ptr(coeff, sh["coeff"], "coeff"), _ptr(inputs, sh["input"], "input"),
+                                   _ptr(value, sh["value"], "value"), _ptr(grad, sh["grad"], "grad"),
+                                   _stream(stream)), "pes_eval_grad")
+        self.generation += 1
+        return value, grad
+
+    def vjp(self, coeff, inputs, upstream, reuse_forward=False, grad_input=None, grad_coeff=None, stream=None):
+        import torch
+        sh = self.shapes()
+        dev = upstream.device
+        if grad_input is None:
+            grad_input = torch.empty(sh["input"], dtype=torch.float64, device=dev)
+        if grad_coeff is None:
+            grad_coeff = torch.empty(sh["coeff"], dtype=torch.float64, device=dev)
+        cp = _ptr(coeff, sh["coeff"], "coeff") if coeff is not None else ctypes.c_void_p(0)
+        ip = _ptr(inputs, sh["input"], "input") if inputs is not None else ctypes.c_void_p(0)
+        _check(lib().pes_vjp(self._h, cp, ip, _ptr(upstream, sh["value"], "upstream"),
+                             _ptr(grad_input, sh["input"], "grad_input"),
+                             _ptr(grad_coeff, sh["coeff"], "grad_coeff"), int(bool(reuse_forward)),
+                             _stream(stream)), "pes_vjp")
+        self.generation += 1
+        return grad_input, grad_coeff
+
+    def workspace_io(self, buffer, to_buffer, stream=None):
+        _check(lib().pes_workspace_io(self._h, ctypes.c_void_p(buffer.data_ptr()), int(bool(to_buffer)),
+                                      _stream(stream)), "pes_workspace_io")
+
+    def check(self, stream=None):
+        _check(lib().pes_check(self._h, _stream(stream)), "pes_check")
+
+    def info(self):
+        pi = PlanInfo()
+        _check(lib().pes_get_plan_info(self._h, ctypes.byref(pi)), "pes_get_plan_info")
+        return pi.as_dict()
+
+
+class Batch:
+    """pes_plan_batch: many polynomials evaluated by one graph-captured launch."""
+
+    def __init__(self, instances, k, **opts):
+        """instances: list of (supports, n, d)."""
+        self.k = int(k)
+        self.count = len(instances)
+        n = np.array([int(t[1]) for t in instances], dtype=np.int32)
+        d = np.array([int(t[2]) for t in instances], dtype=np.int32)
+        N = np.array([len(t[0]) for t in instances], dtype=np.int32)
+        ptrs, idxs = [], []
+        for supp, _, _ in instances:
+            p, i = csr(supp)
+            ptrs.append(p)
+            idxs.append(i[: p[-1]])
+        ptr = np.concatenate(ptrs).astype(np.int32)
+        idx = np.concatenate(idxs).astype(np.int32) if sum(len(x) for x in idxs) else np.zeros(1, np.int32)
+        o = make_options(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().pes_plan_batch(self.count, _ip32(n), _ip32(N), _ip32(d), _ip32(ptr), _ip32(idx), self.k,
+                                    ctypes.byref(o), ctypes.byref(h)), "pes_plan_batch")
+        self._h = h
+        self.n, self.N, self.d = n, N, d
+        offs = [np.zeros(self.count + 1, dtype=np.int64) for _ in range(4)]
+        p64 = [o_.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) for o_ in offs]
+        _check(lib().pes_batch_offsets(self._h, *p64), "pes_batch_offsets")
+        self.coeff_off, self.input_off, self.value_off, self.grad_off = offs
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.pes_batch_destroy(h)
+            self._h = None
+
+    def lengths(self):
+        return {"coeff": int(self.coeff_off[-1]), "input": int(self.input_off[-1]),
+                "value": int(self.value_off[-1]), "grad": int(self.grad_off[-1])}
+
+    def eval_grad(self, coeff, inputs, value, grad, stream=None):
+        ln = self.lengths()
+        _check(lib().pes_eval_grad_batch(self._h, _ptr(coeff, (ln["coeff"],), "coeff"),
+                                         _ptr(inputs, (ln["input"],), "input"),
+                                         _ptr(value, (ln["value"],), "value"), _ptr(grad, (ln["grad"],), "grad"),
+                                         _stream(stream)), "pes_eval_grad_batch")
+        return value, grad
+
+    def check(self, stream=None):
+        _check(lib().pes_batch_check(self._h, _stream(stream)), "pes_batch_check")
+
+    def info(self):
+        pi = PlanInfo()
+        _check(lib().pes_get_batch_info(self._h, ctypes.byref(pi)), "pes_get_batch_info")
+        return pi.as_dict()
+
+
+def md_binary(op, x, y, out=None, stream=None):
+    """Elementwise k-double add (op 'add') or mul (op 'mul') of (k, count) tensors."""
+    import torch
+    k, count = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().pes_md_binary({"add": 0, "mul": 1}[op], k, _ptr(x, (k, count), "x"), _ptr(y, (k, count), "y"),
+                               _ptr(out, (k, count), "out"), count, _stream(stream)), "pes_md_binary")
+    return out
+
+
+def md_costs(k):
+    m, a = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pes_md_costs(int(k), ctypes.byref(m), ctypes.byref(a)), "pes_md_costs")
+    return m.value, a.value
+
+
+def fp64_peak(repeats=5):
+    t = ctypes.c_double()
+    _check(lib().pes_fp64_peak(int(repeats), ctypes.byref(t)), "pes_fp64_peak")
+    return t.value
+
+
+def jobc_stats(supports, n, paper_layout=False, max_layers=4096):
+    ptr, idx = csr(supports)
+    stats = np.zeros(8, dtype=np.int64)
+    layers = np.zeros(max_layers, dtype=np.int32)
+    _check(lib().pes_jobc_stats(_ip32(ptr), _ip32(idx), len(supports), int(n), int(bool(paper_layout)),
+                                stats.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ip32(layers), max_layers),
+           "pes_jobc_stats")
+    keys = ("conv_jobs", "layers", "add_terms", "paper_add_jobs", "slots", "add_levels", "vjp_conv", "vjp_corr")
+    out = {k_: int(v) for k_, v in zip(keys, stats)}
+    out["layer_sizes"] = [int(v) for v in layers[: out["layers"]]]
+    return out
+
+
+def jobc_jobs(supports, n, paper_layout=False):
+    st = jobc_stats(supports, n, paper_layout)
+    ptr, idx = csr(supports)
+    jobs = np.zeros((max(st["conv_jobs"], 1), 4), dtype=np.int32)
+    _check(lib().pes_jobc_jobs(_ip32(ptr), _ip32(idx), len(supports), int(n), int(bool(paper_layout)),
+                               _ip32(jobs), st["conv_jobs"]), "pes_jobc_jobs")
+    return jobs[: st["conv_jobs"]]
+
+
+def jobc_add_levels(supports, n, cap=256):
+    ptr, idx = csr(supports)
+    lv = np.zeros(cap, dtype=np.int64)
+    nl = ctypes.c_int32()
+    _check(lib().pes_jobc_add_levels(_ip32(ptr), _ip32(idx), len(supports), int(n),
+                                     lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nl)),
+           "pes_jobc_add_levels")
+    return [int(v) for v in lv[: nl.value]]
+
+
+def jobc_add_terms(supports, n):
+    st = jobc_stats(supports, n)
+    ptr, idx = csr(supports)
+    add_ptr = np.zeros(int(n) + 2, dtype=np.int32)
+    add_src = np.zeros(max(st["add_terms"], 1), dtype=np.int32)
+    _check(lib().pes_jobc_add_terms(_ip32(ptr), _ip32(idx), len(supports), int(n), _ip32(add_ptr),
+                                    _ip32(add_src), st["add_terms"]), "pes_jobc_add_terms")
+    return add_ptr, add_src[: st["add_terms"]]
+
+
+def selftest_timeout(timeout_ms=500):
+    """Run the bounded-wait failure path; returns the device status it reported."""
+    status = ctypes.c_int32(-1)
+    _check(lib().pes_selftest_timeout(int(timeout_ms), ctypes.byref(status)), "pes_selftest_timeout")
+    return STATUS.get(status.value, status.value)

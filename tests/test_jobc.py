@@ -1,0 +1,138 @@
+"""Job compiler (host, integer only) against the counts the paper prints and a
+symbolic interpretation of its job tables.  No GPU needed: these functions of
+libpes do not touch the device."""
+from collections import Counter
+
+import numpy as np
+import pytest
+
+from paper_2101_10881_gb300 import pes, synth
+from tests.golden.load import paper_counts
+
+PC = paper_counts()
+EXAMPLE = [[0, 2, 5], [0, 1, 4, 5], [1, 2, 3]]  # a1 x1 x3 x6 + a2 x1 x2 x5 x6 + a3 x2 x3 x4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pes.build()
+
+
+def test_example_triplet_and_pair_offsets():
+    jobs = pes.jobc_jobs(EXAMPLE, 6, paper_layout=True)
+    # f_{1,1} := a_1 * z_1 is the first job of layer 1
+    assert list(jobs[0][:3]) == PC["example_triplet_f11"]
+    # f_{1,3} is slot 12: the output of the job f_{1,3} := f_{1,2} * z_6
+    outs = {tuple(j[:2]): j[2] for j in jobs}
+    assert outs[(11, 1 + 3 + 5)] == PC["example_pair_f13"][1]
+    st = pes.jobc_stats(EXAMPLE, 6, paper_layout=True)
+    assert st["slots"] == PC["example_data_array_series"]
+
+
+def test_example_layers():
+    st = pes.jobc_stats(EXAMPLE, 6)
+    assert st["conv_jobs"] == PC["example_convolutions"]
+    assert st["layer_sizes"] == PC["example_layers"]
+
+
+def test_p1_counts():
+    supp = synth.supports_p1()
+    st = pes.jobc_stats(supp, 16)
+    assert st["conv_jobs"] == PC["p1_convolutions"]
+    assert st["layer_sizes"] == PC["p1_conv_layers"]
+    assert st["paper_add_jobs"] == PC["p1_additions"]
+    assert pes.jobc_add_levels(supp, 16) == PC["p1_add_levels"]
+
+
+def test_p2_layers():
+    supp = synth.supports_p2()
+    st = pes.jobc_stats(supp, 128)
+    assert st["conv_jobs"] == PC["p2_convolutions"]
+    assert st["layer_sizes"][:31] == [PC["p2_first_31_layers"]] * 31
+    assert st["layers"] == 64
+
+
+def test_p3_counts():
+    supp = synth.supports_p3()
+    st = pes.jobc_stats(supp, 128)
+    assert st["paper_add_jobs"] == PC["p3_additions"]
+    # three products per monomial of two variables (the table's 24,256 is not 3 x 8128)
+    assert st["conv_jobs"] == 3 * 8128
+    assert st["layer_sizes"] == [2 * 8128, 8128]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_data_array_count_formula(seed):
+    """Eq. (eqcountnum): 1 + N + n + sum (n_k + max(1, n_k-2) + max(0, n_k-2))."""
+    rng = np.random.default_rng(seed)
+    n = 12
+    supp = synth.random_supports(rng, n, 30, 1, 9)
+    st = pes.jobc_stats(supp, n, paper_layout=True)
+    expect = 1 + len(supp) + n + sum(len(s) + max(1, len(s) - 2) + max(0, len(s) - 2) for s in supp)
+    assert st["slots"] == expect
+
+
+def symbolic(supports, n, paper_layout=False):
+    """Interpret the job table on multisets of symbols; check the schedule."""
+    N = len(supports)
+    jobs = pes.jobc_jobs(supports, n, paper_layout)
+    content = {0: Counter(["a0"])}
+    for m in range(1, N + 1):
+        content[m] = Counter([f"a{m}"])
+    for i in range(n):
+        content[1 + N + i] = Counter([f"z{i}"])
+    ready = {s: 0 for s in content}
+    written_in_layer = {}
+    for in1, in2, out, layer in jobs:
+        assert in1 in content and in2 in content, "operand read before it is produced"
+        assert ready[in1] < layer and ready[in2] < layer, "operand produced in the same or a later layer"
+        assert (out, layer) not in written_in_layer, "two jobs of one layer write one slot"
+        written_in_layer[(out, layer)] = True
+        assert layer == 1 + max(ready[in1], ready[in2]), "job not in its earliest layer"
+        content[out] = content[in1] + content[in2]
+        ready[out] = layer
+    return content
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_symbolic_value_and_gradient(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 10
+    supp = synth.random_supports(rng, n, 25, 1, 9)
+    content = symbolic(supp, n)
+    add_ptr, add_src = pes.jobc_add_terms(supp, n)
+    N = len(supp)
+
+    def terms(o):
+        return sorted(tuple(sorted(content[s].elements())) for s in add_src[add_ptr[o]:add_ptr[o + 1]])
+
+    want_value = sorted([("a0",)] + [tuple(sorted([f"a{m + 1}"] + [f"z{v}" for v in s])) for m, s in enumerate(supp)])
+    assert terms(0) == want_value
+    for i in range(n):
+        want = sorted(tuple(sorted([f"a{m + 1}"] + [f"z{v}" for v in s if v != i]))
+                      for m, s in enumerate(supp) if i in s)
+        assert terms(1 + i) == want
+
+
+def test_symbolic_example_paper_layout():
+    symbolic(EXAMPLE, 6, paper_layout=True)
+
+
+def test_invalid_supports():
+    for bad, n in (([[1, 0]], 3), ([[0, 0]], 3), ([[3]], 3), ([[]], 3), ([[0]], 0)):
+        with pytest.raises(pes.PesError) as e:
+            pes.jobc_stats(bad, n)
+        assert e.value.code == 1
+
+
+def test_flop_metric_reproduces_paper():
+    """Sec. 6.2: the P100 figure of 1.25 TFLOPS counts (d+1)^2 deca double
+    multiplications and d(d+1) additions per convolution plus d+1 per addition."""
+    mul, add = pes.md_costs(10)
+    d = 152
+    conv, adds = PC["p1_convolutions"], PC["p1_additions"]
+    mul_ops = conv * (d + 1) ** 2 * mul
+    add_ops = (conv * d * (d + 1) + adds * (d + 1)) * add
+    assert mul_ops == PC["p1_paper_mul_ops_d152"]
+    assert add_ops == PC["p1_paper_add_ops_d152"]
+    assert mul_ops + add_ops == PC["p1_paper_total_ops_d152"]
