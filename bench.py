@@ -1,0 +1,430 @@
+"""Benchmark of polynomial evaluation and differentiation at power series.
+
+Workload (one step): value and full gradient of a p2-like polynomial (n=128
+variables, 128 monomials of 64 distinct variables each, every coefficient and
+input a random series truncated at degree d=152, deca double k=10), through
+the library's C-ABI (pes_eval_grad), inputs resident in device memory.
+
+Headline `value`: double-precision-equivalent TFLOP/s, counting the
+algorithmic work of the method (Sec. 6.2 convention with the triangular
+convolution): per convolution (d+1)(d+2)/2 multiplications and d(d+1)/2
+additions of deca doubles at 3089 and 397 double operations, plus d+1 deca
+double additions per addition job.
+
+Also reported: `e2e` (same metric through the Python API with pinned host
+buffers, copies inside the timed region), `roofline` of the convolution kernel
+against the measured FP64 FMA peak, the oracle as `cpu_baseline`, launch count
+and SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run, one rank per GPU) every rank
+evaluates its own polynomial of the same shape (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "eval+grad DP-equiv TFLOP/s, k=10 d=152; batched vs plain ms/instance at tol"
+UNIT = "TFLOP/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--arith", choices=["fp64", "int"], default="fp64")
+    ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["p2", "p1", "p3"], default="p2",
+                    help="p2: the headline workload; p1 / p3: the paper's other test polynomials (analysis)")
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--d", type=int, default=152)
+    ap.add_argument("--monomials", type=int, default=0,
+                    help="use only the first M monomials of the workload (smaller case for profiling)")
+    ap.add_argument("--cpu-sample-vars", type=int, default=12,
+                    help="variables of the monomial the oracle evaluates as the CPU sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# operation counts
+# ---------------------------------------------------------------------------
+
+def md_costs(k):
+    from paper_2101_10881_gb300 import pes
+    return pes.md_costs(k)
+
+
+def dp_equiv_ops(conv_jobs, add_jobs, d, k):
+    """Double-operation equivalent of the algorithmic work (triangular products)."""
+    cm, ca = md_costs(k)
+    per_conv = (d + 1) * (d + 2) // 2 * cm + d * (d + 1) // 2 * ca
+    return conv_jobs * per_conv + add_jobs * (d + 1) * ca
+
+
+def digit_fma_flops(conv_jobs, d, k):
+    """FP64 flops of the exact digit products the convolution kernel executes:
+    L(L+1)/2 FMAs (2 flops) per term, (d+1)(d+2)/2 terms per convolution."""
+    from paper_2101_10881_gb300 import pes  # noqa: F401
+    L = (53 * k + 28 + 23) // 24 + 1
+    return conv_jobs * (d + 1) * (d + 2) // 2 * (L * (L + 1) // 2) * 2
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu_index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU sample of the same workload (the oracle)
+# ---------------------------------------------------------------------------
+
+def cpu_sample(prob, nvars):
+    """The oracle on one monomial of the workload restricted to its first
+    `nvars` variables (value and gradient at the full degree and precision)."""
+    from paper_2101_10881_gb300 import synth
+    supp = [prob.supports[0][:nvars]]
+    used = sorted(set(supp[0]))
+    remap = {v: i for i, v in enumerate(used)}
+    s2 = [[remap[v] for v in supp[0]]]
+    coeff = prob.coeff[:, :2].copy()
+    inputs = prob.inputs[:, used].copy()
+    sub = synth.Problem("cpu sample", len(used), prob.d, prob.k, s2, coeff, inputs)
+    return sub
+
+
+def run_oracle(sub):
+    from oracle import oracle
+    t0 = time.perf_counter()
+    oracle.eval_grad(sub.supports, sub.n, sub.coeff, sub.inputs)
+    return time.perf_counter() - t0, oracle.threads()
+
+
+def sample_ops(sub):
+    m = len(sub.supports[0])
+    conv = 3 * m - 3 if m >= 2 else 1
+    add_jobs = 1  # a_0 + f_{1,m}; every partial has a single term
+    return dp_equiv_ops(conv, add_jobs, sub.d, sub.k)
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def reference_arm(args, world, rank):
+    """The oracle as it stands, on the machine's host cores, on a bounded sample."""
+    if rank != 0:
+        return 0
+    prob = make_workload(args, 0)
+    sub = cpu_sample(prob, args.cpu_sample_vars)
+    for _ in range(args.warmup):
+        run_oracle(sub)
+    times, cores = [], 1
+    for _ in range(args.steps):
+        t, cores = run_oracle(sub)
+        times.append(t)
+    total = sum(times)
+    ops = sample_ops(sub) * args.steps
+    value = ops / total / 1e12
+    sample = (f"oracle value+gradient of monomial 1 of the workload restricted to its first "
+              f"{len(sub.supports[0])} variables, d={sub.d}, k={sub.k}, per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(prob, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def make_workload(args, rank):
+    from paper_2101_10881_gb300 import synth
+    seed = args.seed + 1000 * rank
+    if args.workload == "p1":
+        return synth.make_problem("p1", synth.supports_p1(), 16, args.d, args.k, seed)
+    if args.workload == "p3":
+        return synth.make_problem("p3", synth.supports_p3(), 128, args.d, args.k, seed)
+    return synth.config1(seed=seed, d=args.d, k=args.k)
+
+
+def workload_config(prob, args):
+    sizes = sorted({len(s) for s in prob.supports})
+    shape = {"p2": "p2-like", "p1": "p1", "p3": "p3"}[args.workload]
+    return {"workload": f"{shape} polynomial n={prob.n} N={prob.N} monomials of {sizes[0] if len(sizes) == 1 else sizes} "
+                        f"variables, d={prob.d}, k={prob.k}, value + full gradient per step",
+            "global_batch": 1, "seq_len": prob.d + 1, "parallelism": f"replicas x{args.gpus}",
+            "arith": args.arith, "threads_per_cta": args.threads,
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); workspace > L2"}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "digits.cuh", "kernels.hpp"):
+        with open(os.path.join(ROOT, "paper_2101_10881_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(conv_jobs_full):
+    """DRAM bytes of one convolution launch from the committed ncu summary, if
+    it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dag_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k_, v_ = line.split("=", 1)
+            vals[k_.strip()] = v_.split("#")[0].strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        per_job = float(vals["dram_bytes_per_launch"]) / float(vals["conv_jobs"])
+    except (KeyError, ValueError, ZeroDivisionError):
+        return None
+    return per_job * conv_jobs_full
+
+
+def ours_arm(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2101_10881_gb300 import pes, synth
+
+    pes.build()
+    dev = torch.device("cuda", local)
+    prob = make_workload(args, rank)
+    if args.monomials:
+        prob = synth.Problem(prob.name, prob.n, prob.d, prob.k, prob.supports[: args.monomials],
+                             prob.coeff[:, : args.monomials + 1].copy(), prob.inputs)
+    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, arith=args.arith, threads=args.threads,
+                    with_vjp=False, profile=True)
+    info = plan.info()
+    C = torch.from_numpy(prob.coeff).to(dev)
+    Z = torch.from_numpy(prob.inputs).to(dev)
+    V = torch.empty(plan.shapes()["value"], dtype=torch.float64, device=dev)
+    G = torch.empty(plan.shapes()["grad"], dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    fp64_peak = pes.fp64_peak(repeats=7)
+    int_peak = pes.int_peak(repeats=7)
+
+    ops_step = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], prob.d, prob.k)
+    digit_flops = digit_fma_flops(info["conv_jobs"], prob.d, prob.k)
+
+    for _ in range(max(args.warmup, 3)):
+        plan.eval_grad(C, Z, V, G)
+    torch.cuda.synchronize(dev)
+    plan.check()
+
+    # ---- device-resident timed region ----
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    step_ms, conv_ms, launches = [], [], 0
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval_grad(C, Z, V, G)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        t = plan.last_timing()
+        conv_ms.append(t["conv_ms"])
+        launches += t["launches"]
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall0
+    barrier(world)
+    clk = clocks.stop()
+    plan.check()
+    total_ms = max_over_ranks(sum(step_ms), world)
+
+    # ---- end to end through the public API: pinned host buffers, copies timed ----
+    hC = torch.from_numpy(prob.coeff).pin_memory()
+    hZ = torch.from_numpy(prob.inputs).pin_memory()
+    hV = torch.empty(V.shape, dtype=torch.float64).pin_memory()
+    hG = torch.empty(G.shape, dtype=torch.float64).pin_memory()
+    h2d = hC.numel() * 8 + hZ.numel() * 8
+    d2h = hV.numel() * 8 + hG.numel() * 8
+    e2e_ms = []
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C.copy_(hC, non_blocking=True)
+        Z.copy_(hZ, non_blocking=True)
+        plan.eval_grad(C, Z, V, G)
+        hV.copy_(V, non_blocking=True)
+        hG.copy_(G, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    barrier(world)
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
+
+    value = world * ops_step * args.steps / (total_ms * 1e-3) / 1e12
+    e2e_value = world * ops_step * args.steps / (e2e_total * 1e-3) / 1e12
+    mean_conv = statistics.mean(conv_ms)
+    work = (f"{info['conv_jobs']} convolutions x {(prob.d + 1) * (prob.d + 2) // 2} terms x "
+            f"{info['digits'] * (info['digits'] + 1) // 2} digit products")
+    if args.arith == "fp64":
+        achieved = digit_flops / (mean_conv * 1e-3) / 1e12
+        roofline = {"bound": "alu", "pipe": "fp64 (DFMA)", "achieved": achieved, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "peak_source": "measured: pes_fp64_peak DFMA microbenchmark (burst, all SMs), this run"}
+    else:
+        achieved = digit_flops / 2 / (mean_conv * 1e-3) / 1e12
+        roofline = {"bound": "alu", "pipe": "int (IMAD.WIDE 32x32+64)", "achieved": achieved, "peak": int_peak,
+                    "unit": "Tops/s", "frac": achieved / int_peak,
+                    "peak_source": "measured: pes_int_peak multiply-add microbenchmark (burst, all SMs), this run"}
+    roofline.update({"traffic": traffic_per_launch(info["conv_jobs"]), "work": work, "kernel_ms": mean_conv})
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(prob, args),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_total / args.steps},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "dp_equiv_over_fp64_peak": value / world / fp64_peak,
+        "peaks": {"fp64_tflops": fp64_peak, "int_mad_wide_tops": int_peak},
+        "ops_per_step": ops_step,
+        "wall_s_timed_region": wall,
+        "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
+                 "grid": info["grid"], "smem_bytes": info["smem_bytes"], "digits": info["digits"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sub = cpu_sample(prob, args.cpu_sample_vars)
+        t, cores = run_oracle(sub)
+        out["cpu_baseline"] = {"value": sample_ops(sub) / t / 1e12, "unit": UNIT, "cores": cores,
+                               "kind": "oracle", "seconds": t,
+                               "sample": f"value+gradient of monomial 1 restricted to its first "
+                                         f"{len(sub.supports[0])} variables, d={sub.d}, k={sub.k}"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args) if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+    rc = ours_arm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

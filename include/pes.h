@@ -64,6 +64,8 @@ typedef struct {
   int32_t ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit */
   int32_t with_vjp;    /* 1: also build the tables of pes_vjp (default 1) */
   int64_t timeout_ms;  /* bound on every device-side wait; 0 = default (60000) */
+  int32_t profile;     /* 1: record CUDA events around each launch of a call (see pes_last_timing) */
+  int32_t pad;
 } pes_options;
 
 /* Fill *opt with the defaults. */
@@ -120,6 +122,14 @@ pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double* input, co
  * bytes.  Lets a caller keep the products of one call alive under its own
  * memory budget and reuse them later with pes_vjp(..., reuse_forward = 1). */
 pes_status pes_workspace_io(pes_plan_t plan, void* buffer, int32_t to_buffer, void* stream);
+
+/* Device time of the launches of the last pes_eval_grad / pes_vjp /
+ * pes_eval_grad_batch call of a plan or batch built with profile = 1, measured
+ * with CUDA events on the call's stream (waits for the events):
+ *   ms[0] pack, ms[1] convolution kernel(s), ms[2] addition, ms[3] unpack;
+ * *launches receives the number of kernels the call launched. */
+pes_status pes_last_timing(pes_plan_t plan, double* ms, int32_t* launches);
+pes_status pes_batch_last_timing(pes_batch_t batch, double* ms, int32_t* launches);
 
 /* Synchronise `stream`, then return (and clear) the device status of the plan:
  * PES_OK, or PES_ETIMEOUT when a bounded wait gave up during a call. */
@@ -183,6 +193,10 @@ pes_status pes_md_costs(int32_t k, double* mul_ops, double* add_ops);
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops per
  * FMA), best of `repeats` timed launches over all SMs. */
 pes_status pes_fp64_peak(int32_t repeats, double* tflops);
+
+/* Measured throughput of 32x32->64-bit integer multiply-add (the digit product
+ * of PES_ARITH_INT) on the current device, in tera-operations per second. */
+pes_status pes_int_peak(int32_t repeats, double* tops);
 
 /* ---- job compiler introspection (host only; no GPU needed) --------------------- */
 

@@ -114,7 +114,7 @@ template <int K, int L>
 PES_HD void to_digits(const double* x, int ls, int32_t g, int64_t (&D)[L]) {
 #pragma unroll
   for (int p = 0; p < L; ++p) D[p] = 0;
-#pragma unroll
+#pragma unroll 1
   for (int l = 0; l < K; ++l) {
     int neg;
     uint64_t mant;
@@ -159,7 +159,7 @@ PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long 
     sign = -1.0;
   }
   const int32_t base_exp = DIGIT_BITS * gs - DIGIT_BITS * (L + 1);
-#pragma unroll
+#pragma unroll 1
   for (int l = 0; l < K; ++l) {
     // highest set bit of the magnitude
     int top = -1;
@@ -172,7 +172,6 @@ PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long 
       }
     }
     if (top < 0) {
-#pragma unroll
       for (int r = l; r < K; ++r) out[r * ls] = 0.0;
       return;
     }

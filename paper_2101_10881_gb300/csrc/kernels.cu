@@ -100,13 +100,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
   }
 }
 
-__device__ __forceinline__ long long mac(int32_t x, int32_t y, long long acc) {
-  long long r;
-  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(r) : "r"(x), "r"(y), "l"(acc));
-  return r;
+// acc += x * y, exactly: 32x32 -> 64-bit integer multiply-add in place, or FP64 FMA
+// on digit products that are exact by construction.
+__device__ __forceinline__ void mac(int32_t x, int32_t y, long long& acc) {
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(x), "r"(y));
 }
 
-__device__ __forceinline__ double mac(double x, double y, double acc) { return __fma_rn(x, y, acc); }
+__device__ __forceinline__ void mac(double x, double y, double& acc) { acc = __fma_rn(x, y, acc); }
 
 __device__ __forceinline__ void set_error(Ctrl* ctrl, int code, long long d0, long long d1) {
   if (atomicCAS(&ctrl->status, 0, code) == 0) {
@@ -311,9 +311,20 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
         const int ix = conv ? i : j + i;
         const int iy = conv ? j - i : i;
         const int delta = gsj - gx[ix] - gy[iy];
-        if (delta < L) {
-          const DigitT* yr = ydig + iy * LP;
-          const DigitT* xr = xdig + ix * LP;
+        const DigitT* yr = ydig + iy * LP;
+        const DigitT* xr = xdig + ix * LP;
+        if (__all_sync(__activemask(), delta == 0)) {
+          // common case: every lane's term is aligned with its reference grid
+          DigitT Y[L];
+#pragma unroll
+          for (int q = 0; q < L; ++q) Y[q] = yr[q];
+#pragma unroll
+          for (int p = 0; p < L; ++p) {
+            const DigitT xv = xr[p];
+#pragma unroll
+            for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+          }
+        } else if (delta < L) {
           DigitT Y[L];
 #pragma unroll
           for (int q = 0; q < L; ++q) Y[q] = yr[q];
@@ -323,7 +334,7 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
             DigitT xv = xr[id < 0 ? 0 : id];
             xv = id < 0 ? DigitT(0) : xv;
 #pragma unroll
-            for (int q = 0; q < L - p; ++q) A[p + q] = mac(xv, Y[q], A[p + q]);
+            for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
           }
         }
         ++i;
@@ -502,6 +513,22 @@ __global__ void fp64_peak_kernel(double* sink, int iters, double a, double b) {
   if (s == 12345.678) sink[blockIdx.x] = s;  // keeps the chains alive
 }
 
+// IMAD.WIDE throughput: 8 independent 32x32->64-bit multiply-add chains per thread.
+__global__ void int_peak_kernel(long long* sink, int iters, int a, int b) {
+  long long acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = threadIdx.x + i;
+  const int x = a + static_cast<int>(threadIdx.x), y = b - static_cast<int>(threadIdx.x);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[i]) : "r"(x), "r"(y));
+  }
+  long long s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += acc[i];
+  if (s == 12345) sink[blockIdx.x] = s;
+}
+
 template <int K, bool INTV>
 void* dag_fn() {
   return reinterpret_cast<void*>(&dag_kernel<K, INTV>);
@@ -603,6 +630,11 @@ cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, do
     case 10: md_binary_kernel<10><<<grid, 128, 0, st>>>(op, x, y, out, count); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_int_peak(long long* sink, int blocks, int threads, int iters, cudaStream_t st) {
+  int_peak_kernel<<<blocks, threads, 0, st>>>(sink, iters, 3, 5);
   return cudaGetLastError();
 }
 

@@ -72,5 +72,6 @@ cudaError_t dag_prepare(int k, int arith, size_t smem);
 cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out,
                              int64_t count, cudaStream_t st);
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters, cudaStream_t st);
+cudaError_t launch_int_peak(long long* sink, int blocks, int threads, int iters, cudaStream_t st);
 
 }  // namespace pes

@@ -79,8 +79,15 @@ struct Exec {
   double* ws = nullptr;
   size_t ws_doubles = 0;
   std::vector<void*> owned;
+  // profiling: events around the phases of the last call
+  bool profile = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int32_t last_launches = 0;
+  bool has_unpack = false;
 
   ~Exec() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
     for (void* p : owned) cudaFree(p);
     cudaFree(inst);
     cudaFree(ctrl);
@@ -151,6 +158,9 @@ struct Exec {
     cudaError_t e = cudaMalloc(&ctrl, sizeof(pes::Ctrl));
     if (e != cudaSuccess) return fail(PES_ENOMEM, "control block");
     PES_CUDA(cudaMemset(ctrl, 0, sizeof(pes::Ctrl)));
+    profile = o.profile != 0;
+    if (profile)
+      for (cudaEvent_t& e : ev) PES_CUDA(cudaEventCreate(&e));
     ws_doubles = std::max<size_t>(ws_doubles_, 8);
     e = cudaMalloc(&ws, ws_doubles * sizeof(double));
     if (e != cudaSuccess) return fail(PES_ENOMEM, "workspace of " + std::to_string(ws_doubles * 8) + " bytes");
@@ -213,6 +223,21 @@ struct Exec {
     a.dst[0] = d0;
     a.dst[1] = d1;
     return pes::launch_unpack(a, k, st);
+  }
+
+  // record phase boundary i (0..4) of the current call
+  cudaError_t mark(int i, cudaStream_t st) const { return profile ? cudaEventRecord(ev[i], st) : cudaSuccess; }
+
+  pes_status last_timing(double* ms, int32_t* launches) {
+    if (!profile) return fail(PES_EINVAL, "built without profile = 1");
+    PES_CUDA(cudaEventSynchronize(ev[4]));
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      PES_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      if (ms) ms[i] = t;
+    }
+    if (launches) *launches = last_launches;
+    return PES_OK;
   }
 
   pes_status check(cudaStream_t st) {
@@ -278,6 +303,8 @@ extern "C" void pes_default_options(pes_options* opt) {
   opt->ctas_per_sm = 0;
   opt->with_vjp = 1;
   opt->timeout_ms = 60000;
+  opt->profile = 0;
+  opt->pad = 0;
 }
 
 extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -374,10 +401,16 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
   if (!coeff || !input || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Exec& E = plan->ex;
+  PES_CUDA(E.mark(0, st));
   PES_CUDA(pes::launch_prologue(E.ctrl, st));
   PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
+  PES_CUDA(E.mark(1, st));
   PES_CUDA(E.run_dag(plan->fwd, 0, st));
+  PES_CUDA(E.mark(2, st));
   PES_CUDA(E.run_add(plan->add, value, grad, st));
+  PES_CUDA(E.mark(3, st));
+  PES_CUDA(E.mark(4, st));
+  E.last_launches = 4;
   return PES_OK;
 }
 
@@ -389,18 +422,26 @@ extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double
     return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Exec& E = plan->ex;
+  PES_CUDA(E.mark(0, st));
   PES_CUDA(pes::launch_prologue(E.ctrl, st));
   if (reuse_forward) {
     PES_CUDA(E.run_pack(plan->pack_u, nullptr, nullptr, upstream, st));
+    PES_CUDA(E.mark(1, st));
     PES_CUDA(E.run_dag(plan->vjp_m, 0, st));
+    E.last_launches = 5 + (plan->vjp_m.n > 0 ? 1 : 0);
   } else {
     PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
     PES_CUDA(E.run_pack(plan->pack_u, nullptr, nullptr, upstream, st));
+    PES_CUDA(E.mark(1, st));
     PES_CUDA(E.run_dag(plan->vjp_fwd, 0, st));
+    E.last_launches = 7;
   }
   PES_CUDA(E.run_add(plan->add_g, E.ws, nullptr, st));
   PES_CUDA(E.run_dag(plan->vjp_corr, 1, st));
+  PES_CUDA(E.mark(2, st));
+  PES_CUDA(E.mark(3, st));
   PES_CUDA(E.run_unpack(plan->unpack, grad_coeff, grad_input, st));
+  PES_CUDA(E.mark(4, st));
   return PES_OK;
 }
 
@@ -413,6 +454,11 @@ extern "C" pes_status pes_workspace_io(pes_plan_t plan, void* buffer, int32_t to
   else
     PES_CUDA(cudaMemcpyAsync(plan->ex.ws, buffer, bytes, cudaMemcpyDeviceToDevice, st));
   return PES_OK;
+}
+
+extern "C" pes_status pes_last_timing(pes_plan_t plan, double* ms, int32_t* launches) {
+  if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  return plan->ex.last_timing(ms, launches);
 }
 
 extern "C" pes_status pes_check(pes_plan_t plan, void* stream) {
@@ -611,8 +657,19 @@ extern "C" pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     std::memcpy(batch->gkey, key, sizeof(key));
   }
+  PES_CUDA(batch->ex.mark(0, st));
+  PES_CUDA(batch->ex.mark(1, st));
   PES_CUDA(cudaGraphLaunch(batch->gexec, st));
+  PES_CUDA(batch->ex.mark(2, st));
+  PES_CUDA(batch->ex.mark(3, st));
+  PES_CUDA(batch->ex.mark(4, st));
+  batch->ex.last_launches = 4;
   return PES_OK;
+}
+
+extern "C" pes_status pes_batch_last_timing(pes_batch_t batch, double* ms, int32_t* launches) {
+  if (!batch) return fail(PES_EINVAL, "batch is NULL");
+  return batch->ex.last_timing(ms, launches);
 }
 
 extern "C" pes_status pes_batch_check(pes_batch_t batch, void* stream) {
@@ -706,6 +763,37 @@ extern "C" pes_status pes_fp64_peak(int32_t repeats, double* tflops) {
   if (e != cudaSuccess) return cuda_fail(e, "fp64 peak kernel");
   const double fmas = static_cast<double>(blocks) * threads * iters * 8.0;
   *tflops = 2.0 * fmas / (static_cast<double>(best) * 1e-3) / 1e12;
+  return PES_OK;
+}
+
+extern "C" pes_status pes_int_peak(int32_t repeats, double* tops) {
+  if (!tops) return fail(PES_EINVAL, "tops is NULL");
+  int dev = 0, nsm = 0;
+  PES_CUDA(cudaGetDevice(&dev));
+  PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  long long* sink = nullptr;
+  const int threads = 256, blocks = nsm * 4, iters = 65536;
+  PES_CUDA(cudaMalloc(&sink, sizeof(long long) * static_cast<size_t>(blocks)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  pes::launch_int_peak(sink, blocks, threads, iters / 8, nullptr);
+  for (int r = 0; r < std::max(1, repeats); ++r) {
+    cudaEventRecord(e0, nullptr);
+    pes::launch_int_peak(sink, blocks, threads, iters, nullptr);
+    cudaEventRecord(e1, nullptr);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "int peak kernel");
+  *tops = static_cast<double>(blocks) * threads * iters * 8.0 / (static_cast<double>(best) * 1e-3) / 1e12;
   return PES_OK;
 }
 

@@ -26,9 +26,9 @@ ARITH = {"fp64": 0, "int": 1}
 
 # every symbol that include/pes.h declares
 EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_destroy", "pes_eval_grad", "pes_vjp",
-           "pes_workspace_io", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
+           "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
-           "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_jobc_stats", "pes_jobc_jobs",
+           "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_int_peak", "pes_jobc_stats", "pes_jobc_jobs",
            "pes_jobc_add_levels", "pes_jobc_add_terms", "pes_selftest_timeout", "pes_status_string",
            "pes_last_error")
 
@@ -41,7 +41,8 @@ class PesError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("arith", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("with_vjp", ctypes.c_int32), ("timeout_ms", ctypes.c_int64)]
+                ("with_vjp", ctypes.c_int32), ("timeout_ms", ctypes.c_int64), ("profile", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -84,6 +85,8 @@ def lib():
                 "pes_vjp": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
                 "pes_workspace_io": (i32, [vp, vp, i32, vp]),
                 "pes_check": (i32, [vp, vp]),
+                "pes_last_timing": (i32, [vp, dp, ip32]),
+                "pes_batch_last_timing": (i32, [vp, dp, ip32]),
                 "pes_get_plan_info": (i32, [vp, ctypes.POINTER(PlanInfo)]),
                 "pes_plan_batch": (i32, [i32, ip32, ip32, ip32, ip32, ip32, i32, ctypes.POINTER(Options),
                                          ctypes.POINTER(vp)]),
@@ -95,6 +98,7 @@ def lib():
                 "pes_md_binary": (i32, [i32, i32, vp, vp, vp, i64, vp]),
                 "pes_md_costs": (i32, [i32, dp, dp]),
                 "pes_fp64_peak": (i32, [i32, dp]),
+                "pes_int_peak": (i32, [i32, dp]),
                 "pes_jobc_stats": (i32, [ip32, ip32, i32, i32, i32, ip64, ip32, i32]),
                 "pes_jobc_jobs": (i32, [ip32, ip32, i32, i32, i32, ip32, i64]),
                 "pes_jobc_add_levels": (i32, [ip32, ip32, i32, i32, ip64, i32, ip32]),
@@ -145,7 +149,7 @@ def _ptr(t, shape, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_options(arith="fp64", threads=128, ctas_per_sm=0, with_vjp=True, timeout_ms=60000):
+def make_options(arith="fp64", threads=128, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False):
     o = Options()
     lib().pes_default_options(ctypes.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
@@ -153,7 +157,15 @@ def make_options(arith="fp64", threads=128, ctas_per_sm=0, with_vjp=True, timeou
     o.ctas_per_sm = int(ctas_per_sm)
     o.with_vjp = int(bool(with_vjp))
     o.timeout_ms = int(timeout_ms)
+    o.profile = int(bool(profile))
     return o
+
+
+def _timing(fn, h, where):
+    ms = (ctypes.c_double * 4)()
+    nl = ctypes.c_int32()
+    _check(fn(h, ms, ctypes.byref(nl)), where)
+    return {"pack_ms": ms[0], "conv_ms": ms[1], "add_ms": ms[2], "unpack_ms": ms[3], "launches": nl.value}
 
 
 class Plan:
@@ -222,6 +234,10 @@ class Plan:
     def check(self, stream=None):
         _check(lib().pes_check(self._h, _stream(stream)), "pes_check")
 
+    def last_timing(self):
+        """Per-phase device time of the last call (plan built with profile=True)."""
+        return _timing(lib().pes_last_timing, self._h, "pes_last_timing")
+
     def info(self):
         pi = PlanInfo()
         _check(lib().pes_get_plan_info(self._h, ctypes.byref(pi)), "pes_get_plan_info")
@@ -277,6 +293,9 @@ class Batch:
     def check(self, stream=None):
         _check(lib().pes_batch_check(self._h, _stream(stream)), "pes_batch_check")
 
+    def last_timing(self):
+        return _timing(lib().pes_batch_last_timing, self._h, "pes_batch_last_timing")
+
     def info(self):
         pi = PlanInfo()
         _check(lib().pes_get_batch_info(self._h, ctypes.byref(pi)), "pes_get_batch_info")
@@ -303,6 +322,12 @@ def md_costs(k):
 def fp64_peak(repeats=5):
     t = ctypes.c_double()
     _check(lib().pes_fp64_peak(int(repeats), ctypes.byref(t)), "pes_fp64_peak")
+    return t.value
+
+
+def int_peak(repeats=5):
+    t = ctypes.c_double()
+    _check(lib().pes_int_peak(int(repeats), ctypes.byref(t)), "pes_int_peak")
     return t.value
 
 
