@@ -232,6 +232,36 @@ pes_status pes_jobc_add_terms(const int32_t* supp_ptr, const int32_t* supp_idx, 
  * the status word (written to *device_status), leaving the context usable. */
 pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status);
 
+/* ---- evaluation without device allocation ------------------------------------ */
+
+/* Same result as pes_plan + pes_eval_grad, for callers that cannot call
+ * cudaMalloc (code running inside another framework's memory pool, plug-ins
+ * whose host forbids device allocations, paths that must keep the device
+ * footprint fixed after start-up).  It allocates nothing on the device: the
+ * job tables, completion flags, control word and workspace of forward,
+ * backward and cross products live in one file-scope static device array of
+ * 64 MiB that is part of this library, so every GPU that loads the library
+ * holds those 64 MiB until the process exits.  The paper has no counterpart.
+ *
+ * Arguments as pes_plan (supports, N, n, d, k) and pes_eval_grad (caller-owned
+ * device buffers coeff, input, value, grad; asynchronous on `stream`).  The job
+ * tables are compiled on the host at every call and copied into the array with
+ * cudaMemcpyAsync; nothing calls cudaMalloc, cudaFree or an allocating library
+ * routine.  Problems whose tables and workspace exceed 64 MiB are rejected
+ * with PES_EUNSUPPORTED_SIZE (message in pes_last_error).
+ *
+ * The first call on a device takes the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  Every call reuses the same array and rewrites
+ * its tables, flags and control word, so calls that overlap on the GPU (on
+ * different streams or threads) race and give wrong results; serialise them.
+ * status_out: NULL, or a host int32 that receives the device status (0, or
+ * PES_ETIMEOUT if a bounded wait gave up) after the call synchronises the
+ * stream. */
+pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
+                                int32_t k, const double* coeff, const double* input, double* value, double* grad,
+                                void* stream, int32_t* status_out);
+
 /* Human-readable name of a status code; never NULL. */
 const char* pes_status_string(pes_status s);
 /* Message of the last PES_EINVAL / PES_ECUDA on this thread ("" if none). */

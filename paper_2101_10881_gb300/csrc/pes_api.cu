@@ -903,3 +903,7 @@ extern "C" const char* pes_status_string(pes_status s) {
 }
 
 extern "C" const char* pes_last_error(void) { return g_last_error.c_str(); }
+
+namespace pes {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace pes

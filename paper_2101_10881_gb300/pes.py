@@ -29,7 +29,7 @@ EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_destroy",
            "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
            "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_int_peak", "pes_jobc_stats", "pes_jobc_jobs",
-           "pes_jobc_add_levels", "pes_jobc_add_terms", "pes_selftest_timeout", "pes_status_string",
+           "pes_jobc_add_levels", "pes_jobc_add_terms", "pes_selftest_timeout", "pes_eval_grad_static", "pes_status_string",
            "pes_last_error")
 
 
@@ -104,6 +104,7 @@ def lib():
                 "pes_jobc_add_levels": (i32, [ip32, ip32, i32, i32, ip64, i32, ip32]),
                 "pes_jobc_add_terms": (i32, [ip32, ip32, i32, i32, ip32, ip32, i64]),
                 "pes_selftest_timeout": (i32, [i64, ip32]),
+                "pes_eval_grad_static": (i32, [ip32, ip32, i32, i32, i32, i32, vp, vp, vp, vp, vp, ip32]),
                 "pes_status_string": (ctypes.c_char_p, [i32]),
                 "pes_last_error": (ctypes.c_char_p, []),
             }
