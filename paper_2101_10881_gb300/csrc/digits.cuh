@@ -108,22 +108,29 @@ PES_HD int64_t window(int neg, uint64_t mant, int32_t lsb, int32_t P) {
   return neg ? -piece : piece;
 }
 
-// Digits of a k-double on grid g into D[0..L-1] (registers), balanced.
-// x: limb l at x[l * ls].  Bits below the last digit are dropped.
+// Digits of a k-double on grid g into D[0..L-1], balanced.  x: limb l at
+// x[l * ls].  Each limb's 53 bits fall into at most four consecutive digit
+// windows, so only those are touched (D is indexed at run time).  Bits below the
+// last digit are dropped.
 template <int K, int L>
-PES_HD void to_digits(const double* x, int ls, int32_t g, int64_t (&D)[L]) {
+PES_HD void to_digits(const double* x, long long ls, int32_t g, int64_t (&D)[L]) {
 #pragma unroll
   for (int p = 0; p < L; ++p) D[p] = 0;
+  const int32_t top = DIGIT_BITS * g;  // bit position just above digit 0
 #pragma unroll 1
   for (int l = 0; l < K; ++l) {
     int neg;
     uint64_t mant;
     int32_t lsb;
     if (!decode(x[l * ls], neg, mant, lsb)) continue;
+    const int32_t hb = lsb + 52;  // highest bit of the limb (mantissas of normal numbers)
+    int32_t p0 = floordiv(top - 1 - hb, DIGIT_BITS);
+    if (p0 < 0) p0 = 0;
+    if (p0 >= L) break;  // this limb and every smaller one lie below the last digit
 #pragma unroll
-    for (int p = 0; p < L; ++p) {
-      int32_t P = DIGIT_BITS * g - DIGIT_BITS * (p + 1);
-      D[p] += window(neg, mant, lsb, P);
+    for (int r = 0; r < 4; ++r) {
+      const int p = p0 + r;
+      if (p < L) D[p] += window(neg, mant, lsb, top - DIGIT_BITS * (p + 1));
     }
   }
   // balanced digits: carry from the bottom up
@@ -136,12 +143,17 @@ PES_HD void to_digits(const double* x, int ls, int32_t g, int64_t (&D)[L]) {
 }
 
 // Round the exact fixed-point sum V = sum_{a=0..L} E[a] 2^(B (L - a)) times
-// 2^(B gs - B (L + 1)) to K nonoverlapping limbs (round to nearest, ties away),
-// written to out[l * ls].  E is destroyed.
+// 2^(B gs - B (L + 1)) to K nonoverlapping limbs (each limb the nearest double
+// to the remainder, ties away from zero), written to out[l * ls].
+//
+// The digits are first carried into [0, 2^B) (digit 0 keeps the sign), then the
+// magnitude is packed into 64-bit words; each limb takes the 53 bits below the
+// highest set bit, rounded; the remainder is V with those bits cleared, or, when
+// the limb was rounded up, 2^mexp minus the bits below mexp with the sign flipped.
 template <int K, int L>
 PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long ls) {
   constexpr int NA = L + 1;
-  // floor-normalise: E[1..L] in [0, 2^B), E[0] carries the sign
+  constexpr int NW = (DIGIT_BITS * L + 64 + 63) / 64 + 1;  // digit 0 holds < 2^40
   auto normalise = [&]() {
 #pragma unroll
     for (int a = NA - 1; a >= 1; --a) {
@@ -158,57 +170,72 @@ PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long 
     normalise();
     sign = -1.0;
   }
+  // pack: digit a occupies bits [B (L - a), B (L - a) + B) (digit 0: upwards)
+  uint64_t Wd[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) Wd[w] = 0;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int pos = DIGIT_BITS * (L - a);
+    const int w = pos / 64, o = pos % 64;
+    const uint64_t v = static_cast<uint64_t>(E[a]);
+    Wd[w] |= v << o;
+    if (o > 0 && w + 1 < NW) Wd[w + 1] |= v >> (64 - o);
+  }
   const int32_t base_exp = DIGIT_BITS * gs - DIGIT_BITS * (L + 1);
 #pragma unroll 1
   for (int l = 0; l < K; ++l) {
-    // highest set bit of the magnitude
-    int top = -1;
-    int32_t h = 0;
+    int tw = -1;
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      if (top < 0 && E[a] != 0) {
-        top = a;
-        h = DIGIT_BITS * (L - a) + (63 - clz64(static_cast<uint64_t>(E[a])));
-      }
-    }
-    if (top < 0) {
+    for (int w = 0; w < NW; ++w)
+      if (Wd[w] != 0) tw = w;
+    if (tw < 0) {
       for (int r = l; r < K; ++r) out[r * ls] = 0.0;
       return;
     }
-    // 64-bit window W = floor(V / 2^(h - 63))
-    uint64_t W = 0;
-    const int32_t wlo = h - 63;
+    uint64_t hi = 0, lo = 0;
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      int32_t pos = DIGIT_BITS * (L - a) - wlo;  // shift of digit a inside the window
-      uint64_t dv = static_cast<uint64_t>(E[a]);
-      if (pos >= 0) {
-        if (pos < 64) W |= dv << pos;
-      } else if (pos > -64) {
-        W |= dv >> (-pos);
-      }
+    for (int w = 0; w < NW; ++w) {
+      if (w == tw) hi = Wd[w];
+      if (w == tw - 1) lo = Wd[w];
     }
-    uint64_t m = (W >> 11) + ((W >> 10) & 1);  // 53 bits, rounded
-    int32_t mexp = h - 52;                      // weight of the mantissa lsb
+    const int hb = 63 - clz64(hi);          // top bit inside word tw
+    const int32_t h = 64 * tw + hb;         // top bit of V
+    // W = the 64 bits of V whose highest is bit h
+    const uint64_t W = (hb == 63) ? hi : ((hi << (63 - hb)) | (lo >> (hb + 1)));
+    const uint64_t rbit = (W >> 10) & 1;
+    const uint64_t m = (W >> 11) + rbit;    // 53 bits, rounded to nearest
+    const int32_t mexp = h - 52;            // weight of the mantissa lsb (may be negative)
     out[l * ls] = sign * ldexp(static_cast<double>(m), mexp + base_exp);
-    // V -= m * 2^mexp (exact): digit a receives the bits of m 2^mexp in its
-    // window [B (L - a), B (L - a) + B); digit 0 receives everything above.
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      int32_t sh = mexp - DIGIT_BITS * (L - a);
-      uint64_t piece;
-      if (sh >= 0)
-        piece = sh >= 64 ? 0 : (m << sh);
-      else
-        piece = (-sh) >= 64 ? 0 : (m >> (-sh));
-      if (a > 0) piece &= static_cast<uint64_t>(DIGIT_MASK);
-      E[a] -= static_cast<int64_t>(piece);
+    if (mexp <= 0) {
+      // every bit of V was taken (exactly, rounding adds nothing below bit 0)
+      for (int r = l + 1; r < K; ++r) out[r * ls] = 0.0;
+      return;
     }
-    normalise();
-    if (E[0] < 0) {
+    const int wm = mexp / 64, om = mexp % 64;
+    if (!rbit) {
+      // remainder: V with bits >= mexp cleared
 #pragma unroll
-      for (int a = 0; a < NA; ++a) E[a] = -E[a];
-      normalise();
+      for (int w = 0; w < NW; ++w) {
+        if (w > wm) Wd[w] = 0;
+        if (w == wm) Wd[w] &= (om == 0) ? 0 : ((uint64_t(1) << om) - 1);
+      }
+    } else {
+      // remainder: -(2^mexp - (V mod 2^mexp)); keep the magnitude, flip the sign
+      uint64_t borrow = 1;  // two's complement of the bits below mexp: ~x + 1
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        if (w < wm) {
+          const uint64_t nv = ~Wd[w] + borrow;
+          borrow = (borrow && nv == 0) ? 1 : 0;
+          Wd[w] = nv;
+        } else if (w == wm) {
+          const uint64_t mask = (om == 0) ? 0 : ((uint64_t(1) << om) - 1);
+          Wd[w] = (~Wd[w] + borrow) & mask;
+        } else {
+          Wd[w] = 0;
+        }
+      }
       sign = -sign;
     }
   }

@@ -140,17 +140,27 @@ struct DagLayout {
   size_t raw, xdig, ydig, gx, gy, gs, bar, misc, total;
 };
 
-__host__ __device__ inline DagLayout dag_layout(int K, int L, int digit_bytes, int smax, int dmax) {
-  const int LP = L | 1;
+// Row strides of the digit arrays (in digits).  Integer variant: an X row is L
+// zero digits followed by the L digits (so a term shifted by delta digits reads
+// the row delta digits early without any select), odd stride; a Y row is padded
+// to a multiple of 4 digits with an odd number of 16-byte groups, so it is read
+// with 128-bit loads without bank conflicts.  FP64 variant: odd stride L | 1.
+__host__ __device__ constexpr int x_stride(int L, bool intv) { return intv ? 2 * L + 1 : (L | 1); }
+__host__ __device__ constexpr int y_stride(int L, bool intv) {
+  return intv ? (((L + 3) / 4) % 2 == 1 ? (L + 3) / 4 * 4 : (L + 3) / 4 * 4 + 4) : (L | 1);
+}
+
+__host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int smax, int dmax) {
+  const int digit_bytes = intv ? 4 : 8;
   DagLayout o;
   size_t raw_bytes = size_t(2) * K * smax * sizeof(double);
   size_t exch_bytes = size_t(dmax + 1) * (L + 1) * sizeof(unsigned long long);
   o.raw = 0;
   size_t off = align_up(raw_bytes > exch_bytes ? raw_bytes : exch_bytes, 128);
   o.xdig = off;
-  off = align_up(off + size_t(smax) * LP * digit_bytes, 16);
+  off = align_up(off + size_t(smax) * x_stride(L, intv) * digit_bytes, 16);
   o.ydig = off;
-  off = align_up(off + size_t(smax) * LP * digit_bytes, 16);
+  off = align_up(off + size_t(smax) * y_stride(L, intv) * digit_bytes, 16);
   o.gx = off;
   off += size_t(smax) * 4;
   o.gy = off;
@@ -174,11 +184,13 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
   using AccT = typename std::conditional<INTV, long long, double>::type;
   constexpr int L = digits_for_k(K);
-  constexpr int LP = L | 1;
-  constexpr int R = 128 / L;  // FP64 accumulators stay exact for R terms
+  constexpr int XS = x_stride(L, INTV);
+  constexpr int YS = y_stride(L, INTV);
+  constexpr int XOFF = INTV ? L : 0;  // digits start after the zero prefix
+  constexpr int R = 128 / L;          // FP64 accumulators stay exact for R terms
 
   extern __shared__ __align__(128) unsigned char smem[];
-  const DagLayout lay = dag_layout(K, L, sizeof(DigitT), a.smax, a.dmax);
+  const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax);
   double* raw = reinterpret_cast<double*>(smem + lay.raw);
   unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.raw);
   DigitT* xdig = reinterpret_cast<DigitT*>(smem + lay.xdig);
@@ -195,6 +207,10 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
   if (tid == 0) {
     mbar_init(bar_addr, 1);
     fence_mbar_init();
+  }
+  if constexpr (INTV) {
+    // zero prefixes of the X rows (the conversions only write the digit part)
+    for (int t = tid; t < a.smax * XS; t += T) xdig[t] = 0;
   }
   __syncthreads();
   const int epoch = *reinterpret_cast<volatile int32_t*>(&a.ctrl->epoch);
@@ -251,12 +267,12 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
       to_digits<K, L>(raw + c, S, g1, D);
       gx[c] = g1;
 #pragma unroll
-      for (int p = 0; p < L; ++p) xdig[c * LP + p] = static_cast<DigitT>(D[p]);
+      for (int p = 0; p < L; ++p) xdig[c * XS + XOFF + p] = static_cast<DigitT>(D[p]);
       const int32_t g2 = grid_of(raw[K * S + c]);
       to_digits<K, L>(raw + K * S + c, S, g2, D);
       gy[c] = g2;
 #pragma unroll
-      for (int p = 0; p < L; ++p) ydig[c * LP + p] = static_cast<DigitT>(D[p]);
+      for (int p = 0; p < L; ++p) ydig[c * YS + p] = static_cast<DigitT>(D[p]);
     }
     __syncthreads();
 
@@ -311,30 +327,42 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
         const int ix = conv ? i : j + i;
         const int iy = conv ? j - i : i;
         const int delta = gsj - gx[ix] - gy[iy];
-        const DigitT* yr = ydig + iy * LP;
-        const DigitT* xr = xdig + ix * LP;
-        if (__all_sync(__activemask(), delta == 0)) {
-          // common case: every lane's term is aligned with its reference grid
-          DigitT Y[L];
+        if constexpr (INTV) {
+          if (delta < L) {
+            // zero prefix: digit p of the shifted term is xs[p], no select
+            const int32_t* xs = xdig + ix * XS + XOFF - delta;
+            const int4* y4 = reinterpret_cast<const int4*>(ydig + iy * YS);
+            int32_t Y[YS];
 #pragma unroll
-          for (int q = 0; q < L; ++q) Y[q] = yr[q];
+            for (int v = 0; v < YS / 4; ++v) {
+              const int4 t4 = y4[v];
+              Y[4 * v] = t4.x;
+              Y[4 * v + 1] = t4.y;
+              Y[4 * v + 2] = t4.z;
+              Y[4 * v + 3] = t4.w;
+            }
 #pragma unroll
-          for (int p = 0; p < L; ++p) {
-            const DigitT xv = xr[p];
+            for (int p = 0; p < L; ++p) {
+              const int32_t xv = xs[p];
 #pragma unroll
-            for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+              for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+            }
           }
-        } else if (delta < L) {
-          DigitT Y[L];
+        } else {
+          if (delta < L) {
+            const DigitT* yr = ydig + iy * YS;
+            const DigitT* xr = xdig + ix * XS;
+            DigitT Y[L];
 #pragma unroll
-          for (int q = 0; q < L; ++q) Y[q] = yr[q];
+            for (int q = 0; q < L; ++q) Y[q] = yr[q];
 #pragma unroll
-          for (int p = 0; p < L; ++p) {
-            const int id = p - delta;
-            DigitT xv = xr[id < 0 ? 0 : id];
-            xv = id < 0 ? DigitT(0) : xv;
+            for (int p = 0; p < L; ++p) {
+              const int id = p - delta;
+              DigitT xv = xr[id < 0 ? 0 : id];
+              xv = id < 0 ? DigitT(0) : xv;
 #pragma unroll
-            for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+              for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+            }
           }
         }
         ++i;
@@ -553,8 +581,7 @@ void* dag_kernel_ptr(int k, int arith) {
 int digits_of_k(int k) { return digits_for_k(k); }
 
 size_t dag_smem_bytes(int k, int arith, int smax, int dmax) {
-  const int digit_bytes = arith == ARITH_INT ? 4 : 8;
-  return dag_layout(k, digits_for_k(k), digit_bytes, smax, dmax).total;
+  return dag_layout(k, digits_for_k(k), arith == ARITH_INT, smax, dmax).total;
 }
 
 cudaError_t dag_prepare(int k, int arith, size_t smem) {
