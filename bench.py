@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--arith", choices=["fp64", "int"], default="fp64")
-    ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["p2", "p1", "p3"], default="p2",
@@ -79,11 +79,10 @@ def dp_equiv_ops(conv_jobs, add_jobs, d, k):
     return conv_jobs * per_conv + add_jobs * (d + 1) * ca
 
 
-def digit_fma_flops(conv_jobs, d, k):
-    """FP64 flops of the exact digit products the convolution kernel executes:
-    L(L+1)/2 FMAs (2 flops) per term, (d+1)(d+2)/2 terms per convolution."""
-    from paper_2101_10881_gb300 import pes  # noqa: F401
-    L = (53 * k + 28 + 23) // 24 + 1
+def digit_fma_flops(conv_jobs, d, digits):
+    """Flops (2 per multiply-add) of the exact digit products the convolution
+    kernel executes: L(L+1)/2 per term, (d+1)(d+2)/2 terms per convolution."""
+    L = digits
     return conv_jobs * (d + 1) * (d + 2) // 2 * (L * (L + 1) // 2) * 2
 
 
@@ -309,7 +308,7 @@ def ours_arm(args, world, rank, local):
     int_peak = pes.int_peak(repeats=7)
 
     ops_step = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], prob.d, prob.k)
-    digit_flops = digit_fma_flops(info["conv_jobs"], prob.d, prob.k)
+    digit_flops = digit_fma_flops(info["conv_jobs"], prob.d, info["digits"])
 
     for _ in range(max(args.warmup, 3)):
         plan.eval_grad(C, Z, V, G)

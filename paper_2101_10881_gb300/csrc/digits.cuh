@@ -3,12 +3,13 @@
 // A k-double number x (limbs x[0..k-1], nonoverlapping, |x[0]| largest) is
 // written on a grid g (an integer) as
 //     x ~= 2^(B g) * sum_{p=0..L-1} X_p 2^(-B (p+1)),   |X_p| <= 2^(B-1),
-// with B = 24-bit balanced digits X_p.  Products of two digits are at most 2^46
-// in magnitude, so they are exact in a double and in an int64, and sums of up to
-// 128 of them stay exact in a double (2^53), which is what makes the
-// multiply-accumulate loop of a truncated series product (Eq. eqconvform) an
-// error-free transformation: every term x_i y_{j-i} is accumulated exactly into
-// digit positions, and the sum is rounded once to k limbs at the end.
+// with B-bit balanced digits X_p.  With B = 24, products of two digits are at
+// most 2^46 in magnitude, exact in a double, and sums of up to 128 of them stay
+// exact in a double (2^53); with B = 28 products are below 2^54 and sums of 512
+// of them stay exact in an int64.  That is what makes the multiply-accumulate
+// loop of a truncated series product (Eq. eqconvform) an error-free
+// transformation: every term x_i y_{j-i} is accumulated exactly into digit
+// positions, and the sum is rounded once to k limbs at the end.
 //
 // The number of digits L per k is chosen so that the dropped tail of every term
 // is below 2^-(53k+12) of the largest term (see digits_for_k).
@@ -48,19 +49,18 @@ PES_HD int clz64(uint64_t x) {
 #endif
 }
 
+// Digit width B: 24 bits for FP64 accumulation (digit products below 2^46, sums
+// of 128 of them exact in a double), 28 bits for 64-bit integer accumulation
+// (products below 2^54, sums of 512 of them exact in an int64).
 constexpr int DIGIT_BITS = 24;
-constexpr int64_t DIGIT_BASE = int64_t(1) << DIGIT_BITS;
-constexpr int64_t DIGIT_HALF = int64_t(1) << (DIGIT_BITS - 1);
-constexpr int64_t DIGIT_MASK = DIGIT_BASE - 1;
+constexpr int DIGIT_BITS_INT = 28;
 // grid of a zero coefficient: far below any real grid so that every term with
 // it is skipped
 constexpr int32_t GRID_ZERO = -(1 << 28);
 
 // L: smallest number of digits with B (L - 1) >= 53 k + 28 (12 guard bits plus
 // log2 of (1024 terms x 40 digit products)), see the error budget above.
-PES_HDC int digits_for_k(int k) {
-  return (53 * k + 28 + DIGIT_BITS - 1) / DIGIT_BITS + 1;
-}
+PES_HDC int digits_for_k(int k, int B = DIGIT_BITS) { return (53 * k + 28 + B - 1) / B + 1; }
 
 PES_HD int32_t floordiv(int32_t a, int32_t b) {
   int32_t q = a / b;
@@ -87,24 +87,26 @@ PES_HD bool decode(double x, int& neg, uint64_t& mant, int32_t& lsb) {
 
 // Grid of a k-double whose leading limb is x0: g = ceil((e + 2) / B) where
 // |x| <= 2^e, so that |x| <= 2^(B g - 2).
+template <int B = DIGIT_BITS>
 PES_HD int32_t grid_of(double x0) {
   uint64_t bits = dbits(x0);
   uint32_t be = static_cast<uint32_t>((bits >> 52) & 0x7FF);
   if ((bits << 1) == 0) return GRID_ZERO;
   int32_t e = (be == 0 ? 1 : static_cast<int32_t>(be)) - 1022;  // |x0| < 2^e
-  return floordiv(e + 2 + DIGIT_BITS - 1, DIGIT_BITS);
+  return floordiv(e + 2 + B - 1, B);
 }
 
 // Signed piece of limb (neg, mant, lsb) inside the digit window whose lsb is at
 // absolute bit position P (bits [P, P + B)), truncated toward zero.
+template <int B>
 PES_HD int64_t window(int neg, uint64_t mant, int32_t lsb, int32_t P) {
   int32_t sh = P - lsb;
   uint64_t v;
   if (sh >= 0)
     v = sh >= 64 ? 0 : (mant >> sh);
   else
-    v = (-sh) >= DIGIT_BITS ? 0 : (mant << (-sh));
-  int64_t piece = static_cast<int64_t>(v & static_cast<uint64_t>(DIGIT_MASK));
+    v = (-sh) >= B ? 0 : (mant << (-sh));
+  int64_t piece = static_cast<int64_t>(v & ((uint64_t(1) << B) - 1));
   return neg ? -piece : piece;
 }
 
@@ -112,11 +114,11 @@ PES_HD int64_t window(int neg, uint64_t mant, int32_t lsb, int32_t P) {
 // x[l * ls].  Each limb's 53 bits fall into at most four consecutive digit
 // windows, so only those are touched (D is indexed at run time).  Bits below the
 // last digit are dropped.
-template <int K, int L>
+template <int K, int L, int B = DIGIT_BITS>
 PES_HD void to_digits(const double* x, long long ls, int32_t g, int64_t (&D)[L]) {
 #pragma unroll
   for (int p = 0; p < L; ++p) D[p] = 0;
-  const int32_t top = DIGIT_BITS * g;  // bit position just above digit 0
+  const int32_t top = B * g;  // bit position just above digit 0
 #pragma unroll 1
   for (int l = 0; l < K; ++l) {
     int neg;
@@ -124,20 +126,20 @@ PES_HD void to_digits(const double* x, long long ls, int32_t g, int64_t (&D)[L])
     int32_t lsb;
     if (!decode(x[l * ls], neg, mant, lsb)) continue;
     const int32_t hb = lsb + 52;  // highest bit of the limb (mantissas of normal numbers)
-    int32_t p0 = floordiv(top - 1 - hb, DIGIT_BITS);
+    int32_t p0 = floordiv(top - 1 - hb, B);
     if (p0 < 0) p0 = 0;
     if (p0 >= L) break;  // this limb and every smaller one lie below the last digit
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int p = p0 + r;
-      if (p < L) D[p] += window(neg, mant, lsb, top - DIGIT_BITS * (p + 1));
+      if (p < L) D[p] += window<B>(neg, mant, lsb, top - B * (p + 1));
     }
   }
   // balanced digits: carry from the bottom up
 #pragma unroll
   for (int p = L - 1; p >= 1; --p) {
-    int64_t c = (D[p] + DIGIT_HALF) >> DIGIT_BITS;
-    D[p] -= c << DIGIT_BITS;
+    int64_t c = (D[p] + (int64_t(1) << (B - 1))) >> B;
+    D[p] -= c << B;
     D[p - 1] += c;
   }
 }
@@ -150,15 +152,15 @@ PES_HD void to_digits(const double* x, long long ls, int32_t g, int64_t (&D)[L])
 // magnitude is packed into 64-bit words; each limb takes the 53 bits below the
 // highest set bit, rounded; the remainder is V with those bits cleared, or, when
 // the limb was rounded up, 2^mexp minus the bits below mexp with the sign flipped.
-template <int K, int L>
+template <int K, int L, int B = DIGIT_BITS>
 PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long ls) {
   constexpr int NA = L + 1;
-  constexpr int NW = (DIGIT_BITS * L + 64 + 63) / 64 + 1;  // digit 0 holds < 2^40
+  constexpr int NW = (B * L + 64 + 63) / 64 + 1;  // digit 0 holds < 2^44
   auto normalise = [&]() {
 #pragma unroll
     for (int a = NA - 1; a >= 1; --a) {
-      int64_t c = E[a] >> DIGIT_BITS;
-      E[a] -= c << DIGIT_BITS;
+      int64_t c = E[a] >> B;
+      E[a] -= c << B;
       E[a - 1] += c;
     }
   };
@@ -176,13 +178,13 @@ PES_HD void from_digits(int64_t (&E)[L + 1], int32_t gs, double* out, long long 
   for (int w = 0; w < NW; ++w) Wd[w] = 0;
 #pragma unroll
   for (int a = 0; a < NA; ++a) {
-    const int pos = DIGIT_BITS * (L - a);
+    const int pos = B * (L - a);
     const int w = pos / 64, o = pos % 64;
     const uint64_t v = static_cast<uint64_t>(E[a]);
     Wd[w] |= v << o;
     if (o > 0 && w + 1 < NW) Wd[w + 1] |= v >> (64 - o);
   }
-  const int32_t base_exp = DIGIT_BITS * gs - DIGIT_BITS * (L + 1);
+  const int32_t base_exp = B * gs - B * (L + 1);
 #pragma unroll 1
   for (int l = 0; l < K; ++l) {
     int tw = -1;

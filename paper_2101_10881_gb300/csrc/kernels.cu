@@ -180,14 +180,17 @@ __device__ __forceinline__ long long conv_start(long long j) { return j * (j + 1
 __device__ __forceinline__ long long corr_start(long long j, long long d) { return j * (d + 1) - j * (j - 1) / 2; }
 
 template <int K, bool INTV>
-__global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
+__global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
   using AccT = typename std::conditional<INTV, long long, double>::type;
-  constexpr int L = digits_for_k(K);
+  constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
+  constexpr int L = digits_for_k(K, B);
   constexpr int XS = x_stride(L, INTV);
   constexpr int YS = y_stride(L, INTV);
   constexpr int XOFF = INTV ? L : 0;  // digits start after the zero prefix
-  constexpr int R = 128 / L;          // FP64 accumulators stay exact for R terms
+  // accumulators stay exact for R terms (each term adds at most L products of
+  // magnitude 2^(2B-2)): 2^53 for FP64, 2^63 for int64
+  constexpr int R = INTV ? static_cast<int>((1LL << (63 - 2 * (B - 1))) / L) : 128 / L;
 
   extern __shared__ __align__(128) unsigned char smem[];
   const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax);
@@ -233,6 +236,10 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
     const ConvJob jb = a.jobs[job];
     const InstInfo in = a.inst[jb.inst];
     const int d = in.d;
+    if (INTV && d + 1 > T) {  // one lane per output coefficient: the plan sizes the CTA for its largest degree
+      if (tid == 0) set_error(a.ctrl, 6, job, d);
+      break;
+    }
     const int S = in.S;
     const long long ls = in.ws_lstride;
     const double* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * S;
@@ -263,13 +270,13 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
     // ---- exact digits of every staged coefficient ----
     for (int c = tid; c <= d; c += T) {
       int64_t D[L];
-      const int32_t g1 = grid_of(raw[c]);
-      to_digits<K, L>(raw + c, S, g1, D);
+      const int32_t g1 = grid_of<B>(raw[c]);
+      to_digits<K, L, B>(raw + c, S, g1, D);
       gx[c] = g1;
 #pragma unroll
       for (int p = 0; p < L; ++p) xdig[c * XS + XOFF + p] = static_cast<DigitT>(D[p]);
-      const int32_t g2 = grid_of(raw[K * S + c]);
-      to_digits<K, L>(raw + K * S + c, S, g2, D);
+      const int32_t g2 = grid_of<B>(raw[K * S + c]);
+      to_digits<K, L, B>(raw + K * S + c, S, g2, D);
       gy[c] = g2;
 #pragma unroll
       for (int p = 0; p < L; ++p) ydig[c * YS + p] = static_cast<DigitT>(D[p]);
@@ -290,26 +297,9 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
     }
     __syncthreads();
 
-    // ---- multiply-accumulate: every thread runs the same number of terms ----
+    // ---- multiply-accumulate ----
     {
       const bool conv = jb.kind == JOB_CONV;
-      const long long W = static_cast<long long>(d + 1) * (d + 2) / 2;
-      const long long g0 = W * tid / T;
-      const long long g1 = W * (tid + 1) / T;
-      const int cnt = static_cast<int>(g1 - g0);
-      int j = 0, i = 0;
-      if (cnt > 0) {
-        int lo = 0, hi = d;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          const long long st = conv ? conv_start(mid) : corr_start(mid, d);
-          if (st <= g0) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
-        i = static_cast<int>(g0 - (conv ? conv_start(j) : corr_start(j, d)));
-      }
-      int nt = conv ? j + 1 : d - j + 1;
-      int gsj = cnt > 0 ? gs[j] : 0;
       AccT A[L];
 #pragma unroll
       for (int t = 0; t < L; ++t) A[t] = 0;
@@ -323,10 +313,8 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
           A[t] = 0;
         }
       };
-      for (int s = 0; s < cnt; ++s) {
-        const int ix = conv ? i : j + i;
-        const int iy = conv ? j - i : i;
-        const int delta = gsj - gx[ix] - gy[iy];
+      // one term x_ix * y_iy of output coefficient j, delta digits below its grid
+      auto term = [&](int ix, int iy, int delta) {
         if constexpr (INTV) {
           if (delta < L) {
             // zero prefix: digit p of the shifted term is xs[p], no select
@@ -365,21 +353,83 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
             }
           }
         }
-        ++i;
-        const bool end_coef = (i == nt);
-        bool do_flush = end_coef;
-        if constexpr (!INTV) do_flush = do_flush || ((s + 1) % R == 0);
-        if (do_flush) flush(j);
-        if (end_coef) {
-          ++j;
-          i = 0;
-          if (j <= d) {
-            nt = conv ? j + 1 : d - j + 1;
-            gsj = gs[j];
+      };
+      if constexpr (INTV) {
+        // Coefficients j and d-j share d+2 terms; the two lanes of a pair split
+        // them so that every lane runs about (d+2)/2 terms and all lanes step
+        // the term index together (X rows are read as broadcasts, Y rows
+        // consecutively).  Lane A: the short coefficient, then the long one from
+        // its last term backwards; lane B: the long one from its first term.
+        const int P = (d + 1) / 2;                 // pairs
+        const bool has_mid = ((d + 1) & 1) != 0;   // the middle coefficient d/2 pairs with itself
+        const int h = (d + 3) / 2;                 // steps of lane A
+        const int l = tid >> 1;
+        int role = 3;                              // 0 A, 1 B, 2 middle, 3 idle
+        if (tid < 2 * P) role = tid & 1;
+        else if (has_mid && tid == 2 * P) role = 2;
+        const int cs = conv ? l : d - l;           // short coefficient: l + 1 terms
+        const int cl = conv ? d - l : l;           // long coefficient: d - l + 1 terms
+        const int ns = l + 1, nl = d - l + 1;
+        const int steps = role == 0 ? h : role == 1 ? d + 2 - h : role == 2 ? d / 2 + 1 : 0;
+        int jcur = role == 1 ? cl : role == 2 ? d / 2 : cs;
+        for (int s = 0; s < steps; ++s) {
+          int j, i;
+          if (role == 0) {
+            if (s < ns) { j = cs; i = s; } else { j = cl; i = nl - 1 - (s - ns); }
+          } else {
+            j = jcur;
+            i = s;
+          }
+          const int ix = conv ? i : j + i;
+          const int iy = conv ? j - i : i;
+          term(ix, iy, gs[j] - gx[ix] - gy[iy]);
+          if (role == 0 && s == ns - 1) {
+            flush(cs);  // lane A leaves its short coefficient
+            jcur = cl;
+          } else if ((s + 1) % R == 0) {
+            flush(jcur);
           }
         }
+        if (steps > 0) flush(jcur);
+      } else {
+        // Every thread runs the same number of consecutive terms of the
+        // concatenated term sequence; partial sums of a coefficient split between
+        // threads meet exactly in the shared exchange row.
+        const long long W = static_cast<long long>(d + 1) * (d + 2) / 2;
+        const long long g0 = W * tid / T;
+        const long long g1 = W * (tid + 1) / T;
+        const int cnt = static_cast<int>(g1 - g0);
+        int j = 0, i = 0;
+        if (cnt > 0) {
+          int lo = 0, hi = d;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const long long st = conv ? conv_start(mid) : corr_start(mid, d);
+            if (st <= g0) lo = mid; else hi = mid - 1;
+          }
+          j = lo;
+          i = static_cast<int>(g0 - (conv ? conv_start(j) : corr_start(j, d)));
+        }
+        int nt = conv ? j + 1 : d - j + 1;
+        int gsj = cnt > 0 ? gs[j] : 0;
+        for (int s = 0; s < cnt; ++s) {
+          const int ix = conv ? i : j + i;
+          const int iy = conv ? j - i : i;
+          term(ix, iy, gsj - gx[ix] - gy[iy]);
+          ++i;
+          const bool end_coef = (i == nt);
+          if (end_coef || ((s + 1) % R == 0)) flush(j);
+          if (end_coef) {
+            ++j;
+            i = 0;
+            if (j <= d) {
+              nt = conv ? j + 1 : d - j + 1;
+              gsj = gs[j];
+            }
+          }
+        }
+        if (i > 0) flush(j);
       }
-      if (i > 0) flush(j);
     }
     __syncthreads();
 
@@ -394,7 +444,7 @@ __global__ void __launch_bounds__(256, 1) dag_kernel(DagArgs a) {
       int64_t E[L + 1];
 #pragma unroll
       for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
-      from_digits<K, L>(E, g, zs + j, ls);
+      from_digits<K, L, B>(E, g, zs + j, ls);
     }
     __syncthreads();
     if (tid == 0) {
@@ -578,10 +628,10 @@ void* dag_kernel_ptr(int k, int arith) {
 
 }  // namespace
 
-int digits_of_k(int k) { return digits_for_k(k); }
+int digits_of_k(int k, int arith) { return digits_for_k(k, arith == ARITH_INT ? DIGIT_BITS_INT : DIGIT_BITS); }
 
 size_t dag_smem_bytes(int k, int arith, int smax, int dmax) {
-  return dag_layout(k, digits_for_k(k), arith == ARITH_INT, smax, dmax).total;
+  return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax).total;
 }
 
 cudaError_t dag_prepare(int k, int arith, size_t smem) {

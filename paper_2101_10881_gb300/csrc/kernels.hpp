@@ -57,9 +57,13 @@ struct CopyArgs {
   double* dst[4];        // unpack: caller buffers by selector
 };
 
+// Threads per CTA of the DAG kernel: one lane per output coefficient, so at
+// least d+1; the register budget of each k caps it.
+__host__ __device__ constexpr int dag_max_threads(int k) { return k >= 8 ? 384 : k >= 4 ? 512 : 768; }
+
 // Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax).
 size_t dag_smem_bytes(int k, int arith, int smax, int dmax);
-int digits_of_k(int k);
+int digits_of_k(int k, int arith);
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_prologue(Ctrl* ctrl, cudaStream_t st);

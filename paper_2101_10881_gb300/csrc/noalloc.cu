@@ -164,7 +164,8 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   STATIC_CUDA(cudaGetDevice(&dev));
   STATIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   STATIC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int arith = pes::ARITH_FP64, threads = 128;
+  const int arith = pes::ARITH_FP64;
+  const int threads = 128;
   const size_t smem = pes::dag_smem_bytes(k, arith, S, d);
   if (smem > static_cast<size_t>(optin)) {
     set_error("degree too large for the shared-memory staging");

@@ -145,6 +145,16 @@ struct Exec {
     PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int optin = 0;
     PES_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    // integer variant: one lane per output coefficient of the largest degree,
+    // whole warps; FP64 variant: 128 threads share the terms evenly
+    if (arith == pes::ARITH_INT)
+      threads = std::max(threads, (dmax + 1 + 31) / 32 * 32);
+    else if (threads == 0)
+      threads = 128;
+    if (threads > pes::dag_max_threads(k))
+      return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(threads) +
+                                             " threads per CTA; at most " + std::to_string(pes::dag_max_threads(k)) +
+                                             " at k=" + std::to_string(k));
     smem = pes::dag_smem_bytes(k, arith, smax, dmax);
     if (smem > static_cast<size_t>(optin))
       return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(smem) +
@@ -259,8 +269,8 @@ pes_status parse_options(const pes_options* opt, pes_options& o) {
   pes_default_options(&o);
   if (opt) o = *opt;
   if (o.arith != PES_ARITH_FP64 && o.arith != PES_ARITH_INT) return fail(PES_EINVAL, "arith must be 0 or 1");
-  if (o.threads == 0) o.threads = 128;
-  if (o.threads != 128 && o.threads != 256) return fail(PES_EINVAL, "threads must be 128 or 256");
+  if (o.threads < 0 || o.threads > 1024 || o.threads % 32 != 0)
+    return fail(PES_EINVAL, "threads must be 0 (automatic) or a multiple of 32 up to 1024");
   if (o.ctas_per_sm < 0) return fail(PES_EINVAL, "ctas_per_sm must be >= 0");
   return PES_OK;
 }
@@ -299,7 +309,7 @@ struct pes_plan_s {
 extern "C" void pes_default_options(pes_options* opt) {
   if (!opt) return;
   opt->arith = PES_ARITH_FP64;
-  opt->threads = 128;
+  opt->threads = 0;
   opt->ctas_per_sm = 0;
   opt->with_vjp = 1;
   opt->timeout_ms = 60000;
@@ -479,7 +489,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->workspace_bytes = plan->ws_bytes;
   info->vjp_conv_jobs = plan->with_vjp ? G.vjp_fwd_jobs - static_cast<int64_t>(G.jobs.size()) : 0;
   info->vjp_corr_jobs = plan->with_vjp ? static_cast<int64_t>(G.vjp_jobs.size()) - G.vjp_fwd_jobs : 0;
-  info->digits = pes::digits_of_k(plan->ex.k);
+  info->digits = pes::digits_of_k(plan->ex.k, plan->ex.arith);
   info->grid = plan->fwd.grid;
   info->threads = plan->ex.threads;
   info->smem_bytes = static_cast<int32_t>(plan->ex.smem);
@@ -685,7 +695,7 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->add_terms = batch->add_terms;
   info->add_jobs = batch->add_jobs;
   info->workspace_bytes = static_cast<int64_t>(batch->ex.ws_doubles * sizeof(double));
-  info->digits = pes::digits_of_k(batch->ex.k);
+  info->digits = pes::digits_of_k(batch->ex.k, batch->ex.arith);
   info->grid = batch->fwd.grid;
   info->threads = batch->ex.threads;
   info->smem_bytes = static_cast<int32_t>(batch->ex.smem);

@@ -150,7 +150,7 @@ def _ptr(t, shape, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_options(arith="fp64", threads=128, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False):
+def make_options(arith="fp64", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False):
     o = Options()
     lib().pes_default_options(ctypes.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)

@@ -11,19 +11,19 @@ using namespace pes;
 
 namespace {
 
-template <int K>
+template <int K, int B>
 void conv_k(int d, const double* x, const double* y, double* z, int corr) {
-  constexpr int L = digits_for_k(K);
+  constexpr int L = digits_for_k(K, B);
   const int S = d + 1;
   std::vector<int32_t> gx(S), gy(S);
   std::vector<int64_t> X(static_cast<size_t>(S) * L), Y(static_cast<size_t>(S) * L);
   for (int c = 0; c < S; ++c) {
     int64_t D[L];
-    gx[c] = grid_of(x[c]);
-    to_digits<K, L>(x + c, S, gx[c], D);
+    gx[c] = grid_of<B>(x[c]);
+    to_digits<K, L, B>(x + c, S, gx[c], D);
     for (int p = 0; p < L; ++p) X[c * L + p] = D[p];
-    gy[c] = grid_of(y[c]);
-    to_digits<K, L>(y + c, S, gy[c], D);
+    gy[c] = grid_of<B>(y[c]);
+    to_digits<K, L, B>(y + c, S, gy[c], D);
     for (int p = 0; p < L; ++p) Y[c * L + p] = D[p];
   }
   for (int j = 0; j <= d; ++j) {
@@ -48,7 +48,7 @@ void conv_k(int d, const double* x, const double* y, double* z, int corr) {
         for (int q = 0; q < L - p; ++q) E[p + q + 1] += xv * Y[iy * L + q];
       }
     }
-    from_digits<K, L>(E, gs, z + j, S);
+    from_digits<K, L, B>(E, gs, z + j, S);
   }
 }
 
@@ -84,10 +84,18 @@ void sum_k(int count, const double* v, double* out) {
     default: return 1;        \
   }
 
-extern "C" int hd_conv(int k, int d, const double* x, const double* y, double* z, int corr) {
-#define C(K) conv_k<K>(d, x, y, z, corr)
-  DISPATCH(k, C)
+extern "C" int hd_conv(int k, int d, const double* x, const double* y, double* z, int corr, int bits) {
+  if (bits == 24) {
+#define C(K) conv_k<K, 24>(d, x, y, z, corr)
+    DISPATCH(k, C)
 #undef C
+  } else if (bits == 28) {
+#define C(K) conv_k<K, 28>(d, x, y, z, corr)
+    DISPATCH(k, C)
+#undef C
+  } else {
+    return 1;
+  }
   return 0;
 }
 

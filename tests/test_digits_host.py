@@ -30,7 +30,7 @@ def dh():
         subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", LIB, SRC], check=True)
     lib = ctypes.CDLL(LIB)
     dp = ctypes.POINTER(ctypes.c_double)
-    lib.hd_conv.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    lib.hd_conv.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int]
     lib.hd_sum.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
     return lib
 
@@ -39,11 +39,11 @@ def _p(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def host_conv(dh, x, y, corr=False):
+def host_conv(dh, x, y, corr=False, bits=24):
     x = np.ascontiguousarray(x)
     y = np.ascontiguousarray(y)
     z = np.empty_like(x)
-    assert dh.hd_conv(x.shape[0], x.shape[1] - 1, _p(x), _p(y), _p(z), int(corr)) == 0
+    assert dh.hd_conv(x.shape[0], x.shape[1] - 1, _p(x), _p(y), _p(z), int(corr), bits) == 0
     return z
 
 
@@ -57,22 +57,24 @@ def normalised(limbs):
     return True
 
 
+@pytest.mark.parametrize("bits", [24, 28])
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("d", [0, 1, 8, 40])
-def test_conv_matches_oracle(dh, k, d):
+def test_conv_matches_oracle(dh, k, d, bits):
     rng = np.random.default_rng(10 * k + d)
     x = random_md(rng, k, (d + 1,))
     y = random_md(rng, k, (d + 1,))
     for corr in (False, True):
-        z = host_conv(dh, x, y, corr)
+        z = host_conv(dh, x, y, corr, bits)
         r = O.corr(x, y) if corr else O.conv(x, y)
         assert normwise_err(z, r) <= TOL[k] * 1e-3
         for j in range(d + 1):
             assert normalised(z[:, j])
 
 
+@pytest.mark.parametrize("bits", [24, 28])
 @pytest.mark.parametrize("k", [1, 2, 4, 8, 10])
-def test_conv_wide_dynamic_range(dh, k):
+def test_conv_wide_dynamic_range(dh, k, bits):
     """Coefficients spanning hundreds of binary orders and exact zeros."""
     rng = np.random.default_rng(77 + k)
     d = 30
@@ -80,7 +82,7 @@ def test_conv_wide_dynamic_range(dh, k):
     y = random_md(rng, k, (d + 1,)) * np.ldexp(1.0, rng.integers(-300, 300, size=d + 1))
     x[:, rng.integers(0, d + 1, size=5)] = 0.0
     y[:, rng.integers(0, d + 1, size=5)] = 0.0
-    z = host_conv(dh, x, y)
+    z = host_conv(dh, x, y, bits=bits)
     r = O.conv(x, y)
     assert normwise_err(z, r) <= TOL[k] * 1e-3
 

@@ -79,12 +79,14 @@ def test_small_random_polynomials(torch, k, d):
     rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
     assert normwise_err(v, rv) <= TOL[k]
     assert normwise_err(g, rg) <= TOL[k]
-    # both multiply-accumulate variants are exact, so they agree bit for bit
-    assert np.array_equal(v, vi) and np.array_equal(g, gi)
+    # both variants accumulate exactly; they differ only in the digit width that
+    # drops the bits far below the k-th limb (24 vs 28 bits)
+    assert normwise_err(vi, rv) <= TOL[k] and normwise_err(gi, rg) <= TOL[k]
+    assert normwise_err(v, vi) <= TOL[k] and normwise_err(g, gi) <= TOL[k]
     assert normalised(v) and normalised(g)
 
 
-@pytest.mark.parametrize("threads", [128, 256])
+@pytest.mark.parametrize("threads", [0, 256])
 def test_ragged_degree_several_tiles(torch, threads):
     """d = 152: 153 coefficients (a ragged last warp), k = 4, monomials of up to
     5 variables, an unused variable and a one-variable monomial."""
@@ -270,4 +272,7 @@ def test_invalid_arguments(torch):
     assert e.value.code == 1
     with pytest.raises(pes.PesError) as e:
         pes.Plan([[0]], 1, 4000, 2)
+    assert e.value.code == 7
+    with pytest.raises(pes.PesError) as e:
+        pes.Plan([[0]], 1, 400, 10)  # one lane per coefficient: at most 384 threads at k=10
     assert e.value.code == 7
