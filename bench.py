@@ -48,7 +48,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--arith", choices=["fp64", "int"], default="fp64")
+    ap.add_argument("--arith", choices=["auto", "fp64", "int"], default="auto",
+                    help="multiply-accumulate pipe of the headline run (auto: integer when the degree allows)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the extra kernel-only timing of the FP64 variant")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -250,7 +253,7 @@ def workload_config(prob, args):
     return {"workload": f"{shape} polynomial n={prob.n} N={prob.N} monomials of {sizes[0] if len(sizes) == 1 else sizes} "
                         f"variables, d={prob.d}, k={prob.k}, value + full gradient per step",
             "global_batch": 1, "seq_len": prob.d + 1, "parallelism": f"replicas x{args.gpus}",
-            "arith": args.arith, "threads_per_cta": args.threads,
+            "arith": args.arith, "threads_per_cta": args.threads or "auto",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); workspace > L2"}
 
 
@@ -262,10 +265,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(conv_jobs_full):
+def traffic_per_launch(conv_jobs_full, arith):
     """DRAM bytes of one convolution launch from the committed ncu summary, if
     it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "dag_kernel_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"dag_kernel_{arith}_traffic.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -310,35 +313,39 @@ def ours_arm(args, world, rank, local):
     ops_step = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], prob.d, prob.k)
     digit_flops = digit_fma_flops(info["conv_jobs"], prob.d, info["digits"])
 
-    for _ in range(max(args.warmup, 3)):
-        plan.eval_grad(C, Z, V, G)
-    torch.cuda.synchronize(dev)
-    plan.check()
+    def timed(p, steps):
+        """Device-resident steps with an L2 flush between them; per-step and
+        convolution-kernel milliseconds from CUDA events on the launching stream."""
+        for _ in range(max(args.warmup, 3)):
+            p.eval_grad(C, Z, V, G)
+        torch.cuda.synchronize(dev)
+        p.check()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        sms, cms, nl = [], [], 0
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.eval_grad(C, Z, V, G)
+            e1.record(stream)
+            e1.synchronize()
+            sms.append(e0.elapsed_time(e1))
+            t = p.last_timing()
+            cms.append(t["conv_ms"])
+            nl += t["launches"]
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        p.check()
+        return sms, cms, nl
 
-    # ---- device-resident timed region ----
     clocks = ClockSampler(local)
-    barrier(world)
-    torch.cuda.synchronize(dev)
     clocks.start()
-    step_ms, conv_ms, launches = [], [], 0
     t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.eval_grad(C, Z, V, G)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        t = plan.last_timing()
-        conv_ms.append(t["conv_ms"])
-        launches += t["launches"]
-    torch.cuda.synchronize(dev)
+    step_ms, conv_ms, launches = timed(plan, args.steps)
     wall = time.perf_counter() - t_wall0
-    barrier(world)
     clk = clocks.stop()
-    plan.check()
     total_ms = max_over_ranks(sum(step_ms), world)
 
     # ---- end to end through the public API: pinned host buffers, copies timed ----
@@ -372,7 +379,8 @@ def ours_arm(args, world, rank, local):
     mean_conv = statistics.mean(conv_ms)
     work = (f"{info['conv_jobs']} convolutions x {(prob.d + 1) * (prob.d + 2) // 2} terms x "
             f"{info['digits'] * (info['digits'] + 1) // 2} digit products")
-    if args.arith == "fp64":
+    arith = info["arith_name"]
+    if arith == "fp64":
         achieved = digit_flops / (mean_conv * 1e-3) / 1e12
         roofline = {"bound": "alu", "pipe": "fp64 (DFMA)", "achieved": achieved, "peak": fp64_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp64_peak,
@@ -382,18 +390,35 @@ def ours_arm(args, world, rank, local):
         roofline = {"bound": "alu", "pipe": "int (IMAD.WIDE 32x32+64)", "achieved": achieved, "peak": int_peak,
                     "unit": "Tops/s", "frac": achieved / int_peak,
                     "peak_source": "measured: pes_int_peak multiply-add microbenchmark (burst, all SMs), this run"}
-    roofline.update({"traffic": traffic_per_launch(info["conv_jobs"]), "work": work, "kernel_ms": mean_conv})
+    roofline.update({"traffic": traffic_per_launch(info["conv_jobs"], arith), "work": work, "kernel_ms": mean_conv})
+
+    # ---- the other multiply-accumulate pipe, kernel-only, same workload ----
+    variants = {arith: {"ms_per_step": total_ms / args.steps, "value": value, "roofline_frac": roofline["frac"],
+                        "pipe": roofline["pipe"], "digits": info["digits"]}}
+    if not args.no_variants and arith == "int":
+        p64 = pes.Plan(prob.supports, prob.n, prob.d, prob.k, arith="fp64", with_vjp=False, profile=True)
+        i64 = p64.info()
+        sms, cms, _ = timed(p64, max(2, min(args.steps, 3)))
+        f64 = digit_fma_flops(i64["conv_jobs"], prob.d, i64["digits"])
+        ms64 = max_over_ranks(sum(sms), world) / len(sms)
+        variants["fp64"] = {"ms_per_step": ms64, "value": world * ops_step / (ms64 * 1e-3) / 1e12,
+                            "roofline_frac": f64 / (statistics.mean(cms) * 1e-3) / 1e12 / fp64_peak,
+                            "pipe": "fp64 (DFMA)", "digits": i64["digits"],
+                            "dp_equiv_over_fp64_peak": ops_step / (ms64 * 1e-3) / 1e12 / fp64_peak}
+        del p64
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(prob, args),
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64" if arith == "int" else "f64",
+        "data": "synthetic", "config": dict(workload_config(prob, args), arith_used=arith,
+                                            values="k-double series (k float64 limbs per coefficient)"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_total / args.steps},
         "roofline": roofline,
         "gpu_launches": launches,
         "clocks": clk,
         "dp_equiv_over_fp64_peak": value / world / fp64_peak,
+        "variants": variants,
         "peaks": {"fp64_tflops": fp64_peak, "int_mad_wide_tops": int_peak},
         "ops_per_step": ops_step,
         "wall_s_timed_region": wall,

@@ -54,13 +54,16 @@ typedef enum {
 typedef struct pes_plan_s* pes_plan_t;
 typedef struct pes_batch_s* pes_batch_t;
 
-/* Arithmetic of the convolution multiply-accumulate loop.  Both give the same
- * values: every output coefficient is the exact sum of its terms' digit
- * products, rounded once to k limbs. */
-enum { PES_ARITH_FP64 = 0, PES_ARITH_INT = 1 };
+/* Arithmetic of the convolution multiply-accumulate loop.  Both accumulate the
+ * digit products of every output coefficient exactly and round the sum once to
+ * k limbs (24-bit digits on the FP64 FMA pipe, 28-bit digits with 32x32->64-bit
+ * integer multiply-add); results agree to within the last limb's rounding.
+ * PES_ARITH_AUTO takes the integer pipe whenever the degree allows one thread
+ * per output coefficient (see PES_EUNSUPPORTED_SIZE), else the FP64 pipe. */
+enum { PES_ARITH_AUTO = -1, PES_ARITH_FP64 = 0, PES_ARITH_INT = 1 };
 
 typedef struct {
-  int32_t arith;       /* PES_ARITH_FP64 (default) or PES_ARITH_INT */
+  int32_t arith;       /* PES_ARITH_AUTO (default), PES_ARITH_FP64 or PES_ARITH_INT */
   int32_t threads;     /* threads per CTA of the convolution kernel: 0 = automatic (d+1 rounded up to
                           whole warps, one lane per output coefficient); else a larger multiple of 32 */
   int32_t ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit */
@@ -149,6 +152,8 @@ typedef struct {
   int32_t grid;            /* persistent CTAs of the convolution kernel */
   int32_t threads;         /* threads per CTA */
   int32_t smem_bytes;      /* dynamic shared memory per CTA */
+  int32_t arith;           /* PES_ARITH_FP64 or PES_ARITH_INT: the pipe the plan uses */
+  int32_t pad;
 } pes_plan_info;
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);

@@ -131,6 +131,11 @@ struct Exec {
   pes_status init(int32_t k_, const pes_options& o, const std::vector<pes::InstInfo>& insts, size_t ws_doubles_) {
     k = k_;
     arith = o.arith;
+    if (arith == PES_ARITH_AUTO) {
+      int dm = 0;
+      for (const auto& in : insts) dm = std::max(dm, in.d);
+      arith = (dm + 1 + 31) / 32 * 32 <= pes::dag_max_threads(k_) ? pes::ARITH_INT : pes::ARITH_FP64;
+    }
     threads = o.threads;
     ctas_per_sm = o.ctas_per_sm;
     timeout_ns = (o.timeout_ms > 0 ? o.timeout_ms : 60000) * 1000000LL;
@@ -268,7 +273,8 @@ struct Exec {
 pes_status parse_options(const pes_options* opt, pes_options& o) {
   pes_default_options(&o);
   if (opt) o = *opt;
-  if (o.arith != PES_ARITH_FP64 && o.arith != PES_ARITH_INT) return fail(PES_EINVAL, "arith must be 0 or 1");
+  if (o.arith != PES_ARITH_AUTO && o.arith != PES_ARITH_FP64 && o.arith != PES_ARITH_INT)
+    return fail(PES_EINVAL, "arith must be -1, 0 or 1");
   if (o.threads < 0 || o.threads > 1024 || o.threads % 32 != 0)
     return fail(PES_EINVAL, "threads must be 0 (automatic) or a multiple of 32 up to 1024");
   if (o.ctas_per_sm < 0) return fail(PES_EINVAL, "ctas_per_sm must be >= 0");
@@ -308,7 +314,7 @@ struct pes_plan_s {
 
 extern "C" void pes_default_options(pes_options* opt) {
   if (!opt) return;
-  opt->arith = PES_ARITH_FP64;
+  opt->arith = PES_ARITH_AUTO;
   opt->threads = 0;
   opt->ctas_per_sm = 0;
   opt->with_vjp = 1;
@@ -493,6 +499,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->grid = plan->fwd.grid;
   info->threads = plan->ex.threads;
   info->smem_bytes = static_cast<int32_t>(plan->ex.smem);
+  info->arith = plan->ex.arith;
   return PES_OK;
 }
 
@@ -699,6 +706,7 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->grid = batch->fwd.grid;
   info->threads = batch->ex.threads;
   info->smem_bytes = static_cast<int32_t>(batch->ex.smem);
+  info->arith = batch->ex.arith;
   return PES_OK;
 }
 

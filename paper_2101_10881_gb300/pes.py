@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpes.so")
 PES_OK = 0
 STATUS = {0: "PES_OK", 1: "PES_EINVAL", 2: "PES_EUNSUPPORTED_K", 3: "PES_ENOMEM", 4: "PES_ECUDA",
           5: "PES_ETIMEOUT", 6: "PES_EINTERNAL", 7: "PES_EUNSUPPORTED_SIZE"}
-ARITH = {"fp64": 0, "int": 1}
+ARITH = {"auto": -1, "fp64": 0, "int": 1}
 
 # every symbol that include/pes.h declares
 EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_destroy", "pes_eval_grad", "pes_vjp",
@@ -50,10 +50,12 @@ class PlanInfo(ctypes.Structure):
                 ("add_jobs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("vjp_conv_jobs", ctypes.c_int64), ("vjp_corr_jobs", ctypes.c_int64),
                 ("digits", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("smem_bytes", ctypes.c_int32)]
+                ("smem_bytes", ctypes.c_int32), ("arith", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+        d = {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "pad"}
+        d["arith_name"] = {0: "fp64", 1: "int"}.get(d["arith"], str(d["arith"]))
+        return d
 
 
 _lock = threading.Lock()
@@ -150,7 +152,7 @@ def _ptr(t, shape, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_options(arith="fp64", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False):
+def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False):
     o = Options()
     lib().pes_default_options(ctypes.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
