@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--d", type=int, default=152)
     ap.add_argument("--monomials", type=int, default=0,
                     help="use only the first M monomials of the workload (smaller case for profiling)")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="instances of the batched comparison in the default run (0 to skip)")
+    ap.add_argument("--batch-k", type=int, default=2)
+    ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
                     help="variables of the monomial the oracle evaluates as the CPU sample")
     return ap.parse_args()
@@ -425,6 +429,10 @@ def ours_arm(args, world, rank, local):
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": info["grid"], "smem_bytes": info["smem_bytes"], "digits": info["digits"]},
     }
+    if not args.no_autograd:
+        out["autograd"] = autograd_measure(args, dev, flush)
+    if args.batch_count > 0:
+        out["batched"] = batch_measure(args, dev, args.batch_count)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub = cpu_sample(prob, args.cpu_sample_vars)
         t, cores = run_oracle(sub)
@@ -435,6 +443,108 @@ def ours_arm(args, world, rank, local):
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
+
+
+def autograd_measure(args, dev, flush):
+    """Config 2 shape (p3: n=128, all 8128 pairs, d=152, k=4): forward through
+    the autograd Function, then the backward (the VJP kernels) of
+    L = sum_j v_j^2, both timed with CUDA events; backward / forward ratio."""
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    from paper_2101_10881_gb300.autograd import poly_eval
+    prob = synth.config2(seed=args.seed)
+    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k)
+    C = torch.from_numpy(prob.coeff).to(dev)
+    Z = torch.from_numpy(prob.inputs).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    fwd, bwd = [], []
+    for it in range(max(args.warmup, 3) + args.steps):
+        Cg = C.clone().requires_grad_(True)
+        Zg = Z.clone().requires_grad_(True)
+        flush.fill_(1)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        v = poly_eval(Cg, Zg, plan)
+        e1.record(stream)
+        v.backward(2 * v.detach())
+        e2.record(stream)
+        e2.synchronize()
+        if it >= max(args.warmup, 3):
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    plan.check()
+    f, b = statistics.mean(fwd), statistics.mean(bwd)
+    info = plan.info()
+    return {"workload": f"p3 n=128 N=8128 d={prob.d} k={prob.k}: value forward, VJP backward of sum_j v_j^2",
+            "forward_ms": f, "backward_ms": b, "backward_over_forward": b / f,
+            "backward_reuses_forward_products": True,
+            "vjp_jobs": {"monomial_products": info["vjp_conv_jobs"], "correlations": info["vjp_corr_jobs"]}}
+
+
+def batch_measure(args, dev, count):
+    """Config 3 recipe (random sparse polynomials: n 8-128, m 16-2048 monomials of
+    2-8 variables, d in {15,31,63,127,152}), first `count` instances, k=2: one
+    graph-captured batched call vs the same instances one plain pes_eval_grad
+    call after another on one stream (plans built beforehand), ms per instance;
+    the batched results must equal the plain ones."""
+    import numpy as np
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    k = args.batch_k
+    shapes = synth.config3_shapes(seed=args.seed, count=count)
+    rng = np.random.default_rng(args.seed + 7)
+    probs = []
+    for b, (n, supp, d) in enumerate(shapes):
+        N = len(supp)
+        probs.append(synth.Problem(f"b{b}", n, d, k, supp, synth.random_md(rng, k, (N + 1, d + 1)),
+                                   synth.random_md(rng, k, (n, d + 1))))
+    B = pes.Batch([(p.supports, p.n, p.d) for p in probs], k, autotune=True, profile=True)
+    C = torch.from_numpy(np.concatenate([p.coeff.ravel() for p in probs])).to(dev)
+    Z = torch.from_numpy(np.concatenate([p.inputs.ravel() for p in probs])).to(dev)
+    ln = B.lengths()
+    V = torch.empty(ln["value"], dtype=torch.float64, device=dev)
+    G = torch.empty(ln["grad"], dtype=torch.float64, device=dev)
+    plans = [pes.Plan(p.supports, p.n, p.d, k, with_vjp=False) for p in probs]
+    Vp = torch.empty_like(V)
+    Gp = torch.empty_like(G)
+    views = []
+    for b, p in enumerate(probs):
+        views.append((C[B.coeff_off[b]:B.coeff_off[b + 1]].view(k, p.N + 1, p.d + 1),
+                      Z[B.input_off[b]:B.input_off[b + 1]].view(k, p.n, p.d + 1),
+                      Vp[B.value_off[b]:B.value_off[b + 1]].view(k, p.d + 1),
+                      Gp[B.grad_off[b]:B.grad_off[b + 1]].view(k, p.n, p.d + 1)))
+    stream = torch.cuda.current_stream(dev)
+
+    def batched():
+        B.eval_grad(C, Z, V, G)
+
+    def plain():
+        for pl, (c, z, v, g) in zip(plans, views):
+            pl.eval_grad(c, z, v, g)
+
+    res = {}
+    for name, fn in (("batched", batched), ("plain", plain)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        times = []
+        for _ in range(max(2, min(args.steps, 3))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[name] = statistics.mean(times)
+    B.check()
+    same = bool(torch.equal(V, Vp) and torch.equal(G, Gp))
+    info = B.info()
+    return {"workload": f"first {count} instances of the batched recipe (seed {args.seed}), k={k}",
+            "instances": count, "conv_jobs": info["conv_jobs"], "groups": info["grid"],
+            "batched_ms_per_instance": res["batched"] / count, "plain_ms_per_instance": res["plain"] / count,
+            "plain_over_batched": res["plain"] / res["batched"],
+            "batched_equals_plain_bitwise": same, "launches_plain_per_call": 4 * count,
+            "graph": "one CUDA graph: per group pack + persistent convolution + addition, groups on forked streams"}
 
 
 def main():

@@ -70,7 +70,8 @@ typedef struct {
   int32_t with_vjp;    /* 1: also build the tables of pes_vjp (default 1) */
   int64_t timeout_ms;  /* bound on every device-side wait; 0 = default (60000) */
   int32_t profile;     /* 1: record CUDA events around each launch of a call (see pes_last_timing) */
-  int32_t pad;
+  int32_t autotune;    /* batches: 1 = time the candidate CTA shapes of every group on the first call and
+                          keep the fastest (cached in $PES_AUTOTUNE_CACHE, else ~/.cache/pes_autotune.txt) */
 } pes_options;
 
 /* Fill *opt with the defaults. */
@@ -131,7 +132,8 @@ pes_status pes_workspace_io(pes_plan_t plan, void* buffer, int32_t to_buffer, vo
 /* Device time of the launches of the last pes_eval_grad / pes_vjp /
  * pes_eval_grad_batch call of a plan or batch built with profile = 1, measured
  * with CUDA events on the call's stream (waits for the events):
- *   ms[0] pack, ms[1] convolution kernel(s), ms[2] addition, ms[3] unpack;
+ *   ms[0] pack, ms[1] convolution kernel(s), ms[2] addition, ms[3] unpack
+ * (for a batch ms[1] is the whole graph and the others are 0);
  * *launches receives the number of kernels the call launched. */
 pes_status pes_last_timing(pes_plan_t plan, double* ms, int32_t* launches);
 pes_status pes_batch_last_timing(pes_batch_t batch, double* ms, int32_t* launches);
@@ -177,8 +179,11 @@ void pes_batch_destroy(pes_batch_t batch);
 pes_status pes_batch_offsets(pes_batch_t batch, int64_t* coeff_off, int64_t* input_off, int64_t* value_off,
                              int64_t* grad_off);
 
-/* All instances at once: one pack, one persistent convolution launch over the
- * concatenated job tables, one addition launch, replayed as a CUDA graph. */
+/* All instances at once.  Instances are grouped by the CTA shape their degree
+ * needs; every group is one pack, one persistent convolution launch over its
+ * concatenated job tables and one addition launch; the groups run on forked
+ * streams; the whole call is captured once as a CUDA graph (re-captured when the
+ * caller's buffers change) and replayed. */
 pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff, const double* input, double* value,
                                double* grad, void* stream);
 pes_status pes_batch_check(pes_batch_t batch, void* stream);

@@ -1,9 +1,13 @@
 // pes_api.cu -- the C-ABI of include/pes.h: plans, batches and launches.
 #include <cuda_runtime.h>
 
+#include <sys/stat.h>
+
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <string>
@@ -183,6 +187,18 @@ struct Exec {
     return PES_OK;
   }
 
+  // threads per CTA and a cap on CTAs per SM (0: as many as fit) for later launches
+  pes_status configure(int32_t t, int32_t ctas_cap, JobList& L) {
+    int bps = 0;
+    PES_CUDA(pes::dag_occupancy(k, arith, t, smem, &bps));
+    if (bps < 1) return fail(PES_EUNSUPPORTED_SIZE, "configuration does not fit on an SM");
+    threads = t;
+    blocks_per_sm = ctas_cap > 0 ? std::min(bps, ctas_cap) : bps;
+    L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(
+                 static_cast<long long>(blocks_per_sm) * nsm, L.n)));
+    return PES_OK;
+  }
+
   pes::DagArgs dag_args(const JobList& L, int counter) const {
     pes::DagArgs a{};
     a.jobs = L.jobs;
@@ -320,7 +336,7 @@ extern "C" void pes_default_options(pes_options* opt) {
   opt->with_vjp = 1;
   opt->timeout_ms = 60000;
   opt->profile = 0;
-  opt->pad = 0;
+  opt->autotune = 0;
 }
 
 extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -506,21 +522,96 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
 // ---------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------
+//
+// Instances are grouped by the CTA shape their degree needs (integer pipe: one
+// lane per output coefficient, d+1 rounded up to whole warps; FP64 pipe: 128
+// threads).  Every group is one persistent launch over its instances'
+// concatenated job tables (sorted by layer, larger degree first); the groups run
+// on forked streams inside one captured CUDA graph.
 
-struct pes_batch_s {
+namespace {
+
+struct Group {
   Exec ex;
   JobList fwd;
   AddTable add;
   CopyTable pack;
-  int32_t count = 0;
+  std::vector<int32_t> members;
+  int64_t conv_jobs = 0, terms = 0;
+  uint64_t signature = 1469598103934665603ull;  // FNV-1a over the job structure
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  ~Group() {
+    if (done) cudaEventDestroy(done);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+void fnv(uint64_t& h, int64_t v) {
+  for (int i = 0; i < 8; ++i) {
+    h ^= static_cast<uint64_t>((v >> (8 * i)) & 0xFF);
+    h *= 1099511628211ull;
+  }
+}
+
+std::string autotune_cache_path() {
+  const char* p = std::getenv("PES_AUTOTUNE_CACHE");
+  if (p && *p) return p;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/pes_autotune.txt";
+}
+
+bool cache_lookup(const std::string& key, int32_t* threads, int32_t* ctas) {
+  FILE* f = std::fopen(autotune_cache_path().c_str(), "r");
+  if (!f) return false;
+  char kb[256];
+  int t = 0, c = 0;
+  bool found = false;
+  while (std::fscanf(f, "%255s %d %d", kb, &t, &c) == 3)
+    if (key == kb) {
+      *threads = t;
+      *ctas = c;
+      found = true;
+    }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const std::string& key, int32_t threads, int32_t ctas) {
+  std::string path = autotune_cache_path();
+  std::string dir = path.substr(0, path.find_last_of('/'));
+  if (!dir.empty()) {
+    std::string cmd_dir = dir;  // create the directory if needed (best effort)
+    for (size_t i = 1; i <= cmd_dir.size(); ++i)
+      if (i == cmd_dir.size() || cmd_dir[i] == '/') mkdir(cmd_dir.substr(0, i).c_str(), 0755);
+  }
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d\n", key.c_str(), threads, ctas);
+  std::fclose(f);
+}
+
+}  // namespace
+
+struct pes_batch_s {
+  std::vector<std::unique_ptr<Group>> groups;
+  int32_t count = 0, k = 0;
+  bool autotune = false, tuned = false, profile = false;
   std::vector<int64_t> coeff_off, input_off, value_off, grad_off;
   int64_t conv_jobs = 0, layers = 0, add_terms = 0, add_jobs = 0;
   // CUDA graph of one call, re-instantiated when the caller's buffers change
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int32_t last_launches = 0;
   ~pes_batch_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    groups.clear();
     if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
@@ -538,14 +629,17 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
   std::unique_ptr<pes_batch_s> B(new (std::nothrow) pes_batch_s());
   if (!B) return fail(PES_ENOMEM, "batch");
   B->count = count;
+  B->k = k;
+  B->autotune = o.autotune != 0;
+  B->profile = o.profile != 0;
 
   std::vector<pes::Program1> progs(static_cast<size_t>(count));
-  std::vector<pes::InstInfo> insts(static_cast<size_t>(count));
   B->coeff_off.assign(static_cast<size_t>(count) + 1, 0);
   B->input_off.assign(static_cast<size_t>(count) + 1, 0);
   B->value_off.assign(static_cast<size_t>(count) + 1, 0);
   B->grad_off.assign(static_cast<size_t>(count) + 1, 0);
-  int64_t prow = 0, qidx = 0, wsbase = 0;
+  std::map<std::pair<int32_t, int32_t>, std::vector<int32_t>> classes;  // (arith, threads) -> instances
+  int64_t prow = 0, qidx = 0;
   for (int32_t b = 0; b < count; ++b) {
     if (d[b] < 0 || d[b] > 1023) return fail(PES_EINVAL, "instance " + std::to_string(b) + ": bad degree");
     pes::Supports sup;
@@ -554,10 +648,6 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     s = build_supports(bp, bi, N[b], n[b], sup);
     if (s != PES_OK) return fail(s, "instance " + std::to_string(b) + ": " + g_last_error);
     progs[static_cast<size_t>(b)] = pes::compile(sup, d[b], false, false);
-    const int32_t S = pes::series_stride(d[b]);
-    const int64_t slots = progs[static_cast<size_t>(b)].n_slots;
-    insts[static_cast<size_t>(b)] = pes::InstInfo{wsbase, slots * S, S, d[b]};
-    wsbase += static_cast<int64_t>(k) * slots * S;
     const int64_t D1 = d[b] + 1;
     B->coeff_off[static_cast<size_t>(b) + 1] = B->coeff_off[static_cast<size_t>(b)] + k * (N[b] + 1) * D1;
     B->input_off[static_cast<size_t>(b) + 1] = B->input_off[static_cast<size_t>(b)] + k * n[b] * D1;
@@ -565,63 +655,102 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     B->grad_off[static_cast<size_t>(b) + 1] = B->grad_off[static_cast<size_t>(b)] + k * n[b] * D1;
     prow += N[b] + 1;
     qidx += sup.ptr.back();
+    const int32_t T = (d[b] + 1 + 31) / 32 * 32;
+    int32_t ar = o.arith;
+    if (ar == PES_ARITH_AUTO) ar = T <= pes::dag_max_threads(k) ? pes::ARITH_INT : pes::ARITH_FP64;
+    classes[{ar, ar == pes::ARITH_INT ? T : 0}].push_back(b);
   }
-  s = B->ex.init(k, o, insts, static_cast<size_t>(wsbase));
-  if (s != PES_OK) return s;
 
-  // concatenate: all jobs sorted by layer, larger degree first inside a layer
-  struct Ref {
-    int32_t layer, d, inst, local;
-  };
-  std::vector<Ref> refs;
-  for (int32_t b = 0; b < count; ++b)
-    for (size_t t = 0; t < progs[static_cast<size_t>(b)].jobs.size(); ++t)
-      refs.push_back({progs[static_cast<size_t>(b)].jobs[t].layer, d[b], b, static_cast<int32_t>(t)});
-  std::stable_sort(refs.begin(), refs.end(), [](const Ref& a, const Ref& b) {
-    if (a.layer != b.layer) return a.layer < b.layer;
-    return a.d > b.d;
-  });
-  std::vector<std::vector<int32_t>> gidx(static_cast<size_t>(count));
-  for (int32_t b = 0; b < count; ++b) gidx[static_cast<size_t>(b)].assign(progs[static_cast<size_t>(b)].jobs.size(), -1);
-  for (size_t g = 0; g < refs.size(); ++g) gidx[static_cast<size_t>(refs[g].inst)][static_cast<size_t>(refs[g].local)] = static_cast<int32_t>(g);
-  std::vector<pes::ConvJob> jobs(refs.size());
-  for (size_t g = 0; g < refs.size(); ++g) {
-    const auto& gi = gidx[static_cast<size_t>(refs[g].inst)];
-    pes::ConvJob j = progs[static_cast<size_t>(refs[g].inst)].jobs[static_cast<size_t>(refs[g].local)];
-    j.dep1 = j.dep1 >= 0 ? gi[static_cast<size_t>(j.dep1)] : -1;
-    j.dep2 = j.dep2 >= 0 ? gi[static_cast<size_t>(j.dep2)] : -1;
-    j.inst = refs[g].inst;
-    jobs[g] = j;
-    B->layers = std::max<int64_t>(B->layers, j.layer);
-  }
-  B->conv_jobs = static_cast<int64_t>(jobs.size());
-  s = B->ex.make_joblist(B->fwd, jobs);
-  if (s != PES_OK) return s;
+  for (auto& cls : classes) {
+    std::unique_ptr<Group> G(new (std::nothrow) Group());
+    if (!G) return fail(PES_ENOMEM, "batch group");
+    G->members = cls.second;
+    const size_t ng = G->members.size();
+    std::vector<pes::InstInfo> insts(ng);
+    int64_t wsbase = 0;
+    for (size_t u = 0; u < ng; ++u) {
+      const int32_t b = G->members[u];
+      const int32_t S = pes::series_stride(d[b]);
+      const int64_t slots = progs[static_cast<size_t>(b)].n_slots;
+      insts[u] = pes::InstInfo{wsbase, slots * S, S, d[b]};
+      wsbase += static_cast<int64_t>(k) * slots * S;
+    }
+    pes_options og = o;
+    og.arith = cls.first.first;
+    og.threads = std::max(o.threads, cls.first.second);
+    s = G->ex.init(k, og, insts, static_cast<size_t>(wsbase));
+    if (s != PES_OK) return s;
 
-  std::vector<pes::CopyRow> rows;
-  std::vector<pes::AddOut> outs;
-  std::vector<int32_t> contrib;
-  for (int32_t b = 0; b < count; ++b) {
-    const pes::Program1& G = progs[static_cast<size_t>(b)];
-    const int64_t D1 = d[b] + 1;
-    const int64_t co = B->coeff_off[static_cast<size_t>(b)], io = B->input_off[static_cast<size_t>(b)];
-    for (int32_t m = 0; m <= N[b]; ++m) rows.push_back({co + m * D1, (N[b] + 1) * D1, 0, b, m, 0});
-    for (int32_t i = 0; i < n[b]; ++i) rows.push_back({io + i * D1, n[b] * D1, 1, b, 1 + N[b] + i, 0});
-    const int32_t c0 = static_cast<int32_t>(contrib.size());
-    contrib.insert(contrib.end(), G.add_src.begin(), G.add_src.end());
-    outs.push_back({B->value_off[static_cast<size_t>(b)], D1, 0, b, c0 + G.add_ptr[0], c0 + G.add_ptr[1]});
-    for (int32_t i = 0; i < n[b]; ++i)
-      outs.push_back({B->grad_off[static_cast<size_t>(b)] + i * D1, n[b] * D1, 1, b, c0 + G.add_ptr[1 + i],
-                      c0 + G.add_ptr[2 + i]});
-    B->add_terms += static_cast<int64_t>(G.add_src.size());
-    for (size_t oo = 0; oo + 1 < G.add_ptr.size(); ++oo)
-      B->add_jobs += std::max(0, G.add_ptr[oo + 1] - G.add_ptr[oo] - 1);
+    struct Ref {
+      int32_t layer, d, inst, local;
+    };
+    std::vector<Ref> refs;
+    for (size_t u = 0; u < ng; ++u) {
+      const int32_t b = G->members[u];
+      for (size_t t = 0; t < progs[static_cast<size_t>(b)].jobs.size(); ++t)
+        refs.push_back({progs[static_cast<size_t>(b)].jobs[t].layer, d[b], static_cast<int32_t>(u),
+                        static_cast<int32_t>(t)});
+    }
+    std::stable_sort(refs.begin(), refs.end(), [](const Ref& x, const Ref& y) {
+      if (x.layer != y.layer) return x.layer < y.layer;
+      return x.d > y.d;
+    });
+    std::vector<std::vector<int32_t>> gidx(ng);
+    for (size_t u = 0; u < ng; ++u) gidx[u].assign(progs[static_cast<size_t>(G->members[u])].jobs.size(), -1);
+    for (size_t g = 0; g < refs.size(); ++g)
+      gidx[static_cast<size_t>(refs[g].inst)][static_cast<size_t>(refs[g].local)] = static_cast<int32_t>(g);
+    std::vector<pes::ConvJob> jobs(refs.size());
+    for (size_t g = 0; g < refs.size(); ++g) {
+      const auto& gi = gidx[static_cast<size_t>(refs[g].inst)];
+      pes::ConvJob j = progs[static_cast<size_t>(G->members[static_cast<size_t>(refs[g].inst)])]
+                           .jobs[static_cast<size_t>(refs[g].local)];
+      j.dep1 = j.dep1 >= 0 ? gi[static_cast<size_t>(j.dep1)] : -1;
+      j.dep2 = j.dep2 >= 0 ? gi[static_cast<size_t>(j.dep2)] : -1;
+      j.inst = refs[g].inst;
+      jobs[g] = j;
+      B->layers = std::max<int64_t>(B->layers, j.layer);
+      fnv(G->signature, j.layer);
+      fnv(G->signature, refs[g].d);
+      G->terms += static_cast<int64_t>(refs[g].d + 1) * (refs[g].d + 2) / 2;
+    }
+    G->conv_jobs = static_cast<int64_t>(jobs.size());
+    B->conv_jobs += G->conv_jobs;
+    s = G->ex.make_joblist(G->fwd, jobs);
+    if (s != PES_OK) return s;
+
+    std::vector<pes::CopyRow> rows;
+    std::vector<pes::AddOut> outs;
+    std::vector<int32_t> contrib;
+    for (size_t u = 0; u < ng; ++u) {
+      const int32_t b = G->members[u];
+      const int32_t iu = static_cast<int32_t>(u);
+      const pes::Program1& P = progs[static_cast<size_t>(b)];
+      const int64_t D1 = d[b] + 1;
+      const int64_t co = B->coeff_off[static_cast<size_t>(b)], io = B->input_off[static_cast<size_t>(b)];
+      for (int32_t m = 0; m <= N[b]; ++m) rows.push_back({co + m * D1, (N[b] + 1) * D1, 0, iu, m, 0});
+      for (int32_t i = 0; i < n[b]; ++i) rows.push_back({io + i * D1, n[b] * D1, 1, iu, 1 + N[b] + i, 0});
+      const int32_t c0 = static_cast<int32_t>(contrib.size());
+      contrib.insert(contrib.end(), P.add_src.begin(), P.add_src.end());
+      outs.push_back({B->value_off[static_cast<size_t>(b)], D1, 0, iu, c0 + P.add_ptr[0], c0 + P.add_ptr[1]});
+      for (int32_t i = 0; i < n[b]; ++i)
+        outs.push_back({B->grad_off[static_cast<size_t>(b)] + i * D1, n[b] * D1, 1, iu, c0 + P.add_ptr[1 + i],
+                        c0 + P.add_ptr[2 + i]});
+      B->add_terms += static_cast<int64_t>(P.add_src.size());
+      for (size_t oo = 0; oo + 1 < P.add_ptr.size(); ++oo)
+        B->add_jobs += std::max(0, P.add_ptr[oo + 1] - P.add_ptr[oo] - 1);
+    }
+    G->pack.n = static_cast<int32_t>(rows.size());
+    s = G->ex.put(&G->pack.rows, rows);
+    if (s == PES_OK) s = G->ex.make_add(G->add, outs, contrib, insts);
+    if (s != PES_OK) return s;
+    PES_CUDA(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
+    PES_CUDA(cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming));
+    B->groups.push_back(std::move(G));
   }
-  B->pack.n = static_cast<int32_t>(rows.size());
-  s = B->ex.put(&B->pack.rows, rows);
-  if (s == PES_OK) s = B->ex.make_add(B->add, outs, contrib, insts);
-  if (s != PES_OK) return s;
   PES_CUDA(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
+  PES_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+  if (B->profile)
+    for (cudaEvent_t& e : B->ev) PES_CUDA(cudaEventCreate(&e));
   *out = B.release();
   return PES_OK;
 }
@@ -639,13 +768,82 @@ extern "C" pes_status pes_batch_offsets(pes_batch_t batch, int64_t* coeff_off, i
   return PES_OK;
 }
 
+static pes_status group_record(Group& G, const double* coeff, const double* input, double* value, double* grad,
+                               cudaStream_t st) {
+  Exec& E = G.ex;
+  PES_CUDA(pes::launch_prologue(E.ctrl, st));
+  PES_CUDA(E.run_pack(G.pack, coeff, input, nullptr, st));
+  PES_CUDA(E.run_dag(G.fwd, 0, st));
+  PES_CUDA(E.run_add(G.add, value, grad, st));
+  return PES_OK;
+}
+
 static pes_status batch_record(pes_batch_t B, const double* coeff, const double* input, double* value,
                                double* grad, cudaStream_t st) {
-  Exec& E = B->ex;
-  PES_CUDA(pes::launch_prologue(E.ctrl, st));
-  PES_CUDA(E.run_pack(B->pack, coeff, input, nullptr, st));
-  PES_CUDA(E.run_dag(B->fwd, 0, st));
-  PES_CUDA(E.run_add(B->add, value, grad, st));
+  if (B->groups.size() == 1) return group_record(*B->groups[0], coeff, input, value, grad, st);
+  PES_CUDA(cudaEventRecord(B->fork, st));
+  for (auto& G : B->groups) {
+    PES_CUDA(cudaStreamWaitEvent(G->stream, B->fork, 0));
+    pes_status s = group_record(*G, coeff, input, value, grad, G->stream);
+    if (s != PES_OK) return s;
+    PES_CUDA(cudaEventRecord(G->done, G->stream));
+  }
+  for (auto& G : B->groups) PES_CUDA(cudaStreamWaitEvent(st, G->done, 0));
+  return PES_OK;
+}
+
+// Pick threads per CTA and CTAs per SM for every group by timing its launches
+// on the caller's data (the values do not depend on the choice); results are
+// kept in a cache file keyed by the group's job structure.
+static pes_status batch_autotune(pes_batch_t B, const double* coeff, const double* input, double* value,
+                                 double* grad, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  PES_CUDA(cudaEventCreate(&e0));
+  PES_CUDA(cudaEventCreate(&e1));
+  for (auto& Gp : B->groups) {
+    Group& G = *Gp;
+    Exec& E = G.ex;
+    char key[200];
+    std::snprintf(key, sizeof(key), "k%d_a%d_t%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.dmax,
+                  static_cast<long long>(G.conv_jobs), static_cast<unsigned long long>(G.signature));
+    int32_t bt = E.threads, bc = 0;
+    if (!cache_lookup(key, &bt, &bc)) {
+      std::vector<std::pair<int32_t, int32_t>> cands;
+      const int32_t base_t = E.threads;
+      int occ = 0;
+      PES_CUDA(pes::dag_occupancy(E.k, E.arith, base_t, E.smem, &occ));
+      for (int32_t t : {base_t, base_t + 32, base_t * 2}) {
+        if (t > pes::dag_max_threads(E.k) || t > 1024) continue;
+        int oc = 0;
+        PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, E.smem, &oc));
+        for (int32_t c = std::max(1, oc); c >= std::max(1, oc - 1); --c) cands.push_back({t, c});
+      }
+      float best = 1e30f;
+      for (const auto& cd : cands) {
+        pes_status s = E.configure(cd.first, cd.second, G.fwd);
+        if (s != PES_OK) return s;
+        s = group_record(G, coeff, input, value, grad, st);  // warm-up
+        if (s != PES_OK) return s;
+        PES_CUDA(cudaEventRecord(e0, st));
+        s = group_record(G, coeff, input, value, grad, st);
+        if (s != PES_OK) return s;
+        PES_CUDA(cudaEventRecord(e1, st));
+        PES_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bt = cd.first;
+          bc = cd.second;
+        }
+      }
+      cache_store(key, bt, bc);
+    }
+    pes_status s = E.configure(bt, bc, G.fwd);
+    if (s != PES_OK) return s;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return PES_OK;
 }
 
@@ -654,6 +852,11 @@ extern "C" pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff
   if (!batch) return fail(PES_EINVAL, "batch is NULL");
   if (!coeff || !input || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (batch->autotune && !batch->tuned) {
+    pes_status s = batch_autotune(batch, coeff, input, value, grad, st);
+    if (s != PES_OK) return s;
+    batch->tuned = true;
+  }
   const void* key[4] = {coeff, input, value, grad};
   if (!batch->gexec || std::memcmp(key, batch->gkey, sizeof(key)) != 0) {
     if (batch->gexec) {
@@ -674,24 +877,38 @@ extern "C" pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     std::memcpy(batch->gkey, key, sizeof(key));
   }
-  PES_CUDA(batch->ex.mark(0, st));
-  PES_CUDA(batch->ex.mark(1, st));
+  if (batch->profile) PES_CUDA(cudaEventRecord(batch->ev[0], st));
   PES_CUDA(cudaGraphLaunch(batch->gexec, st));
-  PES_CUDA(batch->ex.mark(2, st));
-  PES_CUDA(batch->ex.mark(3, st));
-  PES_CUDA(batch->ex.mark(4, st));
-  batch->ex.last_launches = 4;
+  if (batch->profile) PES_CUDA(cudaEventRecord(batch->ev[1], st));
+  batch->last_launches = 0;
+  for (auto& G : batch->groups) batch->last_launches += 3 + (G->fwd.n > 0 ? 1 : 0);
   return PES_OK;
 }
 
 extern "C" pes_status pes_batch_last_timing(pes_batch_t batch, double* ms, int32_t* launches) {
   if (!batch) return fail(PES_EINVAL, "batch is NULL");
-  return batch->ex.last_timing(ms, launches);
+  if (!batch->profile) return fail(PES_EINVAL, "built without profile = 1");
+  PES_CUDA(cudaEventSynchronize(batch->ev[1]));
+  float t = 0.f;
+  PES_CUDA(cudaEventElapsedTime(&t, batch->ev[0], batch->ev[1]));
+  if (ms) {
+    ms[0] = 0.0;
+    ms[1] = t;  // the whole graph (pack, convolutions and additions of every group)
+    ms[2] = 0.0;
+    ms[3] = 0.0;
+  }
+  if (launches) *launches = batch->last_launches;
+  return PES_OK;
 }
 
 extern "C" pes_status pes_batch_check(pes_batch_t batch, void* stream) {
   if (!batch) return fail(PES_EINVAL, "batch is NULL");
-  return batch->ex.check(static_cast<cudaStream_t>(stream));
+  PES_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  for (auto& G : batch->groups) {
+    pes_status s = G->ex.check(G->stream);
+    if (s != PES_OK) return s;
+  }
+  return PES_OK;
 }
 
 extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info) {
@@ -701,12 +918,15 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->layers = batch->layers;
   info->add_terms = batch->add_terms;
   info->add_jobs = batch->add_jobs;
-  info->workspace_bytes = static_cast<int64_t>(batch->ex.ws_doubles * sizeof(double));
-  info->digits = pes::digits_of_k(batch->ex.k, batch->ex.arith);
-  info->grid = batch->fwd.grid;
-  info->threads = batch->ex.threads;
-  info->smem_bytes = static_cast<int32_t>(batch->ex.smem);
-  info->arith = batch->ex.arith;
+  size_t ws = 0;
+  for (auto& G : batch->groups) ws += G->ex.ws_doubles * sizeof(double);
+  info->workspace_bytes = static_cast<int64_t>(ws);
+  const Exec& E0 = batch->groups.front()->ex;
+  info->digits = pes::digits_of_k(batch->k, E0.arith);
+  info->grid = static_cast<int32_t>(batch->groups.size());  // number of groups (persistent launches)
+  info->threads = E0.threads;
+  info->smem_bytes = static_cast<int32_t>(E0.smem);
+  info->arith = E0.arith;
   return PES_OK;
 }
 

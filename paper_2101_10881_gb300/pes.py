@@ -42,7 +42,7 @@ class PesError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("arith", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("with_vjp", ctypes.c_int32), ("timeout_ms", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -152,7 +152,8 @@ def _ptr(t, shape, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False):
+def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False,
+                 autotune=False):
     o = Options()
     lib().pes_default_options(ctypes.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
@@ -161,6 +162,7 @@ def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_
     o.with_vjp = int(bool(with_vjp))
     o.timeout_ms = int(timeout_ms)
     o.profile = int(bool(profile))
+    o.autotune = int(bool(autotune))
     return o
 
 

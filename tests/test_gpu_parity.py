@@ -222,19 +222,24 @@ def test_vjp_central_differences_octo(torch):
             assert abs(fd - an) <= scale * Fraction(1, 10 ** 55)
 
 
-def test_batch_matches_single_plans(torch):
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_matches_single_plans(torch, autotune, tmp_path, monkeypatch):
+    """Mixed degrees (several CTA-shape groups on forked streams in one graph),
+    with and without the autotuner: every instance equals its own plan bit for
+    bit and the oracle within tolerance."""
+    monkeypatch.setenv("PES_AUTOTUNE_CACHE", str(tmp_path / "autotune.txt"))
     rng = np.random.default_rng(40)
     k = 2
     insts, probs = [], []
-    for b in range(6):
+    for b, d in enumerate([0, 7, 15, 31, 40, 63, 100, 152]):
         n = int(rng.integers(3, 9))
         N = int(rng.integers(1, 15))
-        d = int(rng.choice([0, 7, 15, 31]))
         supp = synth.random_supports(rng, n, N, 1, min(n, 5))
         probs.append(synth.Problem(f"b{b}", n, d, k, supp, random_md(rng, k, (N + 1, d + 1)),
                                    random_md(rng, k, (n, d + 1))))
         insts.append((supp, n, d))
-    B = pes.Batch(insts, k)
+    B = pes.Batch(insts, k, autotune=autotune)
+    assert B.info()["grid"] >= 4  # groups of CTA shapes 32, 64, 128, 160
     C = dev(torch, np.concatenate([p.coeff.ravel() for p in probs]))
     Z = dev(torch, np.concatenate([p.inputs.ravel() for p in probs]))
     ln = B.lengths()
@@ -251,6 +256,8 @@ def test_batch_matches_single_plans(torch):
         assert np.array_equal(v, sv) and np.array_equal(g, sg)
         rv, rg = O.eval_grad(p.supports, p.n, p.coeff, p.inputs)
         assert normwise_err(v, rv) <= TOL[k] and normwise_err(g, rg) <= TOL[k]
+    if autotune:
+        assert (tmp_path / "autotune.txt").exists()
 
 
 def test_bounded_wait_reports_timeout(torch):
