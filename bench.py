@@ -55,14 +55,17 @@ def parse_args():
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["p2", "p1", "p3"], default="p2",
-                    help="p2: the headline workload; p1 / p3: the paper's other test polynomials (analysis)")
+    ap.add_argument("--workload", choices=["p2", "p1", "p3", "sweep", "batch"], default="p2",
+                    help="p2: the headline workload; p1 / p3: the paper's other test polynomials (analysis); "
+                         "sweep: the 64x64 system over k x d (one JSON line per cell); "
+                         "batch: the full batched recipe (2048 instances) batched vs plain")
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--d", type=int, default=152)
     ap.add_argument("--monomials", type=int, default=0,
                     help="use only the first M monomials of the workload (smaller case for profiling)")
-    ap.add_argument("--batch-count", type=int, default=256,
-                    help="instances of the batched comparison in the default run (0 to skip)")
+    ap.add_argument("--batch-count", type=int, default=None,
+                    help="instances of the batched comparison (default: 256 in the default run, 2048 with "
+                         "--workload batch; 0 skips it in the default run)")
     ap.add_argument("--batch-k", type=int, default=2)
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
@@ -431,8 +434,9 @@ def ours_arm(args, world, rank, local):
     }
     if not args.no_autograd:
         out["autograd"] = autograd_measure(args, dev, flush)
-    if args.batch_count > 0:
-        out["batched"] = batch_measure(args, dev, args.batch_count)
+    count = 256 if args.batch_count is None else args.batch_count
+    if count > 0:
+        out["batched"] = batch_measure(args, dev, count)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub = cpu_sample(prob, args.cpu_sample_vars)
         t, cores = run_oracle(sub)
@@ -547,12 +551,121 @@ def batch_measure(args, dev, count):
             "graph": "one CUDA graph: per group pack + persistent convolution + addition, groups on forked streams"}
 
 
+def limbs_to_fraction(limbs):
+    from fractions import Fraction
+    return sum((Fraction(float(x)) for x in limbs), Fraction(0))
+
+
+def closed_form_err(supports, coeff, avals, value, prec_bits):
+    """Normwise error of one value series (k, d+1) against the exact closed form
+    c_0 + sum_m c_m exp((sum_{i in S_m} a_i) t) (degree-0 coefficients c_m, exact
+    inputs a_i): every coefficient evaluated in integers scaled by 2^prec_bits,
+    each term rounded once (an error far below every tolerance)."""
+    from fractions import Fraction
+    d = value.shape[1] - 1
+    scale = 1 << prec_bits
+    fact = [1]
+    for j in range(1, d + 1):
+        fact.append(fact[-1] * j)
+    cs = [limbs_to_fraction(coeff[:, m, 0]) for m in range(coeff.shape[1])]
+    ref = [0] * (d + 1)
+    c0 = cs[0]
+    ref[0] += (c0.numerator * scale) // c0.denominator
+    for m, supp in enumerate(supports):
+        sm = sum((Fraction(avals[i]) for i in supp), Fraction(0))
+        c = cs[m + 1]
+        num, den = c.numerator, c.denominator
+        pn, pd = 1, 1
+        for j in range(d + 1):
+            ref[j] += (num * pn * scale) // (den * pd * fact[j])
+            pn *= sm.numerator
+            pd *= sm.denominator
+    got = [limbs_to_fraction(value[:, j]) for j in range(d + 1)]
+    num = max(abs(g * scale - r) for g, r in zip(got, ref))
+    den = max(abs(r) for r in ref)
+    return float(num / den) if den else 0.0
+
+
+def sweep_arm(args, world, rank):
+    """64 polynomials in 64 variables, each 512 monomials of 4-16 variables with
+    degree-0 random coefficients, inputs z_i = exp(a_i t): for every k x d cell,
+    forward (64 value series) and autograd backward of L = sum_p sum_j v_pj^2
+    with respect to the shared inputs and all coefficients; closed-form check of
+    the values of two polynomials per cell."""
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    from paper_2101_10881_gb300.autograd import poly_eval
+    if rank != 0:
+        return 0
+    pes.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    tol = {1: 1e-13, 2: 1e-29, 3: 1e-44, 4: 1e-60, 5: 1e-76, 8: 1e-123, 10: 1e-150}
+    rows = []
+    for k in synth.KS:
+        for d in (0, 7, 15, 31, 63, 127, 152):
+            sysc = synth.config4(d, k, seed=args.seed)
+            plans = [pes.Plan(supp, sysc.n, d, k) for supp, _ in sysc.polys]
+            coeffs = [torch.from_numpy(c).to(dev) for _, c in sysc.polys]
+            Zb = torch.from_numpy(sysc.inputs).to(dev)
+            info = [p.info() for p in plans]
+            conv_jobs = sum(i["conv_jobs"] for i in info)
+            add_jobs = sum(i["add_jobs"] for i in info)
+            times = []
+            for it in range(3):
+                Z = Zb.clone().requires_grad_(True)
+                Cs = [c.clone().requires_grad_(True) for c in coeffs]
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                vs = [poly_eval(c, Z, p) for c, p in zip(Cs, plans)]
+                e1.record(stream)
+                torch.autograd.backward(vs, [2 * v.detach() for v in vs])
+                e2.record(stream)
+                e2.synchronize()
+                times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+            for p in plans:
+                p.check()
+            fwd = min(t[0] for t in times)
+            bwd = min(t[1] for t in times)
+            errs = []
+            for q in (0, 1):
+                supp, c = sysc.polys[q]
+                errs.append(closed_form_err(supp, c, sysc.avals, vs[q].detach().cpu().numpy(), 53 * k + 64))
+            ops = dp_equiv_ops(conv_jobs, add_jobs, d, k)
+            row = {"cell": f"k={k} d={d}", "k": k, "d": d, "forward_ms": fwd, "backward_ms": bwd,
+                   "backward_over_forward": bwd / fwd if fwd > 0 else None,
+                   "forward_dp_equiv_tflops": ops / (fwd * 1e-3) / 1e12, "conv_jobs": conv_jobs,
+                   "closed_form_err": max(errs), "tol": tol[k], "within_tol": max(errs) <= tol[k],
+                   "arith": info[0]["arith_name"]}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del plans, vs, Cs, Z
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "sweep": "64x64 system, k x d", "cells": len(rows),
+                      "all_within_tol": all(r["within_tol"] for r in rows),
+                      "max_backward_over_forward": max(r["backward_over_forward"] or 0 for r in rows)}), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args) if args.impl == "ours" else (
         int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":
         return reference_arm(args, world, rank)
+    if args.workload == "sweep":
+        return sweep_arm(args, world, rank)
+    if args.workload == "batch":
+        import torch
+        from paper_2101_10881_gb300 import pes
+        pes.build()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "batched": batch_measure(args, torch.device("cuda", local),
+                                                                          args.batch_count or 2048)}), flush=True)
+        return 0
     rc = ours_arm(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist

@@ -14,6 +14,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "digits.cuh"
@@ -634,10 +637,23 @@ size_t dag_smem_bytes(int k, int arith, int smax, int dmax) {
   return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax).total;
 }
 
+// The dynamic shared-memory limit is a property of the kernel function on a
+// device, shared by every plan: raise it, never lower it, so that a plan built
+// later for a smaller degree cannot break the launches of an earlier one.
 cudaError_t dag_prepare(int k, int arith, size_t smem) {
   void* fn = dag_kernel_ptr(k, arith);
   if (!fn) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, size_t> granted;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = granted[std::make_tuple(dev, k, arith)];
+  if (smem <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e == cudaSuccess) cur = smem;
+  return e;
 }
 
 cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm) {

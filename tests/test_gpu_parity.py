@@ -260,6 +260,21 @@ def test_batch_matches_single_plans(torch, autotune, tmp_path, monkeypatch):
         assert (tmp_path / "autotune.txt").exists()
 
 
+def test_later_small_plan_keeps_large_plan_launchable(torch):
+    """The shared-memory limit is per kernel function: building a plan for a small
+    degree after one for a large degree must not break the large one."""
+    k = 4
+    rng = np.random.default_rng(9)
+    big = synth.Problem("big", 5, 152, k, [[0, 1, 2], [1, 3, 4]], random_md(rng, k, (3, 153)),
+                        random_md(rng, k, (5, 153)))
+    plan_big = pes.Plan(big.supports, big.n, big.d, k)
+    pes.Plan([[0, 1]], 2, 3, k)  # small degree, built afterwards
+    v, g = plan_big.eval_grad(dev(torch, big.coeff), dev(torch, big.inputs))
+    plan_big.check()
+    rv, rg = O.eval_grad(big.supports, big.n, big.coeff, big.inputs)
+    assert normwise_err(v.cpu().numpy(), rv) <= TOL[k] and normwise_err(g.cpu().numpy(), rg) <= TOL[k]
+
+
 def test_bounded_wait_reports_timeout(torch):
     """A job that waits on a flag nobody sets gives up after the bound and
     reports PES_ETIMEOUT; the context stays usable."""
