@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--arith", choices=["auto", "fp64", "int"], default="auto",
                     help="multiply-accumulate pipe of the headline run (auto: integer when the degree allows)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default CTA shape instead of timing the candidates on the first call")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra kernel-only timing of the FP64 variant")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
@@ -259,6 +261,7 @@ def workload_config(prob, args):
     shape = {"p2": "p2-like", "p1": "p1", "p3": "p3"}[args.workload]
     return {"workload": f"{shape} polynomial n={prob.n} N={prob.N} monomials of {sizes[0] if len(sizes) == 1 else sizes} "
                         f"variables, d={prob.d}, k={prob.k}, value + full gradient per step",
+            "autotune": not args.no_autotune and args.threads == 0,
             "global_batch": 1, "seq_len": prob.d + 1, "parallelism": f"replicas x{args.gpus}",
             "arith": args.arith, "threads_per_cta": args.threads or "auto",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); workspace > L2"}
@@ -305,7 +308,7 @@ def ours_arm(args, world, rank, local):
         prob = synth.Problem(prob.name, prob.n, prob.d, prob.k, prob.supports[: args.monomials],
                              prob.coeff[:, : args.monomials + 1].copy(), prob.inputs)
     plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, arith=args.arith, threads=args.threads,
-                    with_vjp=False, profile=True)
+                    with_vjp=False, profile=True, autotune=not args.no_autotune and args.threads == 0)
     info = plan.info()
     C = torch.from_numpy(prob.coeff).to(dev)
     Z = torch.from_numpy(prob.inputs).to(dev)
@@ -430,7 +433,8 @@ def ours_arm(args, world, rank, local):
         "ops_per_step": ops_step,
         "wall_s_timed_region": wall,
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
-                 "grid": info["grid"], "smem_bytes": info["smem_bytes"], "digits": info["digits"]},
+                 "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],
+                 "smem_bytes": info["smem_bytes"], "digits": info["digits"]},
     }
     if not args.no_autograd:
         out["autograd"] = autograd_measure(args, dev, flush)

@@ -47,8 +47,8 @@ typedef enum {
   PES_ECUDA = 4,             /* a CUDA runtime call failed */
   PES_ETIMEOUT = 5,          /* a device-side wait gave up (see pes_check) */
   PES_EINTERNAL = 6,         /* inconsistent internal state */
-  PES_EUNSUPPORTED_SIZE = 7  /* degree too large: d <= 383 for k = 8, 10; d <= 511 for k = 4, 5;
-                                d <= 767 for k <= 3 (and the shared-memory staging must fit) */
+  PES_EUNSUPPORTED_SIZE = 7  /* degree too large for the shared-memory staging of both operand series
+                                (or for the threads requested) */
 } pes_status;
 
 typedef struct pes_plan_s* pes_plan_t;
@@ -64,8 +64,10 @@ enum { PES_ARITH_AUTO = -1, PES_ARITH_FP64 = 0, PES_ARITH_INT = 1 };
 
 typedef struct {
   int32_t arith;       /* PES_ARITH_AUTO (default), PES_ARITH_FP64 or PES_ARITH_INT */
-  int32_t threads;     /* threads per CTA of the convolution kernel: 0 = automatic (d+1 rounded up to
-                          whole warps, one lane per output coefficient); else a larger multiple of 32 */
+  int32_t threads;     /* threads per CTA of the convolution kernel (a multiple of 32), 0 = automatic.
+                          Integer pipe: the lanes are spread evenly over the coefficient pairs (j, d-j),
+                          automatic = two lanes per pair (one per output coefficient), at least one lane
+                          per pair; FP64 pipe: automatic = 128 */
   int32_t ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit */
   int32_t with_vjp;    /* 1: also build the tables of pes_vjp (default 1) */
   int64_t timeout_ms;  /* bound on every device-side wait; 0 = default (60000) */

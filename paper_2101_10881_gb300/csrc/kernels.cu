@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
     const ConvJob jb = a.jobs[job];
     const InstInfo in = a.inst[jb.inst];
     const int d = in.d;
-    if (INTV && d + 1 > T) {  // one lane per output coefficient: the plan sizes the CTA for its largest degree
+    if (INTV && (d + 2) / 2 > T) {  // at least one lane per coefficient pair: the plan sizes the CTA
       if (tid == 0) set_error(a.ctrl, 6, job, d);
       break;
     }
@@ -358,42 +358,54 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
         }
       };
       if constexpr (INTV) {
-        // Coefficients j and d-j share d+2 terms; the two lanes of a pair split
-        // them so that every lane runs about (d+2)/2 terms and all lanes step
-        // the term index together (X rows are read as broadcasts, Y rows
-        // consecutively).  Lane A: the short coefficient, then the long one from
-        // its last term backwards; lane B: the long one from its first term.
-        const int P = (d + 1) / 2;                 // pairs
+        // Coefficients j and d-j share d+2 terms (the middle coefficient d/2,
+        // when d+1 is odd, forms a group of its own).  The Q = T / groups lanes
+        // of a group split its terms, walked as: the short coefficient from its
+        // first term, then the long one from its last term backwards.  At every
+        // step all lanes with the same rank q inside their group read the same
+        // X row (a broadcast) and consecutive Y rows, and every lane runs about
+        // (d+2)/Q terms.
+        const int P = (d + 1) / 2;                 // pairs (j, d - j), j < d - j
         const bool has_mid = ((d + 1) & 1) != 0;   // the middle coefficient d/2 pairs with itself
-        const int h = (d + 3) / 2;                 // steps of lane A
-        const int l = tid >> 1;
-        int role = 3;                              // 0 A, 1 B, 2 middle, 3 idle
-        if (tid < 2 * P) role = tid & 1;
-        else if (has_mid && tid == 2 * P) role = 2;
-        const int cs = conv ? l : d - l;           // short coefficient: l + 1 terms
-        const int cl = conv ? d - l : l;           // long coefficient: d - l + 1 terms
-        const int ns = l + 1, nl = d - l + 1;
-        const int steps = role == 0 ? h : role == 1 ? d + 2 - h : role == 2 ? d / 2 + 1 : 0;
-        int jcur = role == 1 ? cl : role == 2 ? d / 2 : cs;
-        for (int s = 0; s < steps; ++s) {
+        const int groups = P + (has_mid ? 1 : 0);
+        const int Q = T / groups;                  // lanes per group (>= 1: the plan sizes T)
+        const int grp = tid / Q, q = tid - grp * Q;
+        int cs = 0, cl = 0, ns = 0, nl = 0, tp = 0;
+        if (grp < P) {
+          cs = conv ? grp : d - grp;               // short coefficient: grp + 1 terms
+          cl = conv ? d - grp : grp;               // long coefficient: d - grp + 1 terms
+          ns = grp + 1;
+          nl = d - grp + 1;
+          tp = d + 2;
+        } else if (grp == P && has_mid) {
+          cs = cl = d / 2;
+          ns = d / 2 + 1;
+          tp = ns;
+        }
+        const int H = tp > 0 ? (tp + Q - 1) / Q : 0;
+        const int p0 = q * H;
+        const int p1 = min(p0 + H, tp);
+        int jcur = p0 < ns ? cs : cl;
+        for (int pos = p0; pos < p1; ++pos) {
           int j, i;
-          if (role == 0) {
-            if (s < ns) { j = cs; i = s; } else { j = cl; i = nl - 1 - (s - ns); }
+          if (pos < ns) {
+            j = cs;
+            i = pos;
           } else {
-            j = jcur;
-            i = s;
+            j = cl;
+            i = nl - 1 - (pos - ns);
           }
           const int ix = conv ? i : j + i;
           const int iy = conv ? j - i : i;
           term(ix, iy, gs[j] - gx[ix] - gy[iy]);
-          if (role == 0 && s == ns - 1) {
-            flush(cs);  // lane A leaves its short coefficient
+          if (pos == ns - 1 && pos + 1 < p1) {
+            flush(cs);  // this lane leaves the short coefficient
             jcur = cl;
-          } else if ((s + 1) % R == 0) {
+          } else if ((pos - p0 + 1) % R == 0) {
             flush(jcur);
           }
         }
-        if (steps > 0) flush(jcur);
+        if (p1 > p0) flush(jcur);
       } else {
         // Every thread runs the same number of consecutive terms of the
         // concatenated term sequence; partial sums of a coefficient split between

@@ -138,7 +138,7 @@ struct Exec {
     if (arith == PES_ARITH_AUTO) {
       int dm = 0;
       for (const auto& in : insts) dm = std::max(dm, in.d);
-      arith = (dm + 1 + 31) / 32 * 32 <= pes::dag_max_threads(k_) ? pes::ARITH_INT : pes::ARITH_FP64;
+      arith = (dm + 2) / 2 <= pes::dag_max_threads(k_) ? pes::ARITH_INT : pes::ARITH_FP64;
     }
     threads = o.threads;
     ctas_per_sm = o.ctas_per_sm;
@@ -154,12 +154,17 @@ struct Exec {
     PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int optin = 0;
     PES_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // integer variant: one lane per output coefficient of the largest degree,
-    // whole warps; FP64 variant: 128 threads share the terms evenly
-    if (arith == pes::ARITH_INT)
-      threads = std::max(threads, (dmax + 1 + 31) / 32 * 32);
-    else if (threads == 0)
+    // integer variant: by default two lanes per coefficient pair (one lane per
+    // output coefficient) of the largest degree, whole warps; at least one lane
+    // per pair; FP64 variant: 128 threads share the terms evenly
+    if (arith == pes::ARITH_INT) {
+      const int32_t pairs = (dmax + 2) / 2;
+      const int32_t least = (pairs + 31) / 32 * 32;
+      threads = threads == 0 ? std::max(least, std::min((2 * pairs + 31) / 32 * 32, pes::dag_max_threads(k)))
+                             : std::max(threads, least);
+    } else if (threads == 0) {
       threads = 128;
+    }
     if (threads > pes::dag_max_threads(k))
       return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(threads) +
                                              " threads per CTA; at most " + std::to_string(pes::dag_max_threads(k)) +
@@ -315,12 +320,119 @@ pes_status build_supports(const int32_t* ptr, const int32_t* idx, int32_t N, int
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// autotuning of the convolution launch shape
+// ---------------------------------------------------------------------------
+
+namespace {
+
+void fnv_mix(uint64_t& h, int64_t v) {
+  for (int i = 0; i < 8; ++i) {
+    h ^= static_cast<uint64_t>((v >> (8 * i)) & 0xFF);
+    h *= 1099511628211ull;
+  }
+}
+
+std::string autotune_cache_file() {
+  const char* p = std::getenv("PES_AUTOTUNE_CACHE");
+  if (p && *p) return p;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/pes_autotune.txt";
+}
+
+bool tune_lookup(const std::string& key, int32_t* threads, int32_t* ctas) {
+  FILE* f = std::fopen(autotune_cache_file().c_str(), "r");
+  if (!f) return false;
+  char kb[256];
+  int t = 0, c = 0;
+  bool found = false;
+  while (std::fscanf(f, "%255s %d %d", kb, &t, &c) == 3)
+    if (key == kb) {
+      *threads = t;
+      *ctas = c;
+      found = true;
+    }
+  std::fclose(f);
+  return found;
+}
+
+void tune_store(const std::string& key, int32_t threads, int32_t ctas) {
+  const std::string path = autotune_cache_file();
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos)
+    for (size_t i = 1; i <= slash; ++i)
+      if (i == slash || path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d\n", key.c_str(), threads, ctas);
+  std::fclose(f);
+}
+
+// Time `run` (one whole call on `st`) for every candidate launch shape of the
+// convolution kernel and keep the fastest; the values do not depend on the
+// shape, so the trials may run on the caller's data.  Cached by `key`.
+template <class Run>
+pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cudaStream_t st) {
+  int32_t bt = E.threads, bc = 0;
+  if (!tune_lookup(key, &bt, &bc)) {
+    const int32_t base = E.threads;
+    std::vector<int32_t> ts{base};
+    if (E.arith == pes::ARITH_INT) {
+      for (int32_t t : {base + 32, (base * 3 / 2 + 31) / 32 * 32, base * 2})
+        if (t <= pes::dag_max_threads(E.k) && std::find(ts.begin(), ts.end(), t) == ts.end()) ts.push_back(t);
+    } else {
+      ts.push_back(256);
+    }
+    cudaEvent_t e0, e1;
+    PES_CUDA(cudaEventCreate(&e0));
+    PES_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int32_t t : ts) {
+      int occ = 0;
+      PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, E.smem, &occ));
+      for (int32_t c = std::max(1, occ); c >= std::max(1, occ - 1); --c) {
+        pes_status s = E.configure(t, c, L);
+        if (s != PES_OK) continue;
+        s = run(st);  // warm-up
+        if (s != PES_OK) return s;
+        PES_CUDA(cudaEventRecord(e0, st));
+        s = run(st);
+        if (s != PES_OK) return s;
+        PES_CUDA(cudaEventRecord(e1, st));
+        PES_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bt = t;
+          bc = c;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(key, bt, bc);
+  }
+  return E.configure(bt, bc, L);
+}
+
+std::string tune_key(const Exec& E, int64_t njobs, uint64_t signature) {
+  char key[200];
+  std::snprintf(key, sizeof(key), "k%d_a%d_t%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.dmax,
+                static_cast<long long>(njobs), static_cast<unsigned long long>(signature));
+  return key;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // single plans
 // ---------------------------------------------------------------------------
 
 struct pes_plan_s {
   pes::Program1 prog;
   Exec ex;
+  bool autotune = false, tuned = false;
+  uint64_t signature = 1469598103934665603ull;
   JobList fwd, vjp_fwd, vjp_m, vjp_corr;
   AddTable add, add_g;
   CopyTable pack, pack_u, unpack;
@@ -374,6 +486,12 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
   // forward jobs
   s = P->ex.make_joblist(P->fwd, G.jobs);
   if (s != PES_OK) return s;
+  P->autotune = o.autotune != 0;
+  for (const auto& j : G.jobs) {
+    fnv_mix(P->signature, j.layer);
+    fnv_mix(P->signature, j.dep1);
+    fnv_mix(P->signature, j.dep2);
+  }
 
   // pack rows: coefficients (buffer 0), inputs (buffer 1)
   const int64_t D1 = d + 1;
@@ -433,6 +551,23 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
   if (!coeff || !input || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Exec& E = plan->ex;
+  if (plan->autotune && !plan->tuned) {
+    plan->tuned = true;
+    auto run = [&](cudaStream_t s2) -> pes_status {
+      PES_CUDA(pes::launch_prologue(E.ctrl, s2));
+      PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, s2));
+      PES_CUDA(E.run_dag(plan->fwd, 0, s2));
+      PES_CUDA(E.run_add(plan->add, value, grad, s2));
+      return PES_OK;
+    };
+    pes_status ts = tune_launch(E, plan->fwd, tune_key(E, plan->fwd.n, plan->signature), run, st);
+    if (ts != PES_OK) return ts;
+    // the VJP job lists share the launch shape
+    plan->vjp_fwd.grid = plan->vjp_m.grid = plan->vjp_corr.grid = 0;
+    E.configure(E.threads, E.blocks_per_sm, plan->vjp_fwd);
+    E.configure(E.threads, E.blocks_per_sm, plan->vjp_m);
+    E.configure(E.threads, E.blocks_per_sm, plan->vjp_corr);
+  }
   PES_CUDA(E.mark(0, st));
   PES_CUDA(pes::launch_prologue(E.ctrl, st));
   PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
@@ -547,50 +682,6 @@ struct Group {
   }
 };
 
-void fnv(uint64_t& h, int64_t v) {
-  for (int i = 0; i < 8; ++i) {
-    h ^= static_cast<uint64_t>((v >> (8 * i)) & 0xFF);
-    h *= 1099511628211ull;
-  }
-}
-
-std::string autotune_cache_path() {
-  const char* p = std::getenv("PES_AUTOTUNE_CACHE");
-  if (p && *p) return p;
-  const char* home = std::getenv("HOME");
-  return std::string(home ? home : "/tmp") + "/.cache/pes_autotune.txt";
-}
-
-bool cache_lookup(const std::string& key, int32_t* threads, int32_t* ctas) {
-  FILE* f = std::fopen(autotune_cache_path().c_str(), "r");
-  if (!f) return false;
-  char kb[256];
-  int t = 0, c = 0;
-  bool found = false;
-  while (std::fscanf(f, "%255s %d %d", kb, &t, &c) == 3)
-    if (key == kb) {
-      *threads = t;
-      *ctas = c;
-      found = true;
-    }
-  std::fclose(f);
-  return found;
-}
-
-void cache_store(const std::string& key, int32_t threads, int32_t ctas) {
-  std::string path = autotune_cache_path();
-  std::string dir = path.substr(0, path.find_last_of('/'));
-  if (!dir.empty()) {
-    std::string cmd_dir = dir;  // create the directory if needed (best effort)
-    for (size_t i = 1; i <= cmd_dir.size(); ++i)
-      if (i == cmd_dir.size() || cmd_dir[i] == '/') mkdir(cmd_dir.substr(0, i).c_str(), 0755);
-  }
-  FILE* f = std::fopen(path.c_str(), "a");
-  if (!f) return;
-  std::fprintf(f, "%s %d %d\n", key.c_str(), threads, ctas);
-  std::fclose(f);
-}
-
 }  // namespace
 
 struct pes_batch_s {
@@ -655,9 +746,9 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     B->grad_off[static_cast<size_t>(b) + 1] = B->grad_off[static_cast<size_t>(b)] + k * n[b] * D1;
     prow += N[b] + 1;
     qidx += sup.ptr.back();
-    const int32_t T = (d[b] + 1 + 31) / 32 * 32;
+    const int32_t T = (2 * ((d[b] + 2) / 2) + 31) / 32 * 32;  // default CTA: one lane per coefficient
     int32_t ar = o.arith;
-    if (ar == PES_ARITH_AUTO) ar = T <= pes::dag_max_threads(k) ? pes::ARITH_INT : pes::ARITH_FP64;
+    if (ar == PES_ARITH_AUTO) ar = (d[b] + 2) / 2 <= pes::dag_max_threads(k) ? pes::ARITH_INT : pes::ARITH_FP64;
     classes[{ar, ar == pes::ARITH_INT ? T : 0}].push_back(b);
   }
 
@@ -709,8 +800,8 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
       j.inst = refs[g].inst;
       jobs[g] = j;
       B->layers = std::max<int64_t>(B->layers, j.layer);
-      fnv(G->signature, j.layer);
-      fnv(G->signature, refs[g].d);
+      fnv_mix(G->signature, j.layer);
+      fnv_mix(G->signature, refs[g].d);
       G->terms += static_cast<int64_t>(refs[g].d + 1) * (refs[g].d + 2) / 2;
     }
     G->conv_jobs = static_cast<int64_t>(jobs.size());
@@ -792,58 +883,16 @@ static pes_status batch_record(pes_batch_t B, const double* coeff, const double*
   return PES_OK;
 }
 
-// Pick threads per CTA and CTAs per SM for every group by timing its launches
-// on the caller's data (the values do not depend on the choice); results are
-// kept in a cache file keyed by the group's job structure.
+// Pick the launch shape of every group by timing its launches on the caller's
+// data (see tune_launch).
 static pes_status batch_autotune(pes_batch_t B, const double* coeff, const double* input, double* value,
                                  double* grad, cudaStream_t st) {
-  cudaEvent_t e0, e1;
-  PES_CUDA(cudaEventCreate(&e0));
-  PES_CUDA(cudaEventCreate(&e1));
   for (auto& Gp : B->groups) {
     Group& G = *Gp;
-    Exec& E = G.ex;
-    char key[200];
-    std::snprintf(key, sizeof(key), "k%d_a%d_t%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.dmax,
-                  static_cast<long long>(G.conv_jobs), static_cast<unsigned long long>(G.signature));
-    int32_t bt = E.threads, bc = 0;
-    if (!cache_lookup(key, &bt, &bc)) {
-      std::vector<std::pair<int32_t, int32_t>> cands;
-      const int32_t base_t = E.threads;
-      int occ = 0;
-      PES_CUDA(pes::dag_occupancy(E.k, E.arith, base_t, E.smem, &occ));
-      for (int32_t t : {base_t, base_t + 32, base_t * 2}) {
-        if (t > pes::dag_max_threads(E.k) || t > 1024) continue;
-        int oc = 0;
-        PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, E.smem, &oc));
-        for (int32_t c = std::max(1, oc); c >= std::max(1, oc - 1); --c) cands.push_back({t, c});
-      }
-      float best = 1e30f;
-      for (const auto& cd : cands) {
-        pes_status s = E.configure(cd.first, cd.second, G.fwd);
-        if (s != PES_OK) return s;
-        s = group_record(G, coeff, input, value, grad, st);  // warm-up
-        if (s != PES_OK) return s;
-        PES_CUDA(cudaEventRecord(e0, st));
-        s = group_record(G, coeff, input, value, grad, st);
-        if (s != PES_OK) return s;
-        PES_CUDA(cudaEventRecord(e1, st));
-        PES_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bt = cd.first;
-          bc = cd.second;
-        }
-      }
-      cache_store(key, bt, bc);
-    }
-    pes_status s = E.configure(bt, bc, G.fwd);
+    auto run = [&](cudaStream_t s2) { return group_record(G, coeff, input, value, grad, s2); };
+    pes_status s = tune_launch(G.ex, G.fwd, tune_key(G.ex, G.conv_jobs, G.signature), run, st);
     if (s != PES_OK) return s;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return PES_OK;
 }
 

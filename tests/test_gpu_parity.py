@@ -86,10 +86,11 @@ def test_small_random_polynomials(torch, k, d):
     assert normalised(v) and normalised(g)
 
 
-@pytest.mark.parametrize("threads", [0, 256])
+@pytest.mark.parametrize("threads", [0, 96, 256, 320])
 def test_ragged_degree_several_tiles(torch, threads):
     """d = 152: 153 coefficients (a ragged last warp), k = 4, monomials of up to
-    5 variables, an unused variable and a one-variable monomial."""
+    5 variables, an unused variable and a one-variable monomial; CTA widths from
+    one lane per coefficient pair (96) to four (320)."""
     k, d, n = 4, 152, 6
     supp = [[0, 1, 2, 3, 4], [1, 3], [2], [0, 2, 4], [1, 2, 3, 4]]
     rng = np.random.default_rng(5)
@@ -260,6 +261,23 @@ def test_batch_matches_single_plans(torch, autotune, tmp_path, monkeypatch):
         assert (tmp_path / "autotune.txt").exists()
 
 
+def test_plan_autotune_same_values(torch, tmp_path, monkeypatch):
+    """The first call of an autotuned plan times several CTA shapes on the
+    caller's data; the values equal those of the default shape, and the choice
+    is cached."""
+    monkeypatch.setenv("PES_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    k, d = 10, 100
+    rng = np.random.default_rng(123)
+    supp = synth.random_supports(rng, 12, 20, 2, 6)
+    prob = synth.Problem("tune", 12, d, k, supp, random_md(rng, k, (21, d + 1)), random_md(rng, k, (12, d + 1)))
+    v0, g0, _ = run(torch, prob)
+    v1, g1, plan = run(torch, prob, autotune=True)
+    assert np.array_equal(v0, v1) and np.array_equal(g0, g1)
+    gi, gc = plan.vjp(dev(torch, prob.coeff), dev(torch, prob.inputs), dev(torch, random_md(rng, k, (d + 1,))))
+    plan.check()
+    assert (tmp_path / "tune.txt").read_text().strip()
+
+
 def test_later_small_plan_keeps_large_plan_launchable(torch):
     """The shared-memory limit is per kernel function: building a plan for a small
     degree after one for a large degree must not break the large one."""
@@ -296,5 +314,5 @@ def test_invalid_arguments(torch):
         pes.Plan([[0]], 1, 4000, 2)
     assert e.value.code == 7
     with pytest.raises(pes.PesError) as e:
-        pes.Plan([[0]], 1, 400, 10)  # one lane per coefficient: at most 384 threads at k=10
+        pes.Plan([[0]], 1, 900, 10)  # beyond the shared-memory staging at k=10
     assert e.value.code == 7
