@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra kernel-only timing of the FP64 variant")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
+                    help="staging depth of the convolution kernel (0: automatic / autotuned)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["p2", "p1", "p3", "sweep", "batch"], default="p2",
@@ -308,7 +310,8 @@ def ours_arm(args, world, rank, local):
         prob = synth.Problem(prob.name, prob.n, prob.d, prob.k, prob.supports[: args.monomials],
                              prob.coeff[:, : args.monomials + 1].copy(), prob.inputs)
     plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, arith=args.arith, threads=args.threads,
-                    with_vjp=False, profile=True, autotune=not args.no_autotune and args.threads == 0)
+                    with_vjp=False, profile=True, autotune=not args.no_autotune and args.threads == 0,
+                    staging=args.staging)
     info = plan.info()
     C = torch.from_numpy(prob.coeff).to(dev)
     Z = torch.from_numpy(prob.inputs).to(dev)
@@ -390,6 +393,8 @@ def ours_arm(args, world, rank, local):
     work = (f"{info['conv_jobs']} convolutions x {(prob.d + 1) * (prob.d + 2) // 2} terms x "
             f"{info['digits'] * (info['digits'] + 1) // 2} digit products")
     arith = info["arith_name"]
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_max_mhz = clk.get("sm_max_mhz")
     if arith == "fp64":
         achieved = digit_flops / (mean_conv * 1e-3) / 1e12
         roofline = {"bound": "alu", "pipe": "fp64 (DFMA)", "achieved": achieved, "peak": fp64_peak,
@@ -397,9 +402,16 @@ def ours_arm(args, world, rank, local):
                     "peak_source": "measured: pes_fp64_peak DFMA microbenchmark (burst, all SMs), this run"}
     else:
         achieved = digit_flops / 2 / (mean_conv * 1e-3) / 1e12
-        roofline = {"bound": "alu", "pipe": "int (IMAD.WIDE 32x32+64)", "achieved": achieved, "peak": int_peak,
-                    "unit": "Tops/s", "frac": achieved / int_peak,
-                    "peak_source": "measured: pes_int_peak multiply-add microbenchmark (burst, all SMs), this run"}
+        derived = 8 * 4 * nsm * clk_max_mhz * 1e6 / 1e12 if clk_max_mhz else None
+        peak = derived if derived else int_peak
+        roofline = {"bound": "alu", "pipe": "int (IMAD.WIDE 32x32+64)", "achieved": achieved, "peak": peak,
+                    "unit": "Tops/s", "frac": achieved / peak,
+                    "peak_source": ("derived: 8 lanes/clock per SM sub-partition (a 32x32+64 multiply-add "
+                                    "occupies the heavy FMA pipe 4 clocks per warp, ncu) x 4 x SMs x max SM clock"
+                                    if derived else "measured: pes_int_peak (no clock reading)"),
+                    "peak_measured": {"value": int_peak, "frac": achieved / int_peak,
+                                      "source": "pes_int_peak: 8x8 outer products of shared-memory digit rows "
+                                                "(burst, all SMs), this run"}}
     roofline.update({"traffic": traffic_per_launch(info["conv_jobs"], arith), "work": work, "kernel_ms": mean_conv})
 
     # ---- the other multiply-accumulate pipe, kernel-only, same workload ----
@@ -434,6 +446,7 @@ def ours_arm(args, world, rank, local):
         "wall_s_timed_region": wall,
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],
+                 "staging_depth": plan.info()["staging"],
                  "smem_bytes": info["smem_bytes"], "digits": info["digits"]},
     }
     if not args.no_autograd:

@@ -72,8 +72,16 @@ typedef struct {
   int32_t with_vjp;    /* 1: also build the tables of pes_vjp (default 1) */
   int64_t timeout_ms;  /* bound on every device-side wait; 0 = default (60000) */
   int32_t profile;     /* 1: record CUDA events around each launch of a call (see pes_last_timing) */
-  int32_t autotune;    /* batches: 1 = time the candidate CTA shapes of every group on the first call and
-                          keep the fastest (cached in $PES_AUTOTUNE_CACHE, else ~/.cache/pes_autotune.txt) */
+  int32_t autotune;    /* 1 = on the first call, time the candidate launch shapes of the convolution
+                          kernel (threads per CTA, CTAs per SM, staging depth; for a batch, of every
+                          group) on the caller's data and keep the fastest (cached in
+                          $PES_AUTOTUNE_CACHE, else ~/.cache/pes_autotune.txt) */
+  int32_t staging;     /* staging depth of the convolution kernel: 1 = a CTA stages a job's operands
+                          after rounding the previous job; 2 = it claims the next job and, if that
+                          job's operands are complete, stages them while rounding the current one
+                          (a separate staging buffer: more shared memory); 0 = automatic (1, and both
+                          are tried when autotuning) */
+  int32_t pad;
 } pes_options;
 
 /* Fill *opt with the defaults. */
@@ -157,7 +165,7 @@ typedef struct {
   int32_t threads;         /* threads per CTA */
   int32_t smem_bytes;      /* dynamic shared memory per CTA */
   int32_t arith;           /* PES_ARITH_FP64 or PES_ARITH_INT: the pipe the plan uses */
-  int32_t pad;
+  int32_t staging;         /* staging depth in use (1 or 2) */
 } pes_plan_info;
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);
@@ -209,7 +217,10 @@ pes_status pes_md_costs(int32_t k, double* mul_ops, double* add_ops);
 pes_status pes_fp64_peak(int32_t repeats, double* tflops);
 
 /* Measured throughput of 32x32->64-bit integer multiply-add (the digit product
- * of PES_ARITH_INT) on the current device, in tera-operations per second. */
+ * of PES_ARITH_INT) on the current device, in tera-operations per second, in
+ * the form the convolution kernel issues it: 64-bit accumulators and operands
+ * read from shared memory (an 8 x 8 outer product per pair of 8-digit rows), so
+ * that the compiler cannot replace the products by additions. */
 pes_status pes_int_peak(int32_t repeats, double* tops);
 
 /* ---- job compiler introspection (host only; no GPU needed) --------------------- */

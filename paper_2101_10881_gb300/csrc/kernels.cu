@@ -119,6 +119,10 @@ __device__ __forceinline__ void set_error(Ctrl* ctrl, int code, long long d0, lo
   atomicExch(&ctrl->abort, 1);
 }
 
+__device__ __forceinline__ bool is_done(const DagArgs& a, int dep, int epoch) {
+  return dep < 0 || ld_acquire(a.flags + dep) == epoch;
+}
+
 // Bounded wait until job `dep` of this call has completed.
 __device__ bool wait_done(const DagArgs& a, int dep, int epoch, int job) {
   if (dep < 0) return true;
@@ -140,7 +144,7 @@ __device__ bool wait_done(const DagArgs& a, int dep, int epoch, int job) {
 // ---------------------------------------------------------------------------
 
 struct DagLayout {
-  size_t raw, xdig, ydig, gx, gy, gs, bar, misc, total;
+  size_t raw, exch, xdig, ydig, gx, gy, gs, bar, misc, total;
 };
 
 // Row strides of the digit arrays (in digits).  Integer variant: an X row is L
@@ -153,13 +157,24 @@ __host__ __device__ constexpr int y_stride(int L, bool intv) {
   return intv ? (((L + 3) / 4) % 2 == 1 ? (L + 3) / 4 * 4 : (L + 3) / 4 * 4 + 4) : (L | 1);
 }
 
-__host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int smax, int dmax) {
+// Staging depth 1: the staged limb planes of a job share their bytes with the
+// exchange rows (the limbs are converted to digits before the rows are
+// zeroed).  Depth 2: separate buffers, so that the next job's operands can be
+// staged while the exchange rows of the current one are still being rounded.
+__host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int smax, int dmax, int depth) {
   const int digit_bytes = intv ? 4 : 8;
   DagLayout o;
   size_t raw_bytes = size_t(2) * K * smax * sizeof(double);
   size_t exch_bytes = size_t(dmax + 1) * (L + 1) * sizeof(unsigned long long);
+  size_t off = 0;
   o.raw = 0;
-  size_t off = align_up(raw_bytes > exch_bytes ? raw_bytes : exch_bytes, 128);
+  if (depth >= 2) {
+    o.exch = align_up(raw_bytes, 128);
+    off = align_up(o.exch + exch_bytes, 128);
+  } else {
+    o.exch = 0;
+    off = align_up(raw_bytes > exch_bytes ? raw_bytes : exch_bytes, 128);
+  }
   o.xdig = off;
   off = align_up(off + size_t(smax) * x_stride(L, intv) * digit_bytes, 16);
   o.ydig = off;
@@ -183,7 +198,7 @@ __device__ __forceinline__ long long conv_start(long long j) { return j * (j + 1
 __device__ __forceinline__ long long corr_start(long long j, long long d) { return j * (d + 1) - j * (j - 1) / 2; }
 
 template <int K, bool INTV>
-__global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
+__global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1) dag_kernel(DagArgs a) {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
   using AccT = typename std::conditional<INTV, long long, double>::type;
   constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
@@ -196,9 +211,9 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
   constexpr int R = INTV ? static_cast<int>((1LL << (63 - 2 * (B - 1))) / L) : 128 / L;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax);
+  const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax, a.depth);
   double* raw = reinterpret_cast<double*>(smem + lay.raw);
-  unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.raw);
+  unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.exch);
   DigitT* xdig = reinterpret_cast<DigitT*>(smem + lay.xdig);
   DigitT* ydig = reinterpret_cast<DigitT*>(smem + lay.ydig);
   int32_t* gx = reinterpret_cast<int32_t*>(smem + lay.gx);
@@ -221,17 +236,65 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
   __syncthreads();
   const int epoch = *reinterpret_cast<volatile int32_t*>(&a.ctrl->epoch);
   uint32_t phase = 0;
+  // Staging depth 2: one thread with no coefficient to round (the last one,
+  // when the CTA is wider than the largest series) claims the next job while
+  // the others round the current one, and stages it at once if its operands
+  // are ready.  It never waits there: the job it would wait for may be the one
+  // this CTA has not released yet.  A job claimed but not staged is staged,
+  // with a bounded wait, at the top of the next iteration.
+  const bool ahead = a.depth >= 2;
+  const int stager = (ahead && T > a.dmax + 1) ? T - 1 : 0;
 
+  // misc[0]: claimed job, misc[1]: failure, misc[2]: its operands are being staged
+  auto claim = [&]() {
+    misc[0] = atomicAdd(&a.ctrl->next[a.counter], 1);
+    misc[1] = 0;
+    misc[2] = 0;
+  };
+  // Start the TMA bulk copies of the claimed job's two operand series (2k limb
+  // planes) into `raw` once both are complete; `blocking`: wait (bounded) for
+  // them, else only look.
+  auto stage = [&](bool blocking) {
+    const int job = misc[0];
+    if (job >= a.njobs) return;
+    const ConvJob jb = a.jobs[job];
+    const InstInfo in = a.inst[jb.inst];
+    if (INTV && (in.d + 2) / 2 > T) {  // at least one lane per coefficient pair: the plan sizes the CTA
+      if (blocking) {
+        set_error(a.ctrl, 6, job, in.d);
+        misc[1] = 1;
+      }
+      return;
+    }
+    if (blocking) {
+      if (!wait_done(a, jb.dep1, epoch, job) || !wait_done(a, jb.dep2, epoch, job)) {
+        misc[1] = 1;
+        return;
+      }
+    } else if (!is_done(a, jb.dep1, epoch) || !is_done(a, jb.dep2, epoch)) {
+      return;
+    }
+    const long long ls = in.ws_lstride;
+    const double* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * in.S;
+    const double* ys = a.ws + in.ws_base + static_cast<long long>(jb.in2) * in.S;
+    fence_proxy_async_global();
+    fence_proxy_async_shared();
+    const uint32_t bytes = static_cast<uint32_t>(in.S) * sizeof(double);
+    mbar_expect_tx(bar_addr, 2u * K * bytes);
+    const uint32_t raw_addr = smem_u32(raw);
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      bulk_g2s(raw_addr + static_cast<uint32_t>(l) * bytes, xs + l * ls, bytes, bar_addr);
+      bulk_g2s(raw_addr + static_cast<uint32_t>(K + l) * bytes, ys + l * ls, bytes, bar_addr);
+    }
+    misc[2] = 1;
+  };
+
+  bool claimed = false;  // the stager already claimed the next job
   for (;;) {
     if (tid == 0) {
-      int job = atomicAdd(&a.ctrl->next[a.counter], 1);
-      int bad = 0;
-      if (job < a.njobs) {
-        const ConvJob jb = a.jobs[job];
-        if (!wait_done(a, jb.dep1, epoch, job) || !wait_done(a, jb.dep2, epoch, job)) bad = 1;
-      }
-      misc[0] = job;
-      misc[1] = bad;
+      if (!claimed) claim();
+      if (!misc[2]) stage(true);
     }
     __syncthreads();
     const int job = misc[0];
@@ -239,29 +302,11 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
     const ConvJob jb = a.jobs[job];
     const InstInfo in = a.inst[jb.inst];
     const int d = in.d;
-    if (INTV && (d + 2) / 2 > T) {  // at least one lane per coefficient pair: the plan sizes the CTA
-      if (tid == 0) set_error(a.ctrl, 6, job, d);
-      break;
-    }
     const int S = in.S;
     const long long ls = in.ws_lstride;
-    const double* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * S;
-    const double* ys = a.ws + in.ws_base + static_cast<long long>(jb.in2) * S;
     double* zs = a.ws + in.ws_base + static_cast<long long>(jb.out) * S;
 
-    // ---- stage both operand series (k limb planes each) with TMA bulk copies ----
-    if (tid == 0) {
-      fence_proxy_async_global();
-      fence_proxy_async_shared();
-      const uint32_t bytes = static_cast<uint32_t>(S) * sizeof(double);
-      mbar_expect_tx(bar_addr, 2u * K * bytes);
-      const uint32_t raw_addr = smem_u32(raw);
-#pragma unroll
-      for (int l = 0; l < K; ++l) {
-        bulk_g2s(raw_addr + static_cast<uint32_t>(l) * bytes, xs + l * ls, bytes, bar_addr);
-        bulk_g2s(raw_addr + static_cast<uint32_t>(K + l) * bytes, ys + l * ls, bytes, bar_addr);
-      }
-    }
+    // ---- the operand series (k limb planes each) land in shared memory ----
     const bool landed = mbar_wait(bar_addr, phase, a.timeout_ns);
     if (!__syncthreads_and(landed)) {
       if (tid == 0) set_error(a.ctrl, kStatusTimeout, job, -2);
@@ -360,11 +405,13 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
       if constexpr (INTV) {
         // Coefficients j and d-j share d+2 terms (the middle coefficient d/2,
         // when d+1 is odd, forms a group of its own).  The Q = T / groups lanes
-        // of a group split its terms, walked as: the short coefficient from its
-        // first term, then the long one from its last term backwards.  At every
-        // step all lanes with the same rank q inside their group read the same
-        // X row (a broadcast) and consecutive Y rows, and every lane runs about
-        // (d+2)/Q terms.
+        // of a group (consecutive lanes) split its terms, walked as: the short
+        // coefficient from its first term, then the long one from its last term
+        // backwards.  At every step all lanes with the same rank q inside their
+        // group read the same X row (a broadcast) and consecutive Y rows, and
+        // every lane runs about (d+2)/Q terms.  Only the lane holding a group's
+        // short-to-long switch flushes there; the periodic flushes fall on the
+        // same steps in every lane, so a warp runs them together.
         const int P = (d + 1) / 2;                 // pairs (j, d - j), j < d - j
         const bool has_mid = ((d + 1) & 1) != 0;   // the middle coefficient d/2 pairs with itself
         const int groups = P + (has_mid ? 1 : 0);
@@ -386,6 +433,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
         const int p0 = q * H;
         const int p1 = min(p0 + H, tp);
         int jcur = p0 < ns ? cs : cl;
+        int left = R;  // terms the accumulators take before the next flush
         for (int pos = p0; pos < p1; ++pos) {
           int j, i;
           if (pos < ns) {
@@ -398,11 +446,14 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
           const int ix = conv ? i : j + i;
           const int iy = conv ? j - i : i;
           term(ix, iy, gs[j] - gx[ix] - gy[iy]);
+          --left;
           if (pos == ns - 1 && pos + 1 < p1) {
             flush(cs);  // this lane leaves the short coefficient
             jcur = cl;
-          } else if ((pos - p0 + 1) % R == 0) {
+          }
+          if (left == 0) {  // the same steps in every lane (not reset by the switch)
             flush(jcur);
+            left = R;
           }
         }
         if (p1 > p0) flush(jcur);
@@ -447,6 +498,10 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
       }
     }
     __syncthreads();
+    if (ahead && tid == stager) {
+      claim();
+      stage(false);
+    }
 
     // ---- one output coefficient per thread: round the exact sum to k limbs ----
     for (int j = tid; j <= d; j += T) {
@@ -467,6 +522,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), 1) dag_kernel(DagArgs a) {
       fence_proxy_async_global();
       st_release(a.flags + job, epoch);
     }
+    claimed = ahead;
   }
 }
 
@@ -606,15 +662,29 @@ __global__ void fp64_peak_kernel(double* sink, int iters, double a, double b) {
   if (s == 12345.678) sink[blockIdx.x] = s;  // keeps the chains alive
 }
 
-// IMAD.WIDE throughput: 8 independent 32x32->64-bit multiply-add chains per thread.
-__global__ void int_peak_kernel(long long* sink, int iters, int a, int b) {
+// 32x32->64 multiply-add throughput in the form the convolution kernel issues:
+// 64-bit accumulators and multiplicands read from shared memory.  Every
+// iteration loads two rows of 8 digits (the row index changes with the
+// iteration, so the compiler cannot hoist the products out of the loop; with
+// constant operands it turns the loop into 64-bit additions, which run on
+// another pipe) and accumulates their 8 x 8 outer product into 8 accumulators.
+__global__ void __launch_bounds__(256) int_peak_kernel(long long* sink, int iters, int a, int b) {
+  __shared__ __align__(16) int32_t rows[64 * 8];
+  for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) rows[t] = static_cast<int32_t>((t * 2654435761u) & 0x7FFFFFF) - a;
+  __syncthreads();
   long long acc[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) acc[i] = threadIdx.x + i;
-  const int x = a + static_cast<int>(threadIdx.x), y = b - static_cast<int>(threadIdx.x);
+  for (int i = 0; i < 8; ++i) acc[i] = 7LL * threadIdx.x + i + b;
   for (int it = 0; it < iters; ++it) {
+    const int4* p = reinterpret_cast<const int4*>(rows + ((it + threadIdx.x) & 63) * 8);
+    const int4* q = reinterpret_cast<const int4*>(rows + ((7 * it + threadIdx.x) & 63) * 8);
+    const int4 u = p[0], v = p[1], w = q[0], z = q[1];
+    const int X[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+    const int Y[8] = {w.x, w.y, w.z, w.w, z.x, z.y, z.z, z.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[i]) : "r"(x), "r"(y));
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[i]) : "r"(X[i]), "r"(Y[j]));
   }
   long long s = 0;
 #pragma unroll
@@ -645,8 +715,8 @@ void* dag_kernel_ptr(int k, int arith) {
 
 int digits_of_k(int k, int arith) { return digits_for_k(k, arith == ARITH_INT ? DIGIT_BITS_INT : DIGIT_BITS); }
 
-size_t dag_smem_bytes(int k, int arith, int smax, int dmax) {
-  return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax).total;
+size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth) {
+  return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax, depth).total;
 }
 
 // The dynamic shared-memory limit is a property of the kernel function on a
@@ -677,7 +747,7 @@ cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* block
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st) {
   void* fn = dag_kernel_ptr(k, arith);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = dag_smem_bytes(k, arith, a.smax, a.dmax);
+  const size_t smem = dag_smem_bytes(k, arith, a.smax, a.dmax, a.depth);
   DagArgs copy = a;
   void* args[] = {&copy};
   return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);

@@ -35,6 +35,8 @@ struct DagArgs {
   Ctrl* ctrl;
   int32_t smax;             // largest padded stride of the instances
   int32_t dmax;             // largest degree
+  int32_t depth;            // staging depth: 1, or 2 (next job staged while this one is rounded)
+  int32_t pad;
   long long timeout_ns;     // bound on every wait
 };
 
@@ -57,12 +59,17 @@ struct CopyArgs {
   double* dst[4];        // unpack: caller buffers by selector
 };
 
-// Threads per CTA of the DAG kernel: one lane per output coefficient, so at
-// least d+1; the register budget of each k caps it.
-__host__ __device__ constexpr int dag_max_threads(int k) { return k >= 8 ? 384 : k >= 4 ? 512 : 768; }
+// Threads per CTA of the DAG kernel: at least one lane per coefficient pair of
+// the largest degree; the register budget of each k caps it.  At k = 10 the cap
+// is 256 with two CTAs per SM guaranteed, which holds the kernel to 128
+// registers per thread (the multiply-accumulate loop keeps 21 64-bit
+// accumulators and a digit row in registers).
+__host__ __device__ constexpr int dag_max_threads(int k) { return k >= 10 ? 256 : k >= 8 ? 384 : k >= 4 ? 512 : 768; }
+__host__ __device__ constexpr int dag_min_ctas(int k) { return k >= 10 ? 2 : 1; }
 
-// Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax).
-size_t dag_smem_bytes(int k, int arith, int smax, int dmax);
+// Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax) at
+// staging depth 1 or 2.
+size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth);
 int digits_of_k(int k, int arith);
 
 // Launchers (return cudaError_t of the launch).

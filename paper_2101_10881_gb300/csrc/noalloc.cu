@@ -166,7 +166,7 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   STATIC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int arith = pes::ARITH_FP64;
   const int threads = 128;
-  const size_t smem = pes::dag_smem_bytes(k, arith, S, d);
+  const size_t smem = pes::dag_smem_bytes(k, arith, S, d, 1);
   if (smem > static_cast<size_t>(optin)) {
     set_error("degree too large for the shared-memory staging");
     return PES_EUNSUPPORTED_SIZE;
@@ -212,6 +212,7 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   da.ctrl = ctrl;
   da.smax = S;
   da.dmax = d;
+  da.depth = 1;
   da.timeout_ns = 60000LL * 1000000LL;
 
   pes::AddArgs aa{};

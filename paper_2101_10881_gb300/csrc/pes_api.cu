@@ -75,8 +75,9 @@ struct CopyTable {
 struct Exec {
   int32_t k = 0, arith = 0, threads = 128, ctas_per_sm = 0;
   int32_t smax = 0, dmax = 0;
+  int32_t depth = 1, staging = 0;  // staging depth in use; requested (0 = automatic)
   size_t smem = 0;
-  int32_t blocks_per_sm = 0, nsm = 0;
+  int32_t blocks_per_sm = 0, nsm = 0, optin = 0;
   long long timeout_ns = 0;
   pes::InstInfo* inst = nullptr;
   pes::Ctrl* ctrl = nullptr;
@@ -152,7 +153,6 @@ struct Exec {
     int dev = 0;
     PES_CUDA(cudaGetDevice(&dev));
     PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int optin = 0;
     PES_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     // integer variant: by default two lanes per coefficient pair (one lane per
     // output coefficient) of the largest degree, whole warps; at least one lane
@@ -169,7 +169,10 @@ struct Exec {
       return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(threads) +
                                              " threads per CTA; at most " + std::to_string(pes::dag_max_threads(k)) +
                                              " at k=" + std::to_string(k));
-    smem = pes::dag_smem_bytes(k, arith, smax, dmax);
+    // staging depth: 2 only when asked for and it fits (the autotuner tries both)
+    staging = o.staging;
+    depth = (staging == 2 && pes::dag_smem_bytes(k, arith, smax, dmax, 2) <= static_cast<size_t>(optin)) ? 2 : 1;
+    smem = pes::dag_smem_bytes(k, arith, smax, dmax, depth);
     if (smem > static_cast<size_t>(optin))
       return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(smem) +
                                              " bytes of shared memory at k=" + std::to_string(k));
@@ -192,11 +195,23 @@ struct Exec {
     return PES_OK;
   }
 
-  // threads per CTA and a cap on CTAs per SM (0: as many as fit) for later launches
-  pes_status configure(int32_t t, int32_t ctas_cap, JobList& L) {
+  // shared memory of the convolution kernel at staging depth `dp`, or 0 if it does not fit
+  size_t smem_at(int32_t dp) const {
+    const size_t b = pes::dag_smem_bytes(k, arith, smax, dmax, dp);
+    return b <= static_cast<size_t>(optin) ? b : 0;
+  }
+
+  // threads per CTA, a cap on CTAs per SM (0: as many as fit) and the staging
+  // depth for later launches
+  pes_status configure(int32_t t, int32_t ctas_cap, int32_t dp, JobList& L) {
+    const size_t b = smem_at(dp);
+    if (b == 0) return fail(PES_EUNSUPPORTED_SIZE, "staging depth does not fit in shared memory");
+    PES_CUDA(pes::dag_prepare(k, arith, b));
     int bps = 0;
-    PES_CUDA(pes::dag_occupancy(k, arith, t, smem, &bps));
+    PES_CUDA(pes::dag_occupancy(k, arith, t, b, &bps));
     if (bps < 1) return fail(PES_EUNSUPPORTED_SIZE, "configuration does not fit on an SM");
+    smem = b;
+    depth = dp;
     threads = t;
     blocks_per_sm = ctas_cap > 0 ? std::min(bps, ctas_cap) : bps;
     L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(
@@ -215,6 +230,7 @@ struct Exec {
     a.ctrl = ctrl;
     a.smax = smax;
     a.dmax = dmax;
+    a.depth = depth;
     a.timeout_ns = timeout_ns;
     return a;
   }
@@ -299,6 +315,7 @@ pes_status parse_options(const pes_options* opt, pes_options& o) {
   if (o.threads < 0 || o.threads > 1024 || o.threads % 32 != 0)
     return fail(PES_EINVAL, "threads must be 0 (automatic) or a multiple of 32 up to 1024");
   if (o.ctas_per_sm < 0) return fail(PES_EINVAL, "ctas_per_sm must be >= 0");
+  if (o.staging < 0 || o.staging > 2) return fail(PES_EINVAL, "staging must be 0, 1 or 2");
   return PES_OK;
 }
 
@@ -339,23 +356,24 @@ std::string autotune_cache_file() {
   return std::string(home ? home : "/tmp") + "/.cache/pes_autotune.txt";
 }
 
-bool tune_lookup(const std::string& key, int32_t* threads, int32_t* ctas) {
+bool tune_lookup(const std::string& key, int32_t* threads, int32_t* ctas, int32_t* depth) {
   FILE* f = std::fopen(autotune_cache_file().c_str(), "r");
   if (!f) return false;
-  char kb[256];
-  int t = 0, c = 0;
+  char line[512], kb[256];
+  int t = 0, c = 0, dp = 0;
   bool found = false;
-  while (std::fscanf(f, "%255s %d %d", kb, &t, &c) == 3)
-    if (key == kb) {
+  while (std::fgets(line, sizeof(line), f))
+    if (std::sscanf(line, "%255s %d %d %d", kb, &t, &c, &dp) == 4 && key == kb) {
       *threads = t;
       *ctas = c;
+      *depth = dp;
       found = true;
     }
   std::fclose(f);
   return found;
 }
 
-void tune_store(const std::string& key, int32_t threads, int32_t ctas) {
+void tune_store(const std::string& key, int32_t threads, int32_t ctas, int32_t depth) {
   const std::string path = autotune_cache_file();
   const size_t slash = path.find_last_of('/');
   if (slash != std::string::npos)
@@ -363,7 +381,7 @@ void tune_store(const std::string& key, int32_t threads, int32_t ctas) {
       if (i == slash || path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
   FILE* f = std::fopen(path.c_str(), "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d\n", key.c_str(), threads, ctas);
+  std::fprintf(f, "%s %d %d %d\n", key.c_str(), threads, ctas, depth);
   std::fclose(f);
 }
 
@@ -372,8 +390,8 @@ void tune_store(const std::string& key, int32_t threads, int32_t ctas) {
 // shape, so the trials may run on the caller's data.  Cached by `key`.
 template <class Run>
 pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cudaStream_t st) {
-  int32_t bt = E.threads, bc = 0;
-  if (!tune_lookup(key, &bt, &bc)) {
+  int32_t bt = E.threads, bc = 0, bd = E.depth;
+  if (!tune_lookup(key, &bt, &bc, &bd)) {
     const int32_t base = E.threads;
     std::vector<int32_t> ts{base};
     if (E.arith == pes::ARITH_INT) {
@@ -382,42 +400,50 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
     } else {
       ts.push_back(256);
     }
+    std::vector<int32_t> depths{E.depth};
+    if (E.staging == 0) depths = {1, 2};
     cudaEvent_t e0, e1;
     PES_CUDA(cudaEventCreate(&e0));
     PES_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int32_t t : ts) {
-      int occ = 0;
-      PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, E.smem, &occ));
-      for (int32_t c = std::max(1, occ); c >= std::max(1, occ - 1); --c) {
-        pes_status s = E.configure(t, c, L);
-        if (s != PES_OK) continue;
-        s = run(st);  // warm-up
-        if (s != PES_OK) return s;
-        PES_CUDA(cudaEventRecord(e0, st));
-        s = run(st);
-        if (s != PES_OK) return s;
-        PES_CUDA(cudaEventRecord(e1, st));
-        PES_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bt = t;
-          bc = c;
+    for (int32_t dp : depths) {
+      const size_t b = E.smem_at(dp);
+      if (b == 0) continue;
+      PES_CUDA(pes::dag_prepare(E.k, E.arith, b));
+      for (int32_t t : ts) {
+        int occ = 0;
+        PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, b, &occ));
+        for (int32_t c = std::max(1, occ); c >= std::max(1, occ - 1); --c) {
+          pes_status s = E.configure(t, c, dp, L);
+          if (s != PES_OK) continue;
+          s = run(st);  // warm-up
+          if (s != PES_OK) return s;
+          PES_CUDA(cudaEventRecord(e0, st));
+          s = run(st);
+          if (s != PES_OK) return s;
+          PES_CUDA(cudaEventRecord(e1, st));
+          PES_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            bt = t;
+            bc = c;
+            bd = dp;
+          }
         }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    tune_store(key, bt, bc);
+    tune_store(key, bt, bc, bd);
   }
-  return E.configure(bt, bc, L);
+  return E.configure(bt, bc, bd, L);
 }
 
 std::string tune_key(const Exec& E, int64_t njobs, uint64_t signature) {
   char key[200];
-  std::snprintf(key, sizeof(key), "k%d_a%d_t%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.dmax,
+  std::snprintf(key, sizeof(key), "v2_k%d_a%d_t%d_s%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.staging, E.dmax,
                 static_cast<long long>(njobs), static_cast<unsigned long long>(signature));
   return key;
 }
@@ -449,6 +475,8 @@ extern "C" void pes_default_options(pes_options* opt) {
   opt->timeout_ms = 60000;
   opt->profile = 0;
   opt->autotune = 0;
+  opt->staging = 0;
+  opt->pad = 0;
 }
 
 extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -564,9 +592,9 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
     if (ts != PES_OK) return ts;
     // the VJP job lists share the launch shape
     plan->vjp_fwd.grid = plan->vjp_m.grid = plan->vjp_corr.grid = 0;
-    E.configure(E.threads, E.blocks_per_sm, plan->vjp_fwd);
-    E.configure(E.threads, E.blocks_per_sm, plan->vjp_m);
-    E.configure(E.threads, E.blocks_per_sm, plan->vjp_corr);
+    E.configure(E.threads, E.blocks_per_sm, E.depth, plan->vjp_fwd);
+    E.configure(E.threads, E.blocks_per_sm, E.depth, plan->vjp_m);
+    E.configure(E.threads, E.blocks_per_sm, E.depth, plan->vjp_corr);
   }
   PES_CUDA(E.mark(0, st));
   PES_CUDA(pes::launch_prologue(E.ctrl, st));
@@ -651,6 +679,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->threads = plan->ex.threads;
   info->smem_bytes = static_cast<int32_t>(plan->ex.smem);
   info->arith = plan->ex.arith;
+  info->staging = plan->ex.depth;
   return PES_OK;
 }
 
@@ -976,6 +1005,7 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->threads = E0.threads;
   info->smem_bytes = static_cast<int32_t>(E0.smem);
   info->arith = E0.arith;
+  info->staging = E0.depth;
   return PES_OK;
 }
 
@@ -1059,7 +1089,7 @@ extern "C" pes_status pes_int_peak(int32_t repeats, double* tops) {
   PES_CUDA(cudaGetDevice(&dev));
   PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   long long* sink = nullptr;
-  const int threads = 256, blocks = nsm * 4, iters = 65536;
+  const int threads = 256, blocks = nsm * 4, iters = 8192;
   PES_CUDA(cudaMalloc(&sink, sizeof(long long) * static_cast<size_t>(blocks)));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1080,7 +1110,7 @@ extern "C" pes_status pes_int_peak(int32_t repeats, double* tops) {
   cudaEventDestroy(e1);
   cudaFree(sink);
   if (e != cudaSuccess) return cuda_fail(e, "int peak kernel");
-  *tops = static_cast<double>(blocks) * threads * iters * 8.0 / (static_cast<double>(best) * 1e-3) / 1e12;
+  *tops = static_cast<double>(blocks) * threads * iters * 64.0 / (static_cast<double>(best) * 1e-3) / 1e12;
   return PES_OK;
 }
 

@@ -105,6 +105,49 @@ def test_ragged_degree_several_tiles(torch, threads):
     assert info["conv_jobs"] == 12 + 3 + 1 + 6 + 9
 
 
+@pytest.mark.parametrize("k,dmax", [(10, 487), (8, 591), (2, 1023)])
+def test_maximum_degree(torch, k, dmax):
+    """The largest degree one job's staging takes in the integer variant (both
+    operand series, their digits and the exchange rows in one CTA's shared
+    memory; the API caps d at 1023), every output coefficient against the
+    oracle; one degree more is rejected."""
+    rng = np.random.default_rng(4000 + k)
+    supp, n = [[0, 1], [1, 2, 3]], 4
+    prob = synth.Problem("dmax", n, dmax, k, supp, random_md(rng, k, (3, dmax + 1)),
+                         random_md(rng, k, (n, dmax + 1)))
+    v, g, plan = run(torch, prob)
+    assert plan.info()["arith_name"] == "int"
+    rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
+    assert normwise_err(v, rv) <= TOL[k]
+    assert normwise_err(g, rg) <= TOL[k]
+    assert normalised(v) and normalised(g)
+    with pytest.raises(pes.PesError) as e:
+        pes.Plan(supp, n, dmax + 1, k)
+    assert e.value.code == 7
+
+
+@pytest.mark.parametrize("threads", [96, 192, 256])
+def test_staging_depths_agree(torch, threads):
+    """Staging depth 2 (the next job claimed, and staged when its operands are
+    complete, while the current one is rounded) gives the same bits as depth 1,
+    whether the staging thread has no coefficient of its own (threads > d+1) or
+    is thread 0; a single long monomial makes consecutive jobs depend on each
+    other, so the next job is often not ready when claimed."""
+    k, d = 4, 152
+    rng = np.random.default_rng(77)
+    supp = [list(range(12)), [0, 3, 5], [2, 7], [1, 4, 6, 8, 9, 10, 11]]
+    n = 12
+    prob = synth.Problem("staging", n, d, k, supp, random_md(rng, k, (len(supp) + 1, d + 1)),
+                         random_md(rng, k, (n, d + 1)))
+    v1, g1, p1 = run(torch, prob, threads=threads, staging=1)
+    v2, g2, p2 = run(torch, prob, threads=threads, staging=2)
+    assert p1.info()["staging"] == 1 and p2.info()["staging"] == 2
+    assert np.array_equal(v1, v2) and np.array_equal(g1, g2)
+    rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
+    assert normwise_err(v2, rv) <= TOL[k]
+    assert normwise_err(g2, rg) <= TOL[k]
+
+
 def test_config0_full(torch):
     """p1 at d=8 in double double, every output coefficient."""
     prob = synth.config0()
