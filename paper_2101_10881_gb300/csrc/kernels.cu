@@ -351,15 +351,26 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       AccT A[L];
 #pragma unroll
       for (int t = 0; t < L; ++t) A[t] = 0;
+      // Add the accumulators into the exchange row of coefficient jj: A[t]
+      // belongs to word t+1 (word 0 is headroom above the grid's top digit).
+      // One flush may carry up to 2^63 per accumulator, so the values are first
+      // carried in registers: word t+1 takes the low B bits of A[t] plus the
+      // part of A[t+1] above its low B bits, word 0 the part of A[0] above B
+      // bits.  No word then takes more than about 2^(64-B) per flush, and the
+      // words stay exact however many flushes they receive.
       auto flush = [&](int jj) {
-        unsigned long long* row = exch + jj * (L + 1) + 1;
+        unsigned long long* row = exch + jj * (L + 1);
+        long long hi_next = 0;  // part of A[t+1] above its low B bits
 #pragma unroll
-        for (int t = 0; t < L; ++t) {
+        for (int t = L - 1; t >= 0; --t) {
           long long v;
           if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
-          if (v != 0) atomicAdd(row + t, static_cast<unsigned long long>(v));
+          const long long w = (v & ((1LL << B) - 1)) + hi_next;
+          hi_next = v >> B;  // arithmetic shift: v = hi * 2^B + lo
+          if (w != 0) atomicAdd(row + t + 1, static_cast<unsigned long long>(w));
           A[t] = 0;
         }
+        if (hi_next != 0) atomicAdd(row, static_cast<unsigned long long>(hi_next));
       };
       // one term x_ix * y_iy of output coefficient j, delta digits below its grid
       auto term = [&](int ix, int iy, int delta) {

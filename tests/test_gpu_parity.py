@@ -148,6 +148,36 @@ def test_staging_depths_agree(torch, threads):
     assert normwise_err(g2, rg) <= TOL[k]
 
 
+def max_digit_value(k):
+    """A k-double whose 28-bit digits, on the grid of its leading limb, are all
+    2^27 - 1 (up to the rounding of the last limb): the largest same-signed digit
+    products the integer variant's accumulators can meet."""
+    from fractions import Fraction
+    nd = (53 * k) // 28 + 1
+    f = sum(Fraction(2 ** 27 - 1, 2 ** (28 * p)) for p in range(1, nd + 1))
+    return np.array(synth.round_fraction_to_limbs(f, k))
+
+
+@pytest.mark.parametrize("arith", ["int", "fp64"])
+@pytest.mark.parametrize("k", [2, 10])
+def test_same_signed_maximal_digits(torch, k, arith):
+    """Every input coefficient has all its digits near 2^27 and the same sign, so
+    every digit product is close to 2^54 and nothing cancels: the exact digit sums
+    of a degree-152 convolution exceed 64 bits unless partial sums are carried
+    before they are added up."""
+    d, n = 152, 2
+    supp = [[0, 1]]
+    inputs = np.zeros((k, n, d + 1))
+    inputs[:, :, :] = max_digit_value(k)[:, None, None]
+    coeff = np.zeros((k, 2, d + 1))
+    coeff[0, 1, 0] = 1.0
+    prob = synth.Problem("maxdig", n, d, k, supp, coeff, inputs)
+    v, g, _ = run(torch, prob, arith=arith)
+    rv, rg = O.eval_grad(supp, n, coeff, inputs)
+    assert normwise_err(v, rv) <= TOL[k]
+    assert normwise_err(g, rg) <= TOL[k]
+
+
 def test_config0_full(torch):
     """p1 at d=8 in double double, every output coefficient."""
     prob = synth.config0()
