@@ -447,7 +447,7 @@ def ours_arm(args, world, rank, local):
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],
                  "staging_depth": plan.info()["staging"],
-                 "smem_bytes": info["smem_bytes"], "digits": info["digits"]},
+                 "smem_bytes": plan.info()["smem_bytes"], "digits": info["digits"]},
     }
     if not args.no_autograd:
         out["autograd"] = autograd_measure(args, dev, flush)

@@ -144,6 +144,57 @@ PES_HD void to_digits(const double* x, long long ls, int32_t g, int64_t (&D)[L])
   }
 }
 
+// The exact sum V = sum_{a=0..L} E[a] 2^(B (gs - 1 - a)) as L balanced digits
+// on a grid of its own: returns that grid g' and out[0..L-1] (digit p weighs
+// 2^(B (g' - 1 - p))), the top digit nonzero; GRID_ZERO and zero digits when
+// V = 0.  The digits are carried from the bottom into [-2^(B-1), 2^(B-1)), the
+// top word spills into up to two more digits above it (any 64-bit word fits),
+// leading zero digits are shifted out (a barrel shift over fixed indices, so
+// everything stays in registers), and the digits below the L kept ones are
+// dropped: being balanced, they weigh at most about half a unit of the last
+// kept digit.
+template <int L, int B>
+PES_HD int32_t sum_to_digits(int64_t (&E)[L + 1], int32_t gs, int32_t (&out)[L]) {
+  constexpr int64_t HALF = int64_t(1) << (B - 1);
+  constexpr int N = L + 3;  // F[0], F[1]: digits above E[0]; F[a + 2] = E[a]
+#pragma unroll
+  for (int a = L; a >= 1; --a) {
+    const int64_t c = (E[a] + HALF) >> B;
+    E[a] -= c << B;
+    E[a - 1] += c;
+  }
+  int64_t F[N];
+  {
+    const int64_t c1 = (E[0] + HALF) >> B;
+    const int64_t c2 = (c1 + HALF) >> B;
+    F[0] = c2;
+    F[1] = c1 - (c2 << B);
+    F[2] = E[0] - (c1 << B);
+  }
+#pragma unroll
+  for (int a = 1; a <= L; ++a) F[a + 2] = E[a];
+  int z = N;  // index of the first nonzero digit
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i)
+    if (F[i] != 0) z = i;
+  if (z == N) {
+#pragma unroll
+    for (int p = 0; p < L; ++p) out[p] = 0;
+    return GRID_ZERO;
+  }
+#pragma unroll
+  for (int b = 1; b < N; b <<= 1) {
+    if (z & b) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) F[i] = (i + b < N) ? F[i + b] : 0;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < L; ++p) out[p] = static_cast<int32_t>(F[p]);
+  // F[z] sat at a = z - 2, weighing 2^(B (gs + 1 - z)) = 2^(B (g' - 1))
+  return gs + 2 - z;
+}
+
 // Round the exact fixed-point sum V = sum_{a=0..L} E[a] 2^(B (L - a)) times
 // 2^(B gs - B (L + 1)) to K nonoverlapping limbs (each limb the nearest double
 // to the remainder, ties away from zero), written to out[l * ls].

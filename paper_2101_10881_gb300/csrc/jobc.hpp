@@ -16,12 +16,13 @@ namespace pes {
 // Job kinds.
 enum : int32_t { JOB_CONV = 0, JOB_CORR = 1 };
 
-// Where instance `inst` keeps series slot s, limb l, coefficient j (in doubles,
-// from the workspace base): ws_base + l * ws_lstride + s * S + j.
+// Where instance `inst` keeps series slot s (in int32 words from the workspace
+// base): slot s starts at ws_base + s * ws_sstride and holds S rows of digits
+// (coefficient j at row j, a fixed number of words per row), then the S grids.
 struct InstInfo {
   int64_t ws_base;
-  int64_t ws_lstride;
-  int32_t S;  // padded series stride (multiple of 8 doubles)
+  int64_t ws_sstride;
+  int32_t S;  // padded series length (multiple of 8 coefficients)
   int32_t d;  // truncation degree
 };
 
@@ -37,8 +38,9 @@ struct ConvJob {
 };
 
 // One output series of the addition stage: the exact sum of the series in
-// contrib[cbeg, cend) (slots of instance `inst`), written to destination buffer
-// `dst_sel` at dst_off + l * dst_lstride + j.
+// contrib[cbeg, cend) (slots of instance `inst`), rounded to k limbs and
+// written to destination buffer `dst_sel` at dst_off + l * dst_lstride + j, or,
+// for an addition into the workspace, kept in digit form in slot dst_off.
 struct AddOut {
   int64_t dst_off;
   int64_t dst_lstride;

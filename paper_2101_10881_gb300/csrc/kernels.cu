@@ -161,10 +161,17 @@ __host__ __device__ constexpr int y_stride(int L, bool intv) {
 // exchange rows (the limbs are converted to digits before the rows are
 // zeroed).  Depth 2: separate buffers, so that the next job's operands can be
 // staged while the exchange rows of the current one are still being rounded.
+// int32 words per workspace row of one coefficient: the integer variant's Y
+// row stride (so that a whole operand series lands as Y rows with one bulk
+// copy), else the digits rounded up to 16 bytes.
+__host__ __device__ constexpr int row_words(int L, bool intv) { return intv ? y_stride(L, true) : (L + 3) / 4 * 4; }
+
 __host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int smax, int dmax, int depth) {
   const int digit_bytes = intv ? 4 : 8;
   DagLayout o;
-  size_t raw_bytes = size_t(2) * K * smax * sizeof(double);
+  // staged digit rows: X only (Y rows land in place) for the integer variant,
+  // X and Y for the FP64 variant (converted to doubles)
+  size_t raw_bytes = size_t(intv ? 1 : 2) * smax * row_words(L, intv) * sizeof(int32_t);
   size_t exch_bytes = size_t(dmax + 1) * (L + 1) * sizeof(unsigned long long);
   size_t off = 0;
   o.raw = 0;
@@ -206,13 +213,14 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
   constexpr int XS = x_stride(L, INTV);
   constexpr int YS = y_stride(L, INTV);
   constexpr int XOFF = INTV ? L : 0;  // digits start after the zero prefix
+  constexpr int RW = row_words(L, INTV);  // int32 words per workspace row
   // accumulators stay exact for R terms (each term adds at most L products of
   // magnitude 2^(2B-2)): 2^53 for FP64, 2^63 for int64
   constexpr int R = INTV ? static_cast<int>((1LL << (63 - 2 * (B - 1))) / L) : 128 / L;
 
   extern __shared__ __align__(128) unsigned char smem[];
   const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax, a.depth);
-  double* raw = reinterpret_cast<double*>(smem + lay.raw);
+  int32_t* raw = reinterpret_cast<int32_t*>(smem + lay.raw);
   unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.exch);
   DigitT* xdig = reinterpret_cast<DigitT*>(smem + lay.xdig);
   DigitT* ydig = reinterpret_cast<DigitT*>(smem + lay.ydig);
@@ -274,19 +282,22 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
     } else if (!is_done(a, jb.dep1, epoch) || !is_done(a, jb.dep2, epoch)) {
       return;
     }
-    const long long ls = in.ws_lstride;
-    const double* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * in.S;
-    const double* ys = a.ws + in.ws_base + static_cast<long long>(jb.in2) * in.S;
+    // digit rows, then grids, of each operand series (int32 words)
+    const int32_t* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * in.ws_sstride;
+    const int32_t* ys = a.ws + in.ws_base + static_cast<long long>(jb.in2) * in.ws_sstride;
     fence_proxy_async_global();
     fence_proxy_async_shared();
-    const uint32_t bytes = static_cast<uint32_t>(in.S) * sizeof(double);
-    mbar_expect_tx(bar_addr, 2u * K * bytes);
-    const uint32_t raw_addr = smem_u32(raw);
-#pragma unroll
-    for (int l = 0; l < K; ++l) {
-      bulk_g2s(raw_addr + static_cast<uint32_t>(l) * bytes, xs + l * ls, bytes, bar_addr);
-      bulk_g2s(raw_addr + static_cast<uint32_t>(K + l) * bytes, ys + l * ls, bytes, bar_addr);
+    const uint32_t rbytes = static_cast<uint32_t>(in.S) * RW * sizeof(int32_t);
+    const uint32_t gbytes = static_cast<uint32_t>(in.S) * sizeof(int32_t);
+    mbar_expect_tx(bar_addr, 2u * (rbytes + gbytes));
+    bulk_g2s(smem_u32(raw), xs, rbytes, bar_addr);
+    if constexpr (INTV) {
+      bulk_g2s(smem_u32(ydig), ys, rbytes, bar_addr);
+    } else {
+      bulk_g2s(smem_u32(raw) + rbytes, ys, rbytes, bar_addr);
     }
+    bulk_g2s(smem_u32(gx), xs + static_cast<long long>(in.S) * RW, gbytes, bar_addr);
+    bulk_g2s(smem_u32(gy), ys + static_cast<long long>(in.S) * RW, gbytes, bar_addr);
     misc[2] = 1;
   };
 
@@ -303,10 +314,10 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
     const InstInfo in = a.inst[jb.inst];
     const int d = in.d;
     const int S = in.S;
-    const long long ls = in.ws_lstride;
-    double* zs = a.ws + in.ws_base + static_cast<long long>(jb.out) * S;
+    int32_t* zrows = a.ws + in.ws_base + static_cast<long long>(jb.out) * in.ws_sstride;
+    int32_t* zgrid = zrows + static_cast<long long>(S) * RW;
 
-    // ---- the operand series (k limb planes each) land in shared memory ----
+    // ---- the operand series (digit rows and grids) land in shared memory ----
     const bool landed = mbar_wait(bar_addr, phase, a.timeout_ns);
     if (!__syncthreads_and(landed)) {
       if (tid == 0) set_error(a.ctrl, kStatusTimeout, job, -2);
@@ -315,19 +326,28 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
     }
     phase ^= 1u;
 
-    // ---- exact digits of every staged coefficient ----
-    for (int c = tid; c <= d; c += T) {
-      int64_t D[L];
-      const int32_t g1 = grid_of<B>(raw[c]);
-      to_digits<K, L, B>(raw + c, S, g1, D);
-      gx[c] = g1;
-#pragma unroll
-      for (int p = 0; p < L; ++p) xdig[c * XS + XOFF + p] = static_cast<DigitT>(D[p]);
-      const int32_t g2 = grid_of<B>(raw[K * S + c]);
-      to_digits<K, L, B>(raw + K * S + c, S, g2, D);
-      gy[c] = g2;
-#pragma unroll
-      for (int p = 0; p < L; ++p) ydig[c * YS + p] = static_cast<DigitT>(D[p]);
+    // ---- staged digit rows into the layouts of the multiply-accumulate loop ----
+    if constexpr (INTV) {
+      // X rows behind their zero prefix (the Y rows and both grids are in place)
+      constexpr int V4 = RW / 4;
+      const int4* src = reinterpret_cast<const int4*>(raw);
+      for (int t = tid; t < (d + 1) * V4; t += T) {
+        const int c = t / V4, v = t - c * V4;
+        const int4 q = src[t];
+        int32_t* dst = xdig + c * XS + XOFF + 4 * v;
+        if (4 * v < L) dst[0] = q.x;
+        if (4 * v + 1 < L) dst[1] = q.y;
+        if (4 * v + 2 < L) dst[2] = q.z;
+        if (4 * v + 3 < L) dst[3] = q.w;
+      }
+    } else {
+      const int32_t* rx = raw;
+      const int32_t* ry = raw + S * RW;
+      for (int t = tid; t < (d + 1) * L; t += T) {
+        const int c = t / L, p = t - c * L;
+        xdig[c * XS + p] = static_cast<double>(rx[c * RW + p]);
+        ydig[c * YS + p] = static_cast<double>(ry[c * RW + p]);
+      }
     }
     __syncthreads();
 
@@ -514,18 +534,26 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       stage(false);
     }
 
-    // ---- one output coefficient per thread: round the exact sum to k limbs ----
+    // ---- one output coefficient per thread: the exact sum as L digits on its grid ----
     for (int j = tid; j <= d; j += T) {
       const int32_t g = gs[j];
+      int32_t o[L];
+      int32_t gz = GRID_ZERO;
       if (g < -100000) {
 #pragma unroll
-        for (int l = 0; l < K; ++l) zs[l * ls + j] = 0.0;
-        continue;
-      }
-      int64_t E[L + 1];
+        for (int p = 0; p < L; ++p) o[p] = 0;
+      } else {
+        int64_t E[L + 1];
 #pragma unroll
-      for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
-      from_digits<K, L, B>(E, g, zs + j, ls);
+        for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
+        gz = sum_to_digits<L, B>(E, g, o);
+      }
+      int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j) * RW);
+#pragma unroll
+      for (int v = 0; v < RW / 4; ++v)
+        dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
+                           4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
+      zgrid[j] = gz;
     }
     __syncthreads();
     if (tid == 0) {
@@ -541,30 +569,65 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
 // pack / unpack
 // ---------------------------------------------------------------------------
 
-__global__ void pack_kernel(CopyArgs a, int K) {
-  const long long item = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+// pack: one warp per series; every lane converts coefficients j = lane, lane+32,
+// ... of the caller's k-limb series into L balanced digits on the grid of the
+// leading limb and writes the digit row and grid into the workspace slot.
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256) pack_kernel(CopyArgs a) {
+  constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
+  constexpr int L = digits_for_k(K, B);
+  constexpr int RW = row_words(L, INTV);
+  const long long row = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (item >= static_cast<long long>(a.nrows) * K) return;
-  const int row = static_cast<int>(item / K);
-  const int l = static_cast<int>(item % K);
+  if (row >= a.nrows) return;
   const CopyRow r = a.rows[row];
   const InstInfo in = a.inst[r.inst];
-  const double* src = a.src[r.sel] + r.off + l * r.lstride;
-  double* dst = a.ws + in.ws_base + l * in.ws_lstride + static_cast<long long>(r.slot) * in.S;
-  for (int j = lane; j < in.S; j += 32) dst[j] = j <= in.d ? src[j] : 0.0;
+  const double* src = a.src[r.sel] + r.off;
+  int32_t* rows = a.ws + in.ws_base + static_cast<long long>(r.slot) * in.ws_sstride;
+  int32_t* grids = rows + static_cast<long long>(in.S) * RW;
+  for (int j = lane; j <= in.d; j += 32) {
+    int64_t D[L];
+    const int32_t g = grid_of<B>(src[j]);
+    to_digits<K, L, B>(src + j, r.lstride, g, D);
+    int4* dst = reinterpret_cast<int4*>(rows + static_cast<long long>(j) * RW);
+#pragma unroll
+    for (int v = 0; v < RW / 4; ++v)
+      dst[v] = make_int4(4 * v < L ? static_cast<int32_t>(D[4 * v]) : 0,
+                         4 * v + 1 < L ? static_cast<int32_t>(D[4 * v + 1]) : 0,
+                         4 * v + 2 < L ? static_cast<int32_t>(D[4 * v + 2]) : 0,
+                         4 * v + 3 < L ? static_cast<int32_t>(D[4 * v + 3]) : 0);
+    grids[j] = g;
+  }
 }
 
-__global__ void unpack_kernel(CopyArgs a, int K) {
-  const long long item = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+// unpack: one warp per series; every lane rounds coefficients of a workspace
+// series (digit form) to k limbs in the caller's buffer.
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256) unpack_kernel(CopyArgs a) {
+  constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
+  constexpr int L = digits_for_k(K, B);
+  constexpr int RW = row_words(L, INTV);
+  const long long row = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (item >= static_cast<long long>(a.nrows) * K) return;
-  const int row = static_cast<int>(item / K);
-  const int l = static_cast<int>(item % K);
+  if (row >= a.nrows) return;
   const CopyRow r = a.rows[row];
   const InstInfo in = a.inst[r.inst];
-  double* dst = a.dst[r.sel] + r.off + l * r.lstride;
-  const double* src = a.ws + in.ws_base + l * in.ws_lstride + static_cast<long long>(r.slot) * in.S;
-  for (int j = lane; j <= in.d; j += 32) dst[j] = src[j];
+  double* dst = a.dst[r.sel] + r.off;
+  const int32_t* rows = a.ws + in.ws_base + static_cast<long long>(r.slot) * in.ws_sstride;
+  const int32_t* grids = rows + static_cast<long long>(in.S) * RW;
+  for (int j = lane; j <= in.d; j += 32) {
+    const int32_t g = grids[j];
+    if (g < -100000) {
+#pragma unroll
+      for (int l = 0; l < K; ++l) dst[l * r.lstride + j] = 0.0;
+      continue;
+    }
+    int64_t E[L + 1];
+    E[0] = 0;
+#pragma unroll
+    for (int p = 0; p < L; ++p) E[p + 1] = rows[static_cast<long long>(j) * RW + p];
+    from_digits<K, L, B>(E, g + 1, dst + j, r.lstride);
+  }
 }
 
 __global__ void prologue_kernel(Ctrl* ctrl) {
@@ -579,9 +642,11 @@ __global__ void prologue_kernel(Ctrl* ctrl) {
 // addition stage: warp per output coefficient, exact digit sums, warp shuffles
 // ---------------------------------------------------------------------------
 
-template <int K>
+template <int K, bool INTV>
 __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
-  constexpr int L = digits_for_k(K);
+  constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
+  constexpr int L = digits_for_k(K, B);
+  constexpr int RW = row_words(L, INTV);
   const long long w = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (w >= items) return;
@@ -593,32 +658,31 @@ __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
   const AddOut ao = a.outs[lo];
   const int j = static_cast<int>(w - a.item_ptr[lo]);
   const InstInfo in = a.inst[ao.inst];
-  const long long ls = in.ws_lstride;
-  const double* base = a.ws + in.ws_base + j;
+  const int32_t* base = a.ws + in.ws_base;
+  const long long gofs = static_cast<long long>(in.S) * RW + j;  // grid of coefficient j within a slot
+  const long long rofs = static_cast<long long>(j) * RW;         // row of coefficient j within a slot
 
+  // common grid: the largest grid of the contributions
   int32_t gmax = 2 * GRID_ZERO;
   for (int c = ao.cbeg + lane; c < ao.cend; c += 32)
-    gmax = max(gmax, grid_of(base[static_cast<long long>(a.contrib[c]) * in.S]));
+    gmax = max(gmax, base[static_cast<long long>(a.contrib[c]) * in.ws_sstride + gofs]);
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
 
-  double* dst = a.dst[ao.dst_sel] + ao.dst_off + j;
-  if (gmax < -100000) {
-    if (lane < K) dst[lane * ao.dst_lstride] = 0.0;
-    return;
-  }
+  // every lane sums its contributions' digits, shifted to the common grid
   int64_t acc[L];
 #pragma unroll
   for (int p = 0; p < L; ++p) acc[p] = 0;
-  for (int c = ao.cbeg + lane; c < ao.cend; c += 32) {
-    int64_t D[L];
-    const double* x = base + static_cast<long long>(a.contrib[c]) * in.S;
-    double limbs[K];
+  if (gmax >= -100000) {
+    for (int c = ao.cbeg + lane; c < ao.cend; c += 32) {
+      const int32_t* slot = base + static_cast<long long>(a.contrib[c]) * in.ws_sstride;
+      const int sh = gmax - slot[gofs];  // digits below the common grid's top
+      if (sh >= L) continue;               // below the last digit
+      const int32_t* row = slot + rofs;
 #pragma unroll
-    for (int l = 0; l < K; ++l) limbs[l] = x[l * ls];
-    to_digits<K, L>(limbs, 1, gmax, D);
-#pragma unroll
-    for (int p = 0; p < L; ++p) acc[p] += D[p];
+      for (int q = 0; q < L; ++q)
+        if (q >= sh) acc[q] += row[q - sh];
+    }
   }
 #pragma unroll
   for (int p = 0; p < L; ++p) {
@@ -627,13 +691,35 @@ __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     acc[p] = v;
   }
-  if (lane == 0) {
-    int64_t E[L + 1];
+  if (lane != 0) return;
+  // acc[p] weighs 2^(B (gmax - 1 - p)): word p + 1 of a sum on grid gmax + 1
+  int64_t E[L + 1];
+  E[0] = 0;
 #pragma unroll
-    for (int p = 0; p < L; ++p) E[p] = acc[p];
-    E[L] = 0;
-    from_digits<K, L>(E, gmax, dst, ao.dst_lstride);
+  for (int p = 0; p < L; ++p) E[p + 1] = acc[p];
+  if (a.to_ws) {
+    int32_t* slot = a.ws + in.ws_base + ao.dst_off * in.ws_sstride;
+    int32_t o[L];
+    const int32_t gz = gmax < -100000 ? GRID_ZERO : sum_to_digits<L, B>(E, gmax + 1, o);
+    if (gmax < -100000) {
+#pragma unroll
+      for (int p = 0; p < L; ++p) o[p] = 0;
+    }
+    int4* dst = reinterpret_cast<int4*>(slot + rofs);
+#pragma unroll
+    for (int v = 0; v < RW / 4; ++v)
+      dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
+                         4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
+    slot[gofs] = gz;
+    return;
   }
+  double* dst = a.dst[ao.dst_sel] + ao.dst_off + j;
+  if (gmax < -100000) {
+#pragma unroll
+    for (int l = 0; l < K; ++l) dst[l * ao.dst_lstride] = 0.0;
+    return;
+  }
+  from_digits<K, L, B>(E, gmax + 1, dst, ao.dst_lstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -726,6 +812,8 @@ void* dag_kernel_ptr(int k, int arith) {
 
 int digits_of_k(int k, int arith) { return digits_for_k(k, arith == ARITH_INT ? DIGIT_BITS_INT : DIGIT_BITS); }
 
+int ws_row_words(int k, int arith) { return row_words(digits_of_k(k, arith), arith == ARITH_INT); }
+
 size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth) {
   return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax, depth).total;
 }
@@ -769,36 +857,50 @@ cudaError_t launch_prologue(Ctrl* ctrl, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const CopyArgs& a, int k, cudaStream_t st) {
-  const long long items = static_cast<long long>(a.nrows) * k;
-  if (items == 0) return cudaSuccess;
+// Launch KERNEL<K, INTV><<<grid, block, 0, st>>>(args...) for run-time k and arith.
+#define PES_DISPATCH_K_ARITH(KERNEL, k, arith, grid, block, st, ...)                        \
+  do {                                                                                      \
+    const bool iv_ = (arith) == ARITH_INT;                                                  \
+    switch (k) {                                                                            \
+      case 1: if (iv_) KERNEL<1, true><<<grid, block, 0, st>>>(__VA_ARGS__);                 \
+              else KERNEL<1, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;             \
+      case 2: if (iv_) KERNEL<2, true><<<grid, block, 0, st>>>(__VA_ARGS__);                 \
+              else KERNEL<2, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;             \
+      case 3: if (iv_) KERNEL<3, true><<<grid, block, 0, st>>>(__VA_ARGS__);                 \
+              else KERNEL<3, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;             \
+      case 4: if (iv_) KERNEL<4, true><<<grid, block, 0, st>>>(__VA_ARGS__);                 \
+              else KERNEL<4, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;             \
+      case 5: if (iv_) KERNEL<5, true><<<grid, block, 0, st>>>(__VA_ARGS__);                 \
+              else KERNEL<5, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;             \
+      case 8: if (iv_) KERNEL<8, true><<<grid, block, 0, st>>>(__VA_ARGS__);                 \
+              else KERNEL<8, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;             \
+      case 10: if (iv_) KERNEL<10, true><<<grid, block, 0, st>>>(__VA_ARGS__);               \
+               else KERNEL<10, false><<<grid, block, 0, st>>>(__VA_ARGS__); break;           \
+      default: return cudaErrorInvalidValue;                                                \
+    }                                                                                       \
+  } while (0)
+
+cudaError_t launch_pack(const CopyArgs& a, int k, int arith, cudaStream_t st) {
+  if (a.nrows == 0) return cudaSuccess;
   const int warps = 8;
-  pack_kernel<<<static_cast<unsigned>((items + warps - 1) / warps), warps * 32, 0, st>>>(a, k);
+  const unsigned grid = static_cast<unsigned>((a.nrows + warps - 1) / warps);
+  PES_DISPATCH_K_ARITH(pack_kernel, k, arith, grid, warps * 32, st, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const CopyArgs& a, int k, cudaStream_t st) {
-  const long long items = static_cast<long long>(a.nrows) * k;
-  if (items == 0) return cudaSuccess;
+cudaError_t launch_unpack(const CopyArgs& a, int k, int arith, cudaStream_t st) {
+  if (a.nrows == 0) return cudaSuccess;
   const int warps = 8;
-  unpack_kernel<<<static_cast<unsigned>((items + warps - 1) / warps), warps * 32, 0, st>>>(a, k);
+  const unsigned grid = static_cast<unsigned>((a.nrows + warps - 1) / warps);
+  PES_DISPATCH_K_ARITH(unpack_kernel, k, arith, grid, warps * 32, st, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_add(const AddArgs& a, int k, int64_t items, cudaStream_t st) {
+cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaStream_t st) {
   if (items == 0) return cudaSuccess;
   const int warps = 8;
   const unsigned grid = static_cast<unsigned>((items + warps - 1) / warps);
-  switch (k) {
-    case 1: add_kernel<1><<<grid, warps * 32, 0, st>>>(a, items); break;
-    case 2: add_kernel<2><<<grid, warps * 32, 0, st>>>(a, items); break;
-    case 3: add_kernel<3><<<grid, warps * 32, 0, st>>>(a, items); break;
-    case 4: add_kernel<4><<<grid, warps * 32, 0, st>>>(a, items); break;
-    case 5: add_kernel<5><<<grid, warps * 32, 0, st>>>(a, items); break;
-    case 8: add_kernel<8><<<grid, warps * 32, 0, st>>>(a, items); break;
-    case 10: add_kernel<10><<<grid, warps * 32, 0, st>>>(a, items); break;
-    default: return cudaErrorInvalidValue;
-  }
+  PES_DISPATCH_K_ARITH(add_kernel, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
   return cudaGetLastError();
 }
 

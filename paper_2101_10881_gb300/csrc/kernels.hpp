@@ -25,13 +25,14 @@ struct Ctrl {
   long long diag[4];  // diagnostics: [0] job that timed out, [1] waiting job
 };
 
+// The workspace holds every series in digit form (see InstInfo): int32 words.
 struct DagArgs {
   const ConvJob* jobs;
   int32_t njobs;
   int32_t counter;          // which Ctrl::next
   int32_t* flags;           // per job: epoch when done
   const InstInfo* inst;
-  double* ws;
+  int32_t* ws;
   Ctrl* ctrl;
   int32_t smax;             // largest padded stride of the instances
   int32_t dmax;             // largest degree
@@ -43,18 +44,19 @@ struct DagArgs {
 struct AddArgs {
   const AddOut* outs;
   int32_t nouts;
+  int32_t to_ws;            // 1: results in digit form into workspace slot dst_off of the instance
   const int64_t* item_ptr;  // nouts + 1 prefix sums of (d + 1) over outputs
   const int32_t* contrib;
   const InstInfo* inst;
-  const double* ws;
-  double* dst[2];
+  int32_t* ws;
+  double* dst[2];           // k-limb results: caller buffers by selector
 };
 
 struct CopyArgs {
   const CopyRow* rows;
   int32_t nrows;
   const InstInfo* inst;
-  double* ws;
+  int32_t* ws;
   const double* src[4];  // pack: caller buffers by selector
   double* dst[4];        // unpack: caller buffers by selector
 };
@@ -71,13 +73,19 @@ __host__ __device__ constexpr int dag_min_ctas(int k) { return k >= 10 ? 2 : 1; 
 // staging depth 1 or 2.
 size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth);
 int digits_of_k(int k, int arith);
+// int32 words of one workspace row (the digits of one coefficient, padded) and
+// of one workspace slot (a series of S coefficients: S rows, then S grids).
+int ws_row_words(int k, int arith);
+inline int64_t ws_slot_words(int k, int arith, int32_t S) {
+  return static_cast<int64_t>(S) * (ws_row_words(k, arith) + 1);
+}
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_prologue(Ctrl* ctrl, cudaStream_t st);
-cudaError_t launch_pack(const CopyArgs& a, int k, cudaStream_t st);
-cudaError_t launch_unpack(const CopyArgs& a, int k, cudaStream_t st);
+cudaError_t launch_pack(const CopyArgs& a, int k, int arith, cudaStream_t st);
+cudaError_t launch_unpack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st);
-cudaError_t launch_add(const AddArgs& a, int k, int64_t items, cudaStream_t st);
+cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaStream_t st);
 cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm);
 cudaError_t dag_prepare(int k, int arith, size_t smem);
 cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out,

@@ -118,8 +118,11 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   const int32_t S = pes::series_stride(d);
   const int64_t D1 = d + 1;
 
+  const int arith = pes::ARITH_FP64;
+  const int64_t sstride = pes::ws_slot_words(k, arith, S);
+
   // tables, in host memory first
-  std::vector<pes::InstInfo> inst{{0, static_cast<int64_t>(G.n_slots) * S, S, d}};
+  std::vector<pes::InstInfo> inst{{0, sstride, S, d}};
   std::vector<pes::CopyRow> rows;
   for (int32_t m = 0; m <= N; ++m) rows.push_back({m * D1, (N + 1) * D1, 0, 0, m, 0});
   for (int32_t i = 0; i < n; ++i) rows.push_back({i * D1, n * D1, 1, 0, 1 + N + i, 0});
@@ -149,7 +152,7 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   off = align256(off + G.add_src.size() * sizeof(int32_t));
   const size_t table_bytes = off;
   const size_t o_ws = off;
-  const size_t ws_bytes = static_cast<size_t>(k) * static_cast<size_t>(G.n_slots) * static_cast<size_t>(S) * sizeof(double);
+  const size_t ws_bytes = static_cast<size_t>(G.n_slots) * static_cast<size_t>(sstride) * sizeof(int32_t);
   if (o_ws + ws_bytes > kStaticScratchBytes) {
     set_error("problem needs " + std::to_string(o_ws + ws_bytes) + " bytes of scratch; the static array holds " +
               std::to_string(kStaticScratchBytes));
@@ -164,7 +167,6 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   STATIC_CUDA(cudaGetDevice(&dev));
   STATIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   STATIC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int arith = pes::ARITH_FP64;
   const int threads = 128;
   const size_t smem = pes::dag_smem_bytes(k, arith, S, d, 1);
   if (smem > static_cast<size_t>(optin)) {
@@ -192,7 +194,7 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
 
   auto* ctrl = reinterpret_cast<pes::Ctrl*>(base + o_ctrl);
   auto* dinst = reinterpret_cast<pes::InstInfo*>(base + o_inst);
-  double* ws = reinterpret_cast<double*>(base + o_ws);
+  int32_t* ws = reinterpret_cast<int32_t*>(base + o_ws);
 
   pes::CopyArgs ca{};
   ca.rows = reinterpret_cast<pes::CopyRow*>(base + o_rows);
@@ -228,9 +230,9 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(static_cast<long long>(per_sm) * nsm,
                                                                                static_cast<long long>(da.njobs))));
   STATIC_CUDA(pes::launch_prologue(ctrl, st));
-  STATIC_CUDA(pes::launch_pack(ca, k, st));
+  STATIC_CUDA(pes::launch_pack(ca, k, arith, st));
   if (da.njobs > 0) STATIC_CUDA(pes::launch_dag(da, k, arith, threads, grid, st));
-  STATIC_CUDA(pes::launch_add(aa, k, item_ptr.back(), st));
+  STATIC_CUDA(pes::launch_add(aa, k, arith, item_ptr.back(), st));
 
   if (status_out) {
     STATIC_CUDA(cudaStreamSynchronize(st));

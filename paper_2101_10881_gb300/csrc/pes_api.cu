@@ -72,6 +72,13 @@ struct CopyTable {
 };
 
 // Device state shared by single plans and batches.
+// The arithmetic a launch shape uses: PES_ARITH_AUTO takes the integer pipe
+// when one lane per coefficient pair of the largest degree fits in a CTA.
+int32_t resolve_arith(int32_t k, int32_t requested, int32_t dmax) {
+  if (requested != PES_ARITH_AUTO) return requested;
+  return (dmax + 2) / 2 <= pes::dag_max_threads(k) ? pes::ARITH_INT : pes::ARITH_FP64;
+}
+
 struct Exec {
   int32_t k = 0, arith = 0, threads = 128, ctas_per_sm = 0;
   int32_t smax = 0, dmax = 0;
@@ -81,8 +88,8 @@ struct Exec {
   long long timeout_ns = 0;
   pes::InstInfo* inst = nullptr;
   pes::Ctrl* ctrl = nullptr;
-  double* ws = nullptr;
-  size_t ws_doubles = 0;
+  int32_t* ws = nullptr;  // every series in digit form (see pes::InstInfo)
+  size_t ws_words = 0;
   std::vector<void*> owned;
   // profiling: events around the phases of the last call
   bool profile = false;
@@ -133,14 +140,11 @@ struct Exec {
     return s;
   }
 
-  pes_status init(int32_t k_, const pes_options& o, const std::vector<pes::InstInfo>& insts, size_t ws_doubles_) {
+  // `o.arith` must be resolved (resolve_arith) before the instances' workspace
+  // offsets are laid out: the words per series depend on the arithmetic.
+  pes_status init(int32_t k_, const pes_options& o, const std::vector<pes::InstInfo>& insts, size_t ws_words_) {
     k = k_;
     arith = o.arith;
-    if (arith == PES_ARITH_AUTO) {
-      int dm = 0;
-      for (const auto& in : insts) dm = std::max(dm, in.d);
-      arith = (dm + 2) / 2 <= pes::dag_max_threads(k_) ? pes::ARITH_INT : pes::ARITH_FP64;
-    }
     threads = o.threads;
     ctas_per_sm = o.ctas_per_sm;
     timeout_ns = (o.timeout_ms > 0 ? o.timeout_ms : 60000) * 1000000LL;
@@ -188,10 +192,10 @@ struct Exec {
     profile = o.profile != 0;
     if (profile)
       for (cudaEvent_t& e : ev) PES_CUDA(cudaEventCreate(&e));
-    ws_doubles = std::max<size_t>(ws_doubles_, 8);
-    e = cudaMalloc(&ws, ws_doubles * sizeof(double));
-    if (e != cudaSuccess) return fail(PES_ENOMEM, "workspace of " + std::to_string(ws_doubles * 8) + " bytes");
-    PES_CUDA(cudaMemset(ws, 0, ws_doubles * sizeof(double)));
+    ws_words = std::max<size_t>(ws_words_, 8);
+    e = cudaMalloc(&ws, ws_words * sizeof(int32_t));
+    if (e != cudaSuccess) return fail(PES_ENOMEM, "workspace of " + std::to_string(ws_words * 4) + " bytes");
+    PES_CUDA(cudaMemset(ws, 0, ws_words * sizeof(int32_t)));
     return PES_OK;
   }
 
@@ -240,17 +244,20 @@ struct Exec {
     return pes::launch_dag(dag_args(L, counter), k, arith, threads, L.grid, st);
   }
 
+  // sums into caller buffers (rounded to k limbs), or, with dst0 == dst1 ==
+  // nullptr, into workspace slots in digit form
   cudaError_t run_add(const AddTable& A, double* dst0, double* dst1, cudaStream_t st) const {
     pes::AddArgs a{};
     a.outs = A.outs;
     a.nouts = A.nouts;
+    a.to_ws = (dst0 == nullptr && dst1 == nullptr) ? 1 : 0;
     a.item_ptr = A.item_ptr;
     a.contrib = A.contrib;
     a.inst = inst;
     a.ws = ws;
     a.dst[0] = dst0;
     a.dst[1] = dst1;
-    return pes::launch_add(a, k, A.items, st);
+    return pes::launch_add(a, k, arith, A.items, st);
   }
 
   cudaError_t run_pack(const CopyTable& C, const double* s0, const double* s1, const double* s2,
@@ -263,7 +270,7 @@ struct Exec {
     a.src[0] = s0;
     a.src[1] = s1;
     a.src[2] = s2;
-    return pes::launch_pack(a, k, st);
+    return pes::launch_pack(a, k, arith, st);
   }
 
   cudaError_t run_unpack(const CopyTable& C, double* d0, double* d1, cudaStream_t st) const {
@@ -274,7 +281,7 @@ struct Exec {
     a.ws = ws;
     a.dst[0] = d0;
     a.dst[1] = d1;
-    return pes::launch_unpack(a, k, st);
+    return pes::launch_unpack(a, k, arith, st);
   }
 
   // record phase boundary i (0..4) of the current call
@@ -505,11 +512,12 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
   const pes::Program1& G = P->prog;
   const int32_t S = pes::series_stride(d);
   const int32_t slots = P->with_vjp ? G.n_slots_vjp : G.n_slots;
-  std::vector<pes::InstInfo> insts{{0, static_cast<int64_t>(slots) * S, S, d}};
-  const size_t ws = static_cast<size_t>(k) * static_cast<size_t>(slots) * static_cast<size_t>(S);
-  s = P->ex.init(k, o, insts, ws);
+  o.arith = resolve_arith(k, o.arith, d);
+  const int64_t sstride = pes::ws_slot_words(k, o.arith, S);
+  std::vector<pes::InstInfo> insts{{0, sstride, S, d}};
+  s = P->ex.init(k, o, insts, static_cast<size_t>(slots) * static_cast<size_t>(sstride));
   if (s != PES_OK) return s;
-  P->ws_bytes = static_cast<int64_t>(P->ex.ws_doubles * sizeof(double));
+  P->ws_bytes = static_cast<int64_t>(P->ex.ws_words * sizeof(int32_t));
 
   // forward jobs
   s = P->ex.make_joblist(P->fwd, G.jobs);
@@ -547,11 +555,10 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_m, monly);
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_corr, corr);
     if (s != PES_OK) return s;
-    // gradient series into the workspace (buffer 0 = workspace itself)
+    // gradient series into workspace slots (digit form)
     std::vector<pes::AddOut> gouts;
-    const int64_t lsw = static_cast<int64_t>(slots) * S;
     for (int32_t i = 0; i < n; ++i)
-      gouts.push_back({static_cast<int64_t>(G.slot_g0 + i) * S, lsw, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+      gouts.push_back({static_cast<int64_t>(G.slot_g0 + i), 0, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
     s = P->ex.make_add(P->add_g, gouts, G.add_src, insts);
     if (s != PES_OK) return s;
     std::vector<pes::CopyRow> urow{{0, D1, 2, 0, G.slot_u, 0}};
@@ -631,7 +638,7 @@ extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double
     PES_CUDA(E.run_dag(plan->vjp_fwd, 0, st));
     E.last_launches = 7;
   }
-  PES_CUDA(E.run_add(plan->add_g, E.ws, nullptr, st));
+  PES_CUDA(E.run_add(plan->add_g, nullptr, nullptr, st));
   PES_CUDA(E.run_dag(plan->vjp_corr, 1, st));
   PES_CUDA(E.mark(2, st));
   PES_CUDA(E.mark(3, st));
@@ -642,7 +649,7 @@ extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double
 
 extern "C" pes_status pes_workspace_io(pes_plan_t plan, void* buffer, int32_t to_buffer, void* stream) {
   if (!plan || !buffer) return fail(PES_EINVAL, "NULL argument");
-  const size_t bytes = plan->ex.ws_doubles * sizeof(double);
+  const size_t bytes = plan->ex.ws_words * sizeof(int32_t);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (to_buffer)
     PES_CUDA(cudaMemcpyAsync(buffer, plan->ex.ws, bytes, cudaMemcpyDeviceToDevice, st));
@@ -776,8 +783,7 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     prow += N[b] + 1;
     qidx += sup.ptr.back();
     const int32_t T = (2 * ((d[b] + 2) / 2) + 31) / 32 * 32;  // default CTA: one lane per coefficient
-    int32_t ar = o.arith;
-    if (ar == PES_ARITH_AUTO) ar = (d[b] + 2) / 2 <= pes::dag_max_threads(k) ? pes::ARITH_INT : pes::ARITH_FP64;
+    const int32_t ar = resolve_arith(k, o.arith, d[b]);
     classes[{ar, ar == pes::ARITH_INT ? T : 0}].push_back(b);
   }
 
@@ -792,8 +798,9 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
       const int32_t b = G->members[u];
       const int32_t S = pes::series_stride(d[b]);
       const int64_t slots = progs[static_cast<size_t>(b)].n_slots;
-      insts[u] = pes::InstInfo{wsbase, slots * S, S, d[b]};
-      wsbase += static_cast<int64_t>(k) * slots * S;
+      const int64_t sstride = pes::ws_slot_words(k, cls.first.first, S);
+      insts[u] = pes::InstInfo{wsbase, sstride, S, d[b]};
+      wsbase += slots * sstride;
     }
     pes_options og = o;
     og.arith = cls.first.first;
@@ -997,7 +1004,7 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->add_terms = batch->add_terms;
   info->add_jobs = batch->add_jobs;
   size_t ws = 0;
-  for (auto& G : batch->groups) ws += G->ex.ws_doubles * sizeof(double);
+  for (auto& G : batch->groups) ws += G->ex.ws_words * sizeof(int32_t);
   info->workspace_bytes = static_cast<int64_t>(ws);
   const Exec& E0 = batch->groups.front()->ex;
   info->digits = pes::digits_of_k(batch->k, E0.arith);

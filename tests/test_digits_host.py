@@ -32,6 +32,9 @@ def dh():
     dp = ctypes.POINTER(ctypes.c_double)
     lib.hd_conv.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int]
     lib.hd_sum.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.hd_conv_via_digits.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int]
+    lib.hd_sum_to_digits.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     return lib
 
 
@@ -44,6 +47,14 @@ def host_conv(dh, x, y, corr=False, bits=24):
     y = np.ascontiguousarray(y)
     z = np.empty_like(x)
     assert dh.hd_conv(x.shape[0], x.shape[1] - 1, _p(x), _p(y), _p(z), int(corr), bits) == 0
+    return z
+
+
+def host_conv_via_digits(dh, x, y, corr=False, bits=28):
+    x = np.ascontiguousarray(x)
+    y = np.ascontiguousarray(y)
+    z = np.empty_like(x)
+    assert dh.hd_conv_via_digits(x.shape[0], x.shape[1] - 1, _p(x), _p(y), _p(z), int(corr), bits) == 0
     return z
 
 
@@ -118,3 +129,67 @@ def test_sum_matches_oracle(dh, k):
         ref = O.round_sum(v.T.ravel(), k)
         assert normwise_err(out[:, None], ref[:, None]) <= TOL[k] * 1e-3
         assert normalised(out)
+
+
+@pytest.mark.parametrize("bits", [24, 28])
+@pytest.mark.parametrize("k", [1, 2, 10])
+def test_sum_to_digits_exact(dh, k, bits):
+    """Exact digit sums (words E[0..L] on grid gs) rewritten as L balanced digits
+    on a grid of their own: checked in Python integers against the exact value.
+    The top digit is nonzero, every digit lies in [-2^(B-1), 2^(B-1)), and the
+    digits dropped below the last kept one weigh at most half its unit (plus
+    one part in 2^B of it)."""
+    L = dh.hd_digits_bits(k, bits)
+    B = bits
+    rng = np.random.default_rng(900 + 10 * k + bits)
+    cases = []
+    for _ in range(300):
+        E = [int(v) for v in rng.integers(-(1 << 62), 1 << 62, size=L + 1)]
+        cases.append(E)
+    for _ in range(100):  # small words, cancellation, leading zeros
+        E = [int(v) for v in rng.integers(-(1 << 20), 1 << 20, size=L + 1)]
+        E[: int(rng.integers(0, L + 1))] = [0] * int(rng.integers(0, L + 1))
+        cases.append(E[: L + 1] + [0] * (L + 1 - len(E[: L + 1])))
+    cases.append([0] * (L + 1))
+    cases.append([0] * L + [1])
+    cases.append([-1] + [0] * L)
+    for E in cases:
+        gs = int(rng.integers(-50, 50))
+        out = (ctypes.c_int32 * L)()
+        grid = ctypes.c_int32()
+        arr = (ctypes.c_int64 * (L + 1))(*E)
+        assert dh.hd_sum_to_digits(k, bits, arr, gs, out, ctypes.byref(grid)) == 0
+        # exact values scaled by 2^(B (2 L + 4 - gs)) so that everything is an integer
+        sc = B * (2 * L + 4)
+        V = sum(e << (sc - B * (1 + a)) for a, e in enumerate(E))  # weight 2^(B (gs - 1 - a))
+        if V == 0:
+            assert grid.value == -(1 << 28) and all(o == 0 for o in out)
+            continue
+        g = grid.value
+        assert all(-(1 << (B - 1)) <= o < (1 << (B - 1)) for o in out)
+        assert out[0] != 0
+        # digit p weighs 2^(B (g - 1 - p)); in the scaled units: 2^(sc + B (g - gs - 1 - p))
+        W = 0
+        for p in range(L):
+            e = sc + B * (g - gs - 1 - p)
+            W += out[p] << e if e >= 0 else 0
+            assert e >= 0
+        unit = 1 << (sc + B * (g - gs - L))
+        assert 2 * abs(V - W) <= unit + (unit >> (B - 1))
+
+
+@pytest.mark.parametrize("bits", [24, 28])
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("d", [0, 8, 40])
+def test_conv_via_digits_matches_oracle(dh, k, d, bits):
+    """A product kept in digit form (the workspace form of intermediate series)
+    and rounded to k limbs at the end agrees with the oracle's product."""
+    rng = np.random.default_rng(300 + 10 * k + d)
+    x = random_md(rng, k, (d + 1,)) * np.ldexp(1.0, rng.integers(-60, 60, size=d + 1))
+    y = random_md(rng, k, (d + 1,))
+    for corr in (False, True):
+        z = host_conv_via_digits(dh, x, y, corr, bits)
+        r = O.corr(x, y) if corr else O.conv(x, y)
+        assert normwise_err(z, r) <= TOL[k] * 1e-3
+        for j in range(d + 1):
+            assert normalised(z[:, j])
