@@ -435,19 +435,32 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       };
       if constexpr (INTV) {
         // Coefficients j and d-j share d+2 terms (the middle coefficient d/2,
-        // when d+1 is odd, forms a group of its own).  The Q = T / groups lanes
-        // of a group (consecutive lanes) split its terms, walked as: the short
-        // coefficient from its first term, then the long one from its last term
-        // backwards.  At every step all lanes with the same rank q inside their
-        // group read the same X row (a broadcast) and consecutive Y rows, and
-        // every lane runs about (d+2)/Q terms.  Only the lane holding a group's
-        // short-to-long switch flushes there; the periodic flushes fall on the
-        // same steps in every lane, so a warp runs them together.
+        // when d+1 is odd, forms a group of its own, the last one).  Every lane
+        // of the CTA belongs to a group: each group gets Q = T / groups
+        // consecutive lanes, and the first T mod groups groups one more, so no
+        // lane idles.  The lanes of a group split its terms, walked as: the
+        // short coefficient from its first term, then the long one from its last
+        // term backwards.  At every step all lanes with the same rank q inside
+        // groups of the same size read the same X row (a broadcast) and
+        // consecutive Y rows.  Only the lane holding a group's short-to-long
+        // switch flushes there; the periodic flushes fall on the same steps in
+        // every lane, so a warp runs them together.
         const int P = (d + 1) / 2;                 // pairs (j, d - j), j < d - j
         const bool has_mid = ((d + 1) & 1) != 0;   // the middle coefficient d/2 pairs with itself
         const int groups = P + (has_mid ? 1 : 0);
-        const int Q = T / groups;                  // lanes per group (>= 1: the plan sizes T)
-        const int grp = tid / Q, q = tid - grp * Q;
+        const int Qb = T / groups;                 // lanes per group (>= 1: the plan sizes T)
+        const int extra = T - Qb * groups;         // groups 0 .. extra-1 have Qb + 1 lanes
+        int grp, q, Q;
+        if (tid < extra * (Qb + 1)) {
+          Q = Qb + 1;
+          grp = tid / Q;
+          q = tid - grp * Q;
+        } else {
+          Q = Qb;
+          const int t2 = tid - extra * (Qb + 1);
+          grp = extra + t2 / Q;
+          q = t2 - (grp - extra) * Q;
+        }
         int cs = 0, cl = 0, ns = 0, nl = 0, tp = 0;
         if (grp < P) {
           cs = conv ? grp : d - grp;               // short coefficient: grp + 1 terms
