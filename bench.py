@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
     ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
                     help="staging depth of the convolution kernel (0: automatic / autotuned)")
+    ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="parts per convolution job (0: automatic / autotuned)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["p2", "p1", "p3", "sweep", "batch"], default="p2",
@@ -311,7 +313,7 @@ def ours_arm(args, world, rank, local):
                              prob.coeff[:, : args.monomials + 1].copy(), prob.inputs)
     plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, arith=args.arith, threads=args.threads,
                     with_vjp=False, profile=True, autotune=not args.no_autotune and args.threads == 0,
-                    staging=args.staging)
+                    staging=args.staging, split=args.split)
     info = plan.info()
     C = torch.from_numpy(prob.coeff).to(dev)
     Z = torch.from_numpy(prob.inputs).to(dev)
@@ -446,7 +448,7 @@ def ours_arm(args, world, rank, local):
         "wall_s_timed_region": wall,
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],
-                 "staging_depth": plan.info()["staging"],
+                 "staging_depth": plan.info()["staging"], "split": plan.info()["split"],
                  "smem_bytes": plan.info()["smem_bytes"], "digits": info["digits"]},
     }
     if not args.no_autograd:

@@ -81,7 +81,10 @@ typedef struct {
                           job's operands are complete, stages them while rounding the current one
                           (a separate staging buffer: more shared memory); 0 = automatic (1, and both
                           are tried when autotuning) */
-  int32_t pad;
+  int32_t split;       /* parts per convolution job (integer pipe): 1, 2 or 4; each part computes the
+                          output coefficients of a contiguous range of coefficient pairs (j, d-j), so a
+                          job's dependants wait for all its parts; more parts shorten the chains of long
+                          monomials; 0 = automatic (1, and 1 and 2 are tried when autotuning) */
 } pes_options;
 
 /* Fill *opt with the defaults. */
@@ -166,6 +169,8 @@ typedef struct {
   int32_t smem_bytes;      /* dynamic shared memory per CTA */
   int32_t arith;           /* PES_ARITH_FP64 or PES_ARITH_INT: the pipe the plan uses */
   int32_t staging;         /* staging depth in use (1 or 2) */
+  int32_t split;           /* parts per convolution job in use */
+  int32_t pad;
 } pes_plan_info;
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);

@@ -119,24 +119,40 @@ __device__ __forceinline__ void set_error(Ctrl* ctrl, int code, long long d0, lo
   atomicExch(&ctrl->abort, 1);
 }
 
+// Parts of every job of the launch (a split of 0 reads as 1).
+__device__ __forceinline__ int parts(const DagArgs& a) { return a.split > 1 ? a.split : 1; }
+
+// Every part of job `dep` of this call has completed (dep < 0: an input series).
 __device__ __forceinline__ bool is_done(const DagArgs& a, int dep, int epoch) {
-  return dep < 0 || ld_acquire(a.flags + dep) == epoch;
+  if (dep < 0) return true;
+  const int s = parts(a);
+  for (int p = 0; p < s; ++p)
+    if (ld_acquire(a.flags + dep * s + p) != epoch) return false;
+  return true;
 }
 
-// Bounded wait until job `dep` of this call has completed.
-__device__ bool wait_done(const DagArgs& a, int dep, int epoch, int job) {
-  if (dep < 0) return true;
-  if (ld_acquire(a.flags + dep) == epoch) return true;
+// Bounded wait until sub-job `f` (a flag index) of this call has completed.
+__device__ bool wait_flag(const DagArgs& a, int f, int epoch, int job) {
+  if (ld_acquire(a.flags + f) == epoch) return true;
   unsigned long long t0 = global_timer();
   for (;;) {
-    if (ld_acquire(a.flags + dep) == epoch) return true;
+    if (ld_acquire(a.flags + f) == epoch) return true;
     if (*reinterpret_cast<volatile int32_t*>(&a.ctrl->abort)) return false;
     if (static_cast<long long>(global_timer() - t0) > a.timeout_ns) {
-      set_error(a.ctrl, kStatusTimeout, dep, job);
+      set_error(a.ctrl, kStatusTimeout, f, job);
       return false;
     }
     __nanosleep(200);
   }
+}
+
+// Bounded wait until every part of job `dep` of this call has completed.
+__device__ bool wait_done(const DagArgs& a, int dep, int epoch, int job) {
+  if (dep < 0) return true;
+  const int s = parts(a);
+  for (int p = 0; p < s; ++p)
+    if (!wait_flag(a, dep * s + p, epoch, job)) return false;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -253,18 +269,25 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
   const bool ahead = a.depth >= 2;
   const int stager = (ahead && T > a.dmax + 1) ? T - 1 : 0;
 
-  // misc[0]: claimed job, misc[1]: failure, misc[2]: its operands are being staged
+  // A job may be split into `split` parts, each computing the output
+  // coefficients of a contiguous range of coefficient pairs; part p of job j is
+  // sub-job j * split + p, with a completion flag of its own.
+  const int split = parts(a);
+  const int nsub = a.njobs * split;
+
+  // misc[0]: claimed sub-job, misc[1]: failure, misc[2]: its operands are being staged
   auto claim = [&]() {
     misc[0] = atomicAdd(&a.ctrl->next[a.counter], 1);
     misc[1] = 0;
     misc[2] = 0;
   };
-  // Start the TMA bulk copies of the claimed job's two operand series (2k limb
-  // planes) into `raw` once both are complete; `blocking`: wait (bounded) for
-  // them, else only look.
+  // Start the TMA bulk copies of the claimed sub-job's two operand series
+  // (digit rows and grids) once both are complete; `blocking`: wait (bounded)
+  // for them, else only look.
   auto stage = [&](bool blocking) {
-    const int job = misc[0];
-    if (job >= a.njobs) return;
+    const int sj = misc[0];
+    if (sj >= nsub) return;
+    const int job = sj / split;
     const ConvJob jb = a.jobs[job];
     const InstInfo in = a.inst[jb.inst];
     if (INTV && (in.d + 2) / 2 > T) {  // at least one lane per coefficient pair: the plan sizes the CTA
@@ -308,11 +331,22 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       if (!misc[2]) stage(true);
     }
     __syncthreads();
-    const int job = misc[0];
-    if (job >= a.njobs || misc[1]) break;
+    const int sj = misc[0];
+    if (sj >= nsub || misc[1]) break;
+    const int job = sj / split;
+    const int part = sj - job * split;
     const ConvJob jb = a.jobs[job];
     const InstInfo in = a.inst[jb.inst];
     const int d = in.d;
+    // Coefficients j and d-j form group min(j, d-j) (the middle coefficient d/2
+    // of an even degree is the last group); this part owns groups [g_lo, g_hi).
+    const int npairs = (d + 1) / 2;
+    const int ngroups = npairs + (((d + 1) & 1) != 0 ? 1 : 0);
+    const int g_lo = part * ngroups / split, g_hi = (part + 1) * ngroups / split;
+    auto owned = [&](int j) {
+      const int g = min(j, d - j);
+      return g >= g_lo && g < g_hi;
+    };
     const int S = in.S;
     int32_t* zrows = a.ws + in.ws_base + static_cast<long long>(jb.out) * in.ws_sstride;
     int32_t* zgrid = zrows + static_cast<long long>(S) * RW;
@@ -355,6 +389,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
     const int rows = (d + 1) * (L + 1);
     for (int t = tid; t < rows; t += T) exch[t] = 0ull;
     for (int j = tid; j <= d; j += T) {
+      if (!owned(j)) continue;
       int32_t m = 2 * GRID_ZERO;
       if (jb.kind == JOB_CONV) {
         for (int i = 0; i <= j; ++i) m = max(m, gx[i] + gy[j - i]);
@@ -445,24 +480,28 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
         // consecutive Y rows.  Only the lane holding a group's short-to-long
         // switch flushes there; the periodic flushes fall on the same steps in
         // every lane, so a warp runs them together.
-        const int P = (d + 1) / 2;                 // pairs (j, d - j), j < d - j
-        const bool has_mid = ((d + 1) & 1) != 0;   // the middle coefficient d/2 pairs with itself
-        const int groups = P + (has_mid ? 1 : 0);
-        const int Qb = T / groups;                 // lanes per group (>= 1: the plan sizes T)
-        const int extra = T - Qb * groups;         // groups 0 .. extra-1 have Qb + 1 lanes
-        int grp, q, Q;
-        if (tid < extra * (Qb + 1)) {
-          Q = Qb + 1;
-          grp = tid / Q;
-          q = tid - grp * Q;
-        } else {
-          Q = Qb;
-          const int t2 = tid - extra * (Qb + 1);
-          grp = extra + t2 / Q;
-          q = t2 - (grp - extra) * Q;
+        const int P = npairs;                      // pairs (j, d - j), j < d - j
+        const bool has_mid = ngroups > P;          // the middle coefficient d/2 pairs with itself
+        const int Gp = g_hi - g_lo;                // groups of this part
+        int grp = g_hi, q = 0, Q = 1;              // lanes without a group run no terms
+        if (Gp > 0) {
+          const int Qb = T / Gp;                   // lanes per group (>= 1: the plan sizes T)
+          const int extra = T - Qb * Gp;           // the first `extra` groups have Qb + 1 lanes
+          if (tid < extra * (Qb + 1)) {
+            Q = Qb + 1;
+            grp = g_lo + tid / Q;
+            q = tid - (grp - g_lo) * Q;
+          } else {
+            Q = Qb;
+            const int t2 = tid - extra * (Qb + 1);
+            grp = g_lo + extra + t2 / Q;
+            q = t2 - (grp - g_lo - extra) * Q;
+          }
         }
         int cs = 0, cl = 0, ns = 0, nl = 0, tp = 0;
-        if (grp < P) {
+        if (grp >= g_hi) {
+          // no group: no terms
+        } else if (grp < P) {
           cs = conv ? grp : d - grp;               // short coefficient: grp + 1 terms
           cl = conv ? d - grp : grp;               // long coefficient: d - grp + 1 terms
           ns = grp + 1;
@@ -549,6 +588,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
 
     // ---- one output coefficient per thread: the exact sum as L digits on its grid ----
     for (int j = tid; j <= d; j += T) {
+      if (!owned(j)) continue;
       const int32_t g = gs[j];
       int32_t o[L];
       int32_t gz = GRID_ZERO;
@@ -572,7 +612,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
     if (tid == 0) {
       __threadfence();
       fence_proxy_async_global();
-      st_release(a.flags + job, epoch);
+      st_release(a.flags + sj, epoch);
     }
     claimed = ahead;
   }

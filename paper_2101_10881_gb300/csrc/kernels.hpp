@@ -37,7 +37,8 @@ struct DagArgs {
   int32_t smax;             // largest padded stride of the instances
   int32_t dmax;             // largest degree
   int32_t depth;            // staging depth: 1, or 2 (next job staged while this one is rounded)
-  int32_t pad;
+  int32_t split;            // parts per job (integer variant: 1, 2 or 4): part p of job j is
+                            // dispatched, flagged and waited for as j * split + p
   long long timeout_ns;     // bound on every wait
 };
 
@@ -68,6 +69,7 @@ struct CopyArgs {
 // accumulators and a digit row in registers).
 __host__ __device__ constexpr int dag_max_threads(int k) { return k >= 10 ? 256 : k >= 8 ? 384 : k >= 4 ? 512 : 768; }
 __host__ __device__ constexpr int dag_min_ctas(int k) { return k >= 10 ? 2 : 1; }
+constexpr int kMaxSplit = 4;  // largest number of parts a convolution job is split into
 
 // Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax) at
 // staging depth 1 or 2.

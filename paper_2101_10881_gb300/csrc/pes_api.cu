@@ -83,6 +83,7 @@ struct Exec {
   int32_t k = 0, arith = 0, threads = 128, ctas_per_sm = 0;
   int32_t smax = 0, dmax = 0;
   int32_t depth = 1, staging = 0;  // staging depth in use; requested (0 = automatic)
+  int32_t split = 1, split_req = 0;  // parts per convolution job in use; requested (0 = automatic)
   size_t smem = 0;
   int32_t blocks_per_sm = 0, nsm = 0, optin = 0;
   long long timeout_ns = 0;
@@ -118,13 +119,15 @@ struct Exec {
     pes_status s = put(&L.jobs, jobs);
     if (s != PES_OK) return s;
     if (L.n > 0) {
-      cudaError_t e = cudaMalloc(&L.flags, sizeof(int32_t) * static_cast<size_t>(L.n));
+      // one flag per part of every job, for the largest split
+      const size_t nf = static_cast<size_t>(L.n) * pes::kMaxSplit;
+      cudaError_t e = cudaMalloc(&L.flags, sizeof(int32_t) * nf);
       if (e != cudaSuccess) return fail(PES_ENOMEM, "job flags");
       owned.push_back(L.flags);
-      PES_CUDA(cudaMemset(L.flags, 0, sizeof(int32_t) * static_cast<size_t>(L.n)));
+      PES_CUDA(cudaMemset(L.flags, 0, sizeof(int32_t) * nf));
     }
     long long cap = static_cast<long long>(blocks_per_sm) * nsm;
-    L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(cap, L.n)));
+    L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(cap, static_cast<long long>(L.n) * split)));
     return PES_OK;
   }
 
@@ -175,6 +178,8 @@ struct Exec {
                                              " at k=" + std::to_string(k));
     // staging depth: 2 only when asked for and it fits (the autotuner tries both)
     staging = o.staging;
+    split_req = o.split;
+    split = (arith == pes::ARITH_INT && o.split > 0) ? o.split : 1;
     depth = (staging == 2 && pes::dag_smem_bytes(k, arith, smax, dmax, 2) <= static_cast<size_t>(optin)) ? 2 : 1;
     smem = pes::dag_smem_bytes(k, arith, smax, dmax, depth);
     if (smem > static_cast<size_t>(optin))
@@ -205,9 +210,9 @@ struct Exec {
     return b <= static_cast<size_t>(optin) ? b : 0;
   }
 
-  // threads per CTA, a cap on CTAs per SM (0: as many as fit) and the staging
-  // depth for later launches
-  pes_status configure(int32_t t, int32_t ctas_cap, int32_t dp, JobList& L) {
+  // threads per CTA, a cap on CTAs per SM (0: as many as fit), the staging
+  // depth and the parts per job (integer variant only) for later launches
+  pes_status configure(int32_t t, int32_t ctas_cap, int32_t dp, int32_t sp, JobList& L) {
     const size_t b = smem_at(dp);
     if (b == 0) return fail(PES_EUNSUPPORTED_SIZE, "staging depth does not fit in shared memory");
     PES_CUDA(pes::dag_prepare(k, arith, b));
@@ -216,10 +221,11 @@ struct Exec {
     if (bps < 1) return fail(PES_EUNSUPPORTED_SIZE, "configuration does not fit on an SM");
     smem = b;
     depth = dp;
+    split = arith == pes::ARITH_INT ? std::max(1, sp) : 1;
     threads = t;
     blocks_per_sm = ctas_cap > 0 ? std::min(bps, ctas_cap) : bps;
     L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(
-                 static_cast<long long>(blocks_per_sm) * nsm, L.n)));
+                 static_cast<long long>(blocks_per_sm) * nsm, static_cast<long long>(L.n) * split)));
     return PES_OK;
   }
 
@@ -235,6 +241,7 @@ struct Exec {
     a.smax = smax;
     a.dmax = dmax;
     a.depth = depth;
+    a.split = split;
     a.timeout_ns = timeout_ns;
     return a;
   }
@@ -323,6 +330,8 @@ pes_status parse_options(const pes_options* opt, pes_options& o) {
     return fail(PES_EINVAL, "threads must be 0 (automatic) or a multiple of 32 up to 1024");
   if (o.ctas_per_sm < 0) return fail(PES_EINVAL, "ctas_per_sm must be >= 0");
   if (o.staging < 0 || o.staging > 2) return fail(PES_EINVAL, "staging must be 0, 1 or 2");
+  if (!(o.split == 0 || o.split == 1 || o.split == 2 || o.split == 4))
+    return fail(PES_EINVAL, "split must be 0, 1, 2 or 4");
   return PES_OK;
 }
 
@@ -363,24 +372,25 @@ std::string autotune_cache_file() {
   return std::string(home ? home : "/tmp") + "/.cache/pes_autotune.txt";
 }
 
-bool tune_lookup(const std::string& key, int32_t* threads, int32_t* ctas, int32_t* depth) {
+bool tune_lookup(const std::string& key, int32_t* threads, int32_t* ctas, int32_t* depth, int32_t* split) {
   FILE* f = std::fopen(autotune_cache_file().c_str(), "r");
   if (!f) return false;
   char line[512], kb[256];
-  int t = 0, c = 0, dp = 0;
+  int t = 0, c = 0, dp = 0, sp = 0;
   bool found = false;
   while (std::fgets(line, sizeof(line), f))
-    if (std::sscanf(line, "%255s %d %d %d", kb, &t, &c, &dp) == 4 && key == kb) {
+    if (std::sscanf(line, "%255s %d %d %d %d", kb, &t, &c, &dp, &sp) == 5 && key == kb) {
       *threads = t;
       *ctas = c;
       *depth = dp;
+      *split = sp;
       found = true;
     }
   std::fclose(f);
   return found;
 }
 
-void tune_store(const std::string& key, int32_t threads, int32_t ctas, int32_t depth) {
+void tune_store(const std::string& key, int32_t threads, int32_t ctas, int32_t depth, int32_t split) {
   const std::string path = autotune_cache_file();
   const size_t slash = path.find_last_of('/');
   if (slash != std::string::npos)
@@ -388,7 +398,7 @@ void tune_store(const std::string& key, int32_t threads, int32_t ctas, int32_t d
       if (i == slash || path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
   FILE* f = std::fopen(path.c_str(), "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d\n", key.c_str(), threads, ctas, depth);
+  std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), threads, ctas, depth, split);
   std::fclose(f);
 }
 
@@ -397,8 +407,8 @@ void tune_store(const std::string& key, int32_t threads, int32_t ctas, int32_t d
 // shape, so the trials may run on the caller's data.  Cached by `key`.
 template <class Run>
 pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cudaStream_t st) {
-  int32_t bt = E.threads, bc = 0, bd = E.depth;
-  if (!tune_lookup(key, &bt, &bc, &bd)) {
+  int32_t bt = E.threads, bc = 0, bd = E.depth, bs = E.split;
+  if (!tune_lookup(key, &bt, &bc, &bd, &bs)) {
     const int32_t base = E.threads;
     std::vector<int32_t> ts{base};
     if (E.arith == pes::ARITH_INT) {
@@ -409,48 +419,54 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
     }
     std::vector<int32_t> depths{E.depth};
     if (E.staging == 0) depths = {1, 2};
+    std::vector<int32_t> splits{E.split};
+    if (E.split_req == 0 && E.arith == pes::ARITH_INT) splits = {1, 2};
     cudaEvent_t e0, e1;
     PES_CUDA(cudaEventCreate(&e0));
     PES_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int32_t dp : depths) {
-      const size_t b = E.smem_at(dp);
-      if (b == 0) continue;
-      PES_CUDA(pes::dag_prepare(E.k, E.arith, b));
-      for (int32_t t : ts) {
-        int occ = 0;
-        PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, b, &occ));
-        for (int32_t c = std::max(1, occ); c >= std::max(1, occ - 1); --c) {
-          pes_status s = E.configure(t, c, dp, L);
-          if (s != PES_OK) continue;
-          s = run(st);  // warm-up
-          if (s != PES_OK) return s;
-          PES_CUDA(cudaEventRecord(e0, st));
-          s = run(st);
-          if (s != PES_OK) return s;
-          PES_CUDA(cudaEventRecord(e1, st));
-          PES_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < best) {
-            best = ms;
-            bt = t;
-            bc = c;
-            bd = dp;
+    for (int32_t sp : splits) {
+      for (int32_t dp : depths) {
+        const size_t b = E.smem_at(dp);
+        if (b == 0) continue;
+        PES_CUDA(pes::dag_prepare(E.k, E.arith, b));
+        for (int32_t t : ts) {
+          int occ = 0;
+          PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, b, &occ));
+          for (int32_t c = std::max(1, occ); c >= std::max(1, occ - 1); --c) {
+            pes_status s = E.configure(t, c, dp, sp, L);
+            if (s != PES_OK) continue;
+            s = run(st);  // warm-up
+            if (s != PES_OK) return s;
+            PES_CUDA(cudaEventRecord(e0, st));
+            s = run(st);
+            if (s != PES_OK) return s;
+            PES_CUDA(cudaEventRecord(e1, st));
+            PES_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+              best = ms;
+              bt = t;
+              bc = c;
+              bd = dp;
+              bs = sp;
+            }
           }
         }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    tune_store(key, bt, bc, bd);
+    tune_store(key, bt, bc, bd, bs);
   }
-  return E.configure(bt, bc, bd, L);
+  return E.configure(bt, bc, bd, bs, L);
 }
 
 std::string tune_key(const Exec& E, int64_t njobs, uint64_t signature) {
   char key[200];
-  std::snprintf(key, sizeof(key), "v2_k%d_a%d_t%d_s%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.staging, E.dmax,
+  std::snprintf(key, sizeof(key), "v3_k%d_a%d_t%d_s%d_p%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.staging,
+                E.split_req, E.dmax,
                 static_cast<long long>(njobs), static_cast<unsigned long long>(signature));
   return key;
 }
@@ -483,7 +499,7 @@ extern "C" void pes_default_options(pes_options* opt) {
   opt->profile = 0;
   opt->autotune = 0;
   opt->staging = 0;
-  opt->pad = 0;
+  opt->split = 0;
 }
 
 extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -599,9 +615,9 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
     if (ts != PES_OK) return ts;
     // the VJP job lists share the launch shape
     plan->vjp_fwd.grid = plan->vjp_m.grid = plan->vjp_corr.grid = 0;
-    E.configure(E.threads, E.blocks_per_sm, E.depth, plan->vjp_fwd);
-    E.configure(E.threads, E.blocks_per_sm, E.depth, plan->vjp_m);
-    E.configure(E.threads, E.blocks_per_sm, E.depth, plan->vjp_corr);
+    E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, plan->vjp_fwd);
+    E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, plan->vjp_m);
+    E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, plan->vjp_corr);
   }
   PES_CUDA(E.mark(0, st));
   PES_CUDA(pes::launch_prologue(E.ctrl, st));
@@ -687,6 +703,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->smem_bytes = static_cast<int32_t>(plan->ex.smem);
   info->arith = plan->ex.arith;
   info->staging = plan->ex.depth;
+  info->split = plan->ex.split;
   return PES_OK;
 }
 
@@ -1013,6 +1030,7 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->smem_bytes = static_cast<int32_t>(E0.smem);
   info->arith = E0.arith;
   info->staging = E0.depth;
+  info->split = E0.split;
   return PES_OK;
 }
 

@@ -148,6 +148,33 @@ def test_staging_depths_agree(torch, threads):
     assert normwise_err(g2, rg) <= TOL[k]
 
 
+@pytest.mark.parametrize("split", [2, 4])
+def test_split_jobs_agree(torch, split):
+    """Jobs split into parts over ranges of coefficient pairs (each part with a
+    flag of its own, dependants waiting for all parts) give the same bits as
+    whole jobs, forward and VJP, for an odd and an even number of coefficients
+    and for a degree with fewer pairs than parts."""
+    k = 4
+    rng = np.random.default_rng(88 + split)
+    supp = [list(range(9)), [0, 3, 5], [2, 7], [1, 4, 6, 8]]
+    n = 9
+    for d in (152, 41, 2):
+        prob = synth.Problem("split", n, d, k, supp, random_md(rng, k, (len(supp) + 1, d + 1)),
+                             random_md(rng, k, (n, d + 1)))
+        v1, g1, p1 = run(torch, prob, split=1)
+        v2, g2, p2 = run(torch, prob, split=split)
+        assert p2.info()["split"] == split
+        assert np.array_equal(v1, v2) and np.array_equal(g1, g2)
+        u = dev(torch, random_md(rng, k, (d + 1,)))
+        C, Z = dev(torch, prob.coeff), dev(torch, prob.inputs)
+        r1 = p1.vjp(C, Z, u)
+        r2 = p2.vjp(C, Z, u)
+        p2.check()
+        assert all(torch.equal(a, b) for a, b in zip(r1, r2))
+    rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
+    assert normwise_err(v2, rv) <= TOL[k] and normwise_err(g2, rg) <= TOL[k]
+
+
 def max_digit_value(k):
     """A k-double whose 28-bit digits, on the grid of its leading limb, are all
     2^27 - 1 (up to the rounding of the last limb): the largest same-signed digit
