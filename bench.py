@@ -61,7 +61,7 @@ def parse_args():
                     help="parts per convolution job (0: automatic / autotuned)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["p2", "p1", "p3", "sweep", "batch"], default="p2",
+    ap.add_argument("--workload", choices=["p2", "p1", "p3", "sweep", "batch", "batch-small"], default="p2",
                     help="p2: the headline workload; p1 / p3: the paper's other test polynomials (analysis); "
                          "sweep: the 64x64 system over k x d (one JSON line per cell); "
                          "batch: the full batched recipe (2048 instances) batched vs plain")
@@ -456,6 +456,7 @@ def ours_arm(args, world, rank, local):
     count = 256 if args.batch_count is None else args.batch_count
     if count > 0:
         out["batched"] = batch_measure(args, dev, count)
+        out["batched_small"] = batch_measure(args, dev, 2048, small=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub = cpu_sample(prob, args.cpu_sample_vars)
         t, cores = run_oracle(sub)
@@ -504,9 +505,10 @@ def autograd_measure(args, dev, flush):
             "vjp_jobs": {"monomial_products": info["vjp_conv_jobs"], "correlations": info["vjp_corr_jobs"]}}
 
 
-def batch_measure(args, dev, count):
+def batch_measure(args, dev, count, small=False):
     """Config 3 recipe (random sparse polynomials: n 8-128, m 16-2048 monomials of
-    2-8 variables, d in {15,31,63,127,152}), first `count` instances, k=2: one
+    2-8 variables, d in {15,31,63,127,152}), first `count` instances, k=2 (or,
+    with `small`, the small instances of synth.small_batch_shapes): one
     graph-captured batched call vs the same instances one plain pes_eval_grad
     call after another on one stream (plans built beforehand), ms per instance;
     the batched results must equal the plain ones."""
@@ -514,7 +516,7 @@ def batch_measure(args, dev, count):
     import torch
     from paper_2101_10881_gb300 import pes, synth
     k = args.batch_k
-    shapes = synth.config3_shapes(seed=args.seed, count=count)
+    shapes = (synth.small_batch_shapes if small else synth.config3_shapes)(seed=args.seed, count=count)
     rng = np.random.default_rng(args.seed + 7)
     probs = []
     for b, (n, supp, d) in enumerate(shapes):
@@ -562,7 +564,9 @@ def batch_measure(args, dev, count):
     B.check()
     same = bool(torch.equal(V, Vp) and torch.equal(G, Gp))
     info = B.info()
-    return {"workload": f"first {count} instances of the batched recipe (seed {args.seed}), k={k}",
+    what = ("small instances (n 4-16, 4-32 monomials of 2-4 variables, d in {7,15,31})" if small
+            else "instances of the batched recipe")
+    return {"workload": f"first {count} {what} (seed {args.seed}), k={k}",
             "instances": count, "conv_jobs": info["conv_jobs"], "groups": info["grid"],
             "batched_ms_per_instance": res["batched"] / count, "plain_ms_per_instance": res["plain"] / count,
             "plain_over_batched": res["plain"] / res["batched"],
@@ -677,13 +681,15 @@ def main():
         return reference_arm(args, world, rank)
     if args.workload == "sweep":
         return sweep_arm(args, world, rank)
-    if args.workload == "batch":
+    if args.workload in ("batch", "batch-small"):
         import torch
         from paper_2101_10881_gb300 import pes
         pes.build()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "batched": batch_measure(args, torch.device("cuda", local),
-                                                                          args.batch_count or 2048)}), flush=True)
+                                                                          args.batch_count or 2048,
+                                                                          small=args.workload == "batch-small")}),
+                  flush=True)
         return 0
     rc = ours_arm(args, world, rank, local)
     if world > 1:

@@ -121,6 +121,22 @@ def config3_shapes(seed: int = 0, count: int = 2048):
     return out
 
 
+def small_batch_shapes(seed: int = 0, count: int = 2048):
+    """Shapes of a batch of small instances (list of (n, supports, d)): n uniform
+    in 4-16, 4-32 monomials of 2-4 distinct variables, d drawn from {7, 15, 31}.
+    The batched recipe's own instances are large (thousands of convolutions
+    each); these are the instances where one launch per instance is dominated by
+    launch and dependency latency."""
+    rng = np.random.default_rng(seed + 4242)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(4, 17))
+        N = int(rng.integers(4, 33))
+        d = int(rng.choice([7, 15, 31]))
+        out.append((n, random_supports(rng, n, N, 2, min(4, n)), d))
+    return out
+
+
 def config3(seed: int = 0, count: int = 2048, k: int = 2):
     probs = []
     for b, (n, supp, d) in enumerate(config3_shapes(seed, count)):
