@@ -42,7 +42,7 @@ UNIT = "TFLOP/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -76,7 +76,7 @@ def parse_args():
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
                     help="variables of the monomial the oracle evaluates as the CPU sample")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------
@@ -155,16 +155,24 @@ class ClockSampler:
 # distributed plumbing
 # ---------------------------------------------------------------------------
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """World, rank and local rank from the torchrun environment; for N > 1 one
+    process group (NCCL, one GPU per rank; gloo when asked for or without CUDA,
+    for the host-side logic)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if backend is None:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    elif torch.cuda.is_available():
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
+    elif backend == "nccl":
         torch.cuda.set_device(0)
     return world, rank, local
 
@@ -180,9 +188,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_tflops(world, ops_per_step, steps, max_ms):
+    """Whole-job throughput under weak scaling: every rank ran `steps` steps of
+    its own workload of `ops_per_step` operations; the slowest rank's time."""
+    return world * ops_per_step * steps / (max_ms * 1e-3) / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -389,8 +404,8 @@ def ours_arm(args, world, rank, local):
     barrier(world)
     e2e_total = max_over_ranks(sum(e2e_ms), world)
 
-    value = world * ops_step * args.steps / (total_ms * 1e-3) / 1e12
-    e2e_value = world * ops_step * args.steps / (e2e_total * 1e-3) / 1e12
+    value = whole_job_tflops(world, ops_step, args.steps, total_ms)
+    e2e_value = whole_job_tflops(world, ops_step, args.steps, e2e_total)
     mean_conv = statistics.mean(conv_ms)
     work = (f"{info['conv_jobs']} convolutions x {(prob.d + 1) * (prob.d + 2) // 2} terms x "
             f"{info['digits'] * (info['digits'] + 1) // 2} digit products")
