@@ -95,6 +95,14 @@ def dp_equiv_ops(conv_jobs, add_jobs, d, k):
     return conv_jobs * per_conv + add_jobs * (d + 1) * ca
 
 
+def paper_convention_ops(conv_jobs, add_jobs, d, k):
+    """Double-operation equivalent in the paper's own count (Sec. 6.2): every
+    convolution as (d+1)^2 k-double multiplications and d(d+1) additions (the
+    zero-padded loop), every series addition as d+1 additions."""
+    cm, ca = md_costs(k)
+    return conv_jobs * ((d + 1) ** 2 * cm + d * (d + 1) * ca) + add_jobs * (d + 1) * ca
+
+
 def digit_fma_flops(conv_jobs, d, digits):
     """Flops (2 per multiply-add) of the exact digit products the convolution
     kernel executes: L(L+1)/2 per term, (d+1)(d+2)/2 terms per convolution."""
@@ -460,6 +468,11 @@ def ours_arm(args, world, rank, local):
         "variants": variants,
         "peaks": {"fp64_tflops": fp64_peak, "int_mad_wide_tops": int_peak},
         "ops_per_step": ops_step,
+        "paper_convention": {
+            "value": whole_job_tflops(world, paper_convention_ops(info["conv_jobs"], info["add_jobs"], prob.d,
+                                                                  prob.k), args.steps, total_ms),
+            "unit": UNIT,
+            "rule": "the paper's count: (d+1)^2 k-double multiplications and d(d+1) additions per convolution"},
         "wall_s_timed_region": wall,
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],

@@ -136,3 +136,11 @@ def test_flop_metric_reproduces_paper():
     assert mul_ops == PC["p1_paper_mul_ops_d152"]
     assert add_ops == PC["p1_paper_add_ops_d152"]
     assert mul_ops + add_ops == PC["p1_paper_total_ops_d152"]
+
+
+def test_bench_paper_convention_count():
+    """bench.py's paper-convention count is the same rule: it reproduces the
+    paper's total for p1 at d = 152."""
+    import bench
+    assert bench.paper_convention_ops(PC["p1_convolutions"], PC["p1_additions"], 152, 10) == \
+        PC["p1_paper_total_ops_d152"]
