@@ -58,6 +58,8 @@ def _load():
                 "orc_corr": [c_int, c_int, dp, dp, dp],
                 "orc_eval_grad": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, c_int],
                 "orc_vjp": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, dp, c_int],
+                "orc_eval_grad_pow": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, c_int],
+                "orc_vjp_pow": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, dp, c_int],
                 "orc_threads": [c_int],
                 "orc_conv_many": [c_int, c_int, c_int, dp, dp, dp, c_int],
             }.items():
@@ -145,10 +147,24 @@ def _supports(supports):
     return ptr, np.asarray(idx, dtype=np.int32)
 
 
-def eval_grad(supports, n, coeff, inputs, nthreads: int = 0, grad: bool = True):
+def _exponents(exponents, supports):
+    """Flat int32 exponents aligned with the supports (None: all 1)."""
+    if exponents is None:
+        return None
+    assert len(exponents) == len(supports)
+    flat = []
+    for s, e in zip(supports, exponents):
+        assert len(e) == len(s)
+        flat.extend(int(v) for v in e)
+    return np.ascontiguousarray(np.array(flat, dtype=np.int32))
+
+
+def eval_grad(supports, n, coeff, inputs, nthreads: int = 0, grad: bool = True, exponents=None):
     """Value (k, d+1) and gradient (k, n, d+1) of the polynomial at the series.
 
     supports: list of increasing 0-based variable index lists, one per monomial.
+    exponents: None (every exponent 1) or one list of positive exponents per
+    monomial, aligned with its support.
     coeff: (k, N+1, d+1) with index 0 the constant term; inputs: (k, n, d+1).
     """
     coeff, inputs = _f64(coeff), _f64(inputs)
@@ -156,24 +172,34 @@ def eval_grad(supports, n, coeff, inputs, nthreads: int = 0, grad: bool = True):
     N = len(supports)
     assert n1 == N + 1 and inputs.shape == (k, n, s)
     ptr, idx = _supports(supports)
+    ex = _exponents(exponents, supports)
     value = np.empty((k, s))
     g = np.empty((k, n, s)) if grad else None
     gp = _dp(g) if grad else ctypes.POINTER(ctypes.c_double)()
-    _check(_load().orc_eval_grad(k, s - 1, N, n, _ip(ptr), _ip(idx), _dp(coeff), _dp(inputs),
-                                 _dp(value), gp, nthreads), "eval_grad")
+    if ex is None:
+        _check(_load().orc_eval_grad(k, s - 1, N, n, _ip(ptr), _ip(idx), _dp(coeff), _dp(inputs),
+                                     _dp(value), gp, nthreads), "eval_grad")
+    else:
+        _check(_load().orc_eval_grad_pow(k, s - 1, N, n, _ip(ptr), _ip(idx), _ip(ex), _dp(coeff),
+                                         _dp(inputs), _dp(value), gp, nthreads), "eval_grad_pow")
     return (value, g) if grad else value
 
 
-def vjp(supports, n, coeff, inputs, upstream, nthreads: int = 0):
+def vjp(supports, n, coeff, inputs, upstream, nthreads: int = 0, exponents=None):
     """(grad_input (k, n, d+1), grad_coeff (k, N+1, d+1)) of <upstream, value>."""
     coeff, inputs, upstream = _f64(coeff), _f64(inputs), _f64(upstream)
     k, n1, s = coeff.shape
     N = len(supports)
     ptr, idx = _supports(supports)
+    ex = _exponents(exponents, supports)
     gi = np.empty((k, n, s))
     gc = np.empty((k, N + 1, s))
-    _check(_load().orc_vjp(k, s - 1, N, n, _ip(ptr), _ip(idx), _dp(coeff), _dp(inputs),
-                           _dp(upstream), _dp(gi), _dp(gc), nthreads), "vjp")
+    if ex is None:
+        _check(_load().orc_vjp(k, s - 1, N, n, _ip(ptr), _ip(idx), _dp(coeff), _dp(inputs),
+                               _dp(upstream), _dp(gi), _dp(gc), nthreads), "vjp")
+    else:
+        _check(_load().orc_vjp_pow(k, s - 1, N, n, _ip(ptr), _ip(idx), _ip(ex), _dp(coeff), _dp(inputs),
+                                   _dp(upstream), _dp(gi), _dp(gc), nthreads), "vjp_pow")
     return gi, gc
 
 

@@ -353,27 +353,48 @@ static int check_supports(int N, int n, const int32_t *ptr, const int32_t *idx)
     return 0;
 }
 
-/* Product of coefficient a_m with the input series of all variables of monomial m
- * except variable `skip` (skip < 0: all of them), left to right.  Result in out
- * (limb stride S).  t0/t1 are scratch series of k*S doubles. */
-static void monomial_product(int k, int d, size_t S, const double *coeff, size_t cstride,
-                             const double *input, size_t istride, const int32_t *vars, int nv,
-                             int m, int skip, double *out, double *t0, double *t1, expn *e)
+/* Exponents: NULL means every variable has exponent 1; else one positive
+ * exponent per support entry, at most ORC_MAX_EXP. */
+#define ORC_MAX_EXP 64
+static int check_exponents(int N, const int32_t *ptr, const int32_t *ex)
 {
-    /* start from a_m */
+    if (!ex)
+        return 0;
+    for (int t = 0; t < (N > 0 ? ptr[N] : 0); ++t)
+        if (ex[t] < 1 || ex[t] > ORC_MAX_EXP)
+            return 1;
+    return 0;
+}
+
+/* Product of a start series with the input series of the variables of
+ * monomial m, every variable repeated as often as its exponent (ex NULL: once),
+ * variable `skip` once fewer (skip < 0: none), left to right.  The start series
+ * is the coefficient a_m when m >= 1, else the constant series 1.  Result in
+ * out (limb stride S).  t0/t1 are scratch series of k*S doubles. */
+static void monomial_product(int k, int d, size_t S, const double *coeff, size_t cstride,
+                             const double *input, size_t istride, const int32_t *vars,
+                             const int32_t *ex, int nv, int m, int skip, double *out, double *t0,
+                             double *t1, expn *e)
+{
     double *cur = t0, *nxt = t1;
-    for (int l = 0; l < k; ++l)
-        memcpy(cur + (size_t)l * S, coeff + (size_t)l * cstride + (size_t)m * S, sizeof(double) * S);
+    if (m >= 1) {
+        for (int l = 0; l < k; ++l)
+            memcpy(cur + (size_t)l * S, coeff + (size_t)l * cstride + (size_t)m * S, sizeof(double) * S);
+    } else {
+        memset(cur, 0, sizeof(double) * (size_t)k * S);
+        cur[0] = 1.0;
+    }
     for (int v = 0; v < nv; ++v) {
-        if (vars[v] == skip)
-            continue;
-        cser a = {cur, S};
-        cser b = {input + (size_t)vars[v] * S, istride};
-        ser c = {nxt, S};
-        conv(k, d, a, b, c, e);
-        double *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+        int reps = (ex ? ex[v] : 1) - (vars[v] == skip ? 1 : 0);
+        for (int r = 0; r < reps; ++r) {
+            cser a = {cur, S};
+            cser b = {input + (size_t)vars[v] * S, istride};
+            ser c = {nxt, S};
+            conv(k, d, a, b, c, e);
+            double *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
     }
     for (int l = 0; l < k; ++l)
         memcpy(out + (size_t)l * S, cur + (size_t)l * S, sizeof(double) * S);
@@ -390,18 +411,21 @@ static int used_threads(int nthreads)
 }
 
 /*
- * value[k][d+1] = a_0 + sum_m a_m prod_{i in S_m} z_i
- * grad[k][n][d+1]: grad_i = sum_{m : i in S_m} a_m prod_{j in S_m, j != i} z_j
+ * value[k][d+1] = a_0 + sum_m a_m prod_{i in S_m} z_i^{e_i}
+ * grad[k][n][d+1]: grad_i = sum_{m : i in S_m} e_i a_m z_i^{e_i - 1} prod_{j in S_m, j != i} z_j^{e_j}
+ * (Eq. eqpolynomial; exponents e from supp_exp, all 1 when supp_exp is NULL;
+ * every power is repeated multiplication, the factor e_i is e_i additions).
  * coeff: [k][N+1][d+1] (index 0 is a_0), input: [k][n][d+1].
  * supp_ptr: N+1 row pointers, supp_idx: 0-based variable ids, increasing per row.
  * grad may be NULL (value only).  nthreads <= 0 uses the OpenMP default.
  * Returns 0 on success, 1 on invalid arguments, 3 on allocation failure.
  */
-int orc_eval_grad(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
-                  const double *coeff, const double *input, double *value, double *grad,
-                  int nthreads)
+int orc_eval_grad_pow(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
+                      const int32_t *supp_exp, const double *coeff, const double *input, double *value,
+                      double *grad, int nthreads)
 {
-    if (!valid_k(k) || d < 0 || check_supports(N, n, supp_ptr, supp_idx))
+    if (!valid_k(k) || d < 0 || check_supports(N, n, supp_ptr, supp_idx) ||
+        check_exponents(N, supp_ptr, supp_exp))
         return 1;
     const size_t S = (size_t)d + 1;
     const size_t cstride = (size_t)(N + 1) * S; /* limb stride of coeff */
@@ -436,8 +460,9 @@ int orc_eval_grad(int k, int d, int N, int n, const int32_t *supp_ptr, const int
             if (!ok)
                 continue;
             const int32_t *vars = supp_idx + supp_ptr[m];
+            const int32_t *ex = supp_exp ? supp_exp + supp_ptr[m] : NULL;
             int nv = supp_ptr[m + 1] - supp_ptr[m];
-            monomial_product(k, d, S, coeff, cstride, input, istride, vars, nv, m + 1, -1, prod,
+            monomial_product(k, d, S, coeff, cstride, input, istride, vars, ex, nv, m + 1, -1, prod,
                              prod + (size_t)k * S, prod + 2 * (size_t)k * S, &e);
             for (size_t j = 0; j < S; ++j)
                 add_value(&part[j], k, prod + j, S);
@@ -492,16 +517,19 @@ int orc_eval_grad(int k, int d, int N, int n, const int32_t *supp_ptr, const int
                 g[j].m = 0;
             for (int m = 0; m < N; ++m) {
                 const int32_t *vars = supp_idx + supp_ptr[m];
+                const int32_t *ex = supp_exp ? supp_exp + supp_ptr[m] : NULL;
                 int nv = supp_ptr[m + 1] - supp_ptr[m];
-                int has = 0;
+                int mult = 0; /* exponent of x_i in monomial m (0: absent) */
                 for (int v = 0; v < nv; ++v)
-                    has |= (vars[v] == i);
-                if (!has)
+                    if (vars[v] == i)
+                        mult = ex ? ex[v] : 1;
+                if (!mult)
                     continue;
-                monomial_product(k, d, S, coeff, cstride, input, istride, vars, nv, m + 1, i,
+                monomial_product(k, d, S, coeff, cstride, input, istride, vars, ex, nv, m + 1, i,
                                  prod, prod + (size_t)k * S, prod + 2 * (size_t)k * S, &e);
-                for (size_t j = 0; j < S; ++j)
-                    add_value(&g[j], k, prod + j, S);
+                for (int r = 0; r < mult; ++r) /* the factor e_i, added exactly */
+                    for (size_t j = 0; j < S; ++j)
+                        add_value(&g[j], k, prod + j, S);
             }
             for (size_t j = 0; j < S; ++j)
                 round_k(&g[j], k, grad + (size_t)i * S + j, istride);
@@ -524,22 +552,32 @@ int orc_eval_grad(int k, int d, int N, int n, const int32_t *supp_ptr, const int
     return fail ? 3 : 0;
 }
 
+int orc_eval_grad(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
+                  const double *coeff, const double *input, double *value, double *grad,
+                  int nthreads)
+{
+    return orc_eval_grad_pow(k, d, N, n, supp_ptr, supp_idx, NULL, coeff, input, value, grad, nthreads);
+}
+
 /*
  * Vector-Jacobian product of the value series with an upstream series u (d+1
  * coefficients of k limbs, [k][d+1]):
- *   L = sum_l u_l v_l,   v = a_0 + sum_m a_m M_m,   M_m = prod_{i in S_m} z_i.
- * Because every variable appears with exponent 1, v is affine in each input
- * coefficient, and
+ *   L = sum_l u_l v_l,   v = a_0 + sum_m a_m M_m,   M_m = prod_{i in S_m} z_i^{e_i}.
+ * v is linear in every coefficient series, and the derivative of L along the
+ * coefficients of an input series z_i is the correlation of u with the
+ * partial derivative g_i (the chain rule for the truncated product), so
  *   dL/da_0[j] = u_j,
  *   dL/da_m[j] = sum_{l=j..d} u_l M_m[l-j],
  *   dL/dz_i[j] = sum_{l=j..d} u_l g_i[l-j],   g_i = dp/dx_i (z).
- * grad_coeff: [k][N+1][d+1]; grad_input: [k][n][d+1].
+ * grad_coeff: [k][N+1][d+1]; grad_input: [k][n][d+1].  supp_exp as in
+ * orc_eval_grad_pow.
  */
-int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
-            const double *coeff, const double *input, const double *upstream,
-            double *grad_input, double *grad_coeff, int nthreads)
+int orc_vjp_pow(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
+                const int32_t *supp_exp, const double *coeff, const double *input, const double *upstream,
+                double *grad_input, double *grad_coeff, int nthreads)
 {
-    if (!valid_k(k) || d < 0 || check_supports(N, n, supp_ptr, supp_idx))
+    if (!valid_k(k) || d < 0 || check_supports(N, n, supp_ptr, supp_idx) ||
+        check_exponents(N, supp_ptr, supp_exp))
         return 1;
     const size_t S = (size_t)d + 1;
     const size_t cstride = (size_t)(N + 1) * S;
@@ -552,7 +590,7 @@ int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *
         free(g);
         return 3;
     }
-    int rc = orc_eval_grad(k, d, N, n, supp_ptr, supp_idx, coeff, input, value, g, nthreads);
+    int rc = orc_eval_grad_pow(k, d, N, n, supp_ptr, supp_idx, supp_exp, coeff, input, value, g, nthreads);
     int fail = rc != 0;
     if (!fail) {
         for (int l = 0; l < k; ++l) /* dL/da_0 = u */
@@ -574,22 +612,12 @@ int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *
                 if (t < N) {
                     int m = t;
                     const int32_t *vars = supp_idx + supp_ptr[m];
+                    const int32_t *ex = supp_exp ? supp_exp + supp_ptr[m] : NULL;
                     int nv = supp_ptr[m + 1] - supp_ptr[m];
-                    /* M_m: the monomial without its coefficient, left to right */
-                    double *cur = prod + (size_t)k * S, *nxt = prod + 2 * (size_t)k * S;
-                    for (int l = 0; l < k; ++l)
-                        memcpy(cur + (size_t)l * S, input + (size_t)l * istride + (size_t)vars[0] * S,
-                               sizeof(double) * S);
-                    for (int v = 1; v < nv; ++v) {
-                        cser a = {cur, S};
-                        cser b = {input + (size_t)vars[v] * S, istride};
-                        ser c = {nxt, S};
-                        conv(k, d, a, b, c, &e);
-                        double *tmp = cur;
-                        cur = nxt;
-                        nxt = tmp;
-                    }
-                    cser cm = {cur, S};
+                    /* M_m: the monomial without its coefficient, left to right from 1 */
+                    monomial_product(k, d, S, coeff, cstride, input, istride, vars, ex, nv, 0, -1, prod,
+                                     prod + (size_t)k * S, prod + 2 * (size_t)k * S, &e);
+                    cser cm = {prod, S};
                     ser r = {grad_coeff + (size_t)(m + 1) * S, cstride};
                     corr(k, d, cu, cm, r, &e);
                 } else {
@@ -614,6 +642,14 @@ int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *
     free(value);
     free(g);
     return fail ? (rc ? rc : 3) : 0;
+}
+
+int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
+            const double *coeff, const double *input, const double *upstream,
+            double *grad_input, double *grad_coeff, int nthreads)
+{
+    return orc_vjp_pow(k, d, N, n, supp_ptr, supp_idx, NULL, coeff, input, upstream, grad_input, grad_coeff,
+                       nthreads);
 }
 
 /* number of threads the oracle would use for nthreads (for reporting) */

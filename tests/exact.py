@@ -134,6 +134,43 @@ def eval_grad_fr(supports, n, coeff_fr, input_fr):
     return value, grad
 
 
+def eval_grad_pow_fr(supports, exponents, n, coeff_fr, input_fr):
+    """Monomials with exponents: a_m prod z_v^{e_v}; the partial for x_i is
+    e_i a_m z_i^{e_i - 1} prod_{v != i} z_v^{e_v}."""
+    S = len(coeff_fr[0])
+    value = list(coeff_fr[0])
+    grad = [[Fraction(0)] * S for _ in range(n)]
+
+    def power_product(start, supp, ex, skip):
+        t = list(start)
+        for v, e in zip(supp, ex):
+            for _ in range(e - (1 if v == skip else 0)):
+                t = conv_fr(t, input_fr[v])
+        return t
+
+    for m, (supp, ex) in enumerate(zip(supports, exponents)):
+        t = power_product(coeff_fr[m + 1], supp, ex, None)
+        value = [a + b for a, b in zip(value, t)]
+        for i, e in zip(supp, ex):
+            g = power_product(coeff_fr[m + 1], supp, ex, i)
+            grad[i] = [a + e * b for a, b in zip(grad[i], g)]
+    return value, grad
+
+
+def vjp_pow_fr(supports, exponents, n, coeff_fr, input_fr, u_fr):
+    _, grad = eval_grad_pow_fr(supports, exponents, n, coeff_fr, input_fr)
+    gin = [corr_fr(u_fr, grad[i]) for i in range(n)]
+    S = len(u_fr)
+    gco = [list(u_fr)]
+    for supp, ex in zip(supports, exponents):
+        mono = [Fraction(1)] + [Fraction(0)] * (S - 1)
+        for v, e in zip(supp, ex):
+            for _ in range(e):
+                mono = conv_fr(mono, input_fr[v])
+        gco.append(corr_fr(u_fr, mono))
+    return gin, gco
+
+
 def vjp_fr(supports, n, coeff_fr, input_fr, u_fr):
     S = len(coeff_fr[0])
     _, grad = eval_grad_fr(supports, n, coeff_fr, input_fr)
