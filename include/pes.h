@@ -105,6 +105,17 @@ pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N,
                     int32_t k, pes_plan_t* out);
 pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
                        int32_t k, const pes_options* opt, pes_plan_t* out);
+
+/* Monomials with positive powers (Sec. 3): monomial m is
+ * a_m prod_t x_{supp_idx[t]}^{supp_exp[t]} over its support entries t.
+ * supp_exp holds one exponent in [1, 64] per support entry.  The common factor
+ * prod z_v^(e_v - 1) is formed from a table of series powers (repeated
+ * products) and folded into the coefficient series, the reverse mode runs on
+ * the monomial of exponents one, and every partial derivative is added with
+ * the variable's exponent as an integer factor; pes_eval_grad and pes_vjp then
+ * work as for any plan.  Everything else as pes_plan_ex. */
+pes_status pes_plan_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
+                           int32_t n, int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
 void pes_plan_destroy(pes_plan_t plan);
 
 /* Value and gradient of the polynomial at the input series (Sec. 4 and 5).
@@ -236,12 +247,18 @@ pes_status pes_int_peak(int32_t repeats, double* tops);
  * jobs per layer.  paper_layout = 1 counts the data array of Eq. (eqcountnum). */
 pes_status pes_jobc_stats(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                           int32_t paper_layout, int64_t* stats, int32_t* layer_sizes, int32_t cap);
+/* The same for monomials with powers (supp_exp as in pes_plan_powers). */
+pes_status pes_jobc_stats_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
+                                 int32_t n, int32_t paper_layout, int64_t* stats, int32_t* layer_sizes, int32_t cap);
 
 /* Convolution jobs in dispatch order: jobs[4 t + 0..3] = (input 1, input 2,
  * output, layer), inputs and outputs as slots of the data array (multiply by
  * d+1 for the paper's offsets of Sec. 5); at most cap jobs. */
 pes_status pes_jobc_jobs(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                          int32_t paper_layout, int32_t* jobs, int64_t cap);
+/* The same for monomials with powers (supp_exp as in pes_plan_powers). */
+pes_status pes_jobc_jobs_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
+                                int32_t n, int32_t paper_layout, int32_t* jobs, int64_t cap);
 
 /* Sizes of the levels of the paper's pairwise addition tree (Sec. 5 and the
  * launch counts of Sec. 6.1); at most cap levels, *nlevels receives the count. */
@@ -255,6 +272,11 @@ pes_status pes_jobc_add_levels(const int32_t* supp_ptr, const int32_t* supp_idx,
  * add_ptr: n+2 entries; at most cap terms are written. */
 pes_status pes_jobc_add_terms(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                               int32_t* add_ptr, int32_t* add_src, int64_t cap);
+/* The same for monomials with powers; add_mult[t] receives the integer factor
+ * of term t (the exponent of the variable for a partial derivative, else 1). */
+pes_status pes_jobc_add_terms_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                     int32_t N, int32_t n, int32_t* add_ptr, int32_t* add_src, int32_t* add_mult,
+                                     int64_t cap);
 
 /* Self-test of the failure path: runs the convolution kernel on one job that
  * waits for a completion flag nobody sets, with the given bound (ms).  Returns

@@ -14,6 +14,16 @@
 // is the coefficient series a itself.
 // bA is kept in its own slot (the paper updates b_{n-2} in place) so that the
 // product of the variables alone stays available to the VJP.
+//
+// Monomials with positive powers (Sec. 3): a x_{i_1}^{e_1} ... x_{i_n}^{e_n} is
+// a' x_{i_1} ... x_{i_n} with the common factor F = prod z_{i_v}^{e_v - 1}
+// folded into the coefficient, a' = a * F, which the reverse mode above then
+// uses in place of a.  The powers z^q come from a table built by repeated
+// products (z^2 = z z, z^q = z^{q-1} z), F is the product of the powers its
+// variables need, and the partial for x_{i_v} is e_v times the exponent-one
+// partial (the derivative of z^{e} is e z^{e-1}): the addition stage adds that
+// contribution with the integer factor e_v.  Every job sits in the earliest
+// layer its operands allow.
 #include "jobc.hpp"
 
 #include <algorithm>
@@ -34,6 +44,14 @@ std::string validate(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t 
         return "indices not strictly increasing in monomial " + std::to_string(m);
     }
   }
+  return "";
+}
+
+std::string validate_exponents(const int32_t* ptr, const int32_t* ex, int32_t N) {
+  if (ex == nullptr) return "";
+  for (int32_t t = 0; t < (N > 0 ? ptr[N] : 0); ++t)
+    if (ex[t] < 1 || ex[t] > kMaxExponent)
+      return "exponent out of [1, " + std::to_string(kMaxExponent) + "] at support entry " + std::to_string(t);
   return "";
 }
 
@@ -106,28 +124,80 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   }
   P.n_slots = next;
 
-  // ---- convolution jobs ----
+  // ---- power table, common factors and a' (monomials with exponents > 1) ----
+  // q-th power of z_v: the input slot for q = 1, else a table slot
+  std::vector<int32_t> qmax(static_cast<size_t>(n), 1);
+  for (int32_t t = 0; t < (N > 0 ? s.ptr[static_cast<size_t>(N)] : 0); ++t)
+    qmax[static_cast<size_t>(s.idx[static_cast<size_t>(t)])] =
+        std::max(qmax[static_cast<size_t>(s.idx[static_cast<size_t>(t)])], s.exponent(t) - 1);
+  std::vector<int32_t> pow0(static_cast<size_t>(n), -1);  // slot of z_v^2 (z_v^q at pow0 + q - 2)
+  for (int32_t v = 0; v < n; ++v) {
+    if (qmax[static_cast<size_t>(v)] >= 2) {
+      pow0[static_cast<size_t>(v)] = next;
+      next += qmax[static_cast<size_t>(v)] - 1;
+      P.has_powers = true;
+    }
+  }
+  auto POW = [&](int32_t v, int32_t q) { return q == 1 ? Z(v) : pow0[static_cast<size_t>(v)] + q - 2; };
+  std::vector<int32_t> acoef(static_cast<size_t>(N));  // slot of the coefficient the reverse mode uses
+  std::vector<std::vector<int32_t>> fchain(static_cast<size_t>(N));  // common-factor chain slots
+  for (int32_t m = 0; m < N; ++m) {
+    acoef[static_cast<size_t>(m)] = A(m + 1);
+    int32_t np = 0;
+    for (int32_t t = s.ptr[static_cast<size_t>(m)]; t < s.ptr[static_cast<size_t>(m) + 1]; ++t) np += s.exponent(t) >= 2;
+    if (np == 0) continue;
+    P.has_powers = true;
+    for (int32_t c = 0; c + 1 < np; ++c) fchain[static_cast<size_t>(m)].push_back(next++);
+    acoef[static_cast<size_t>(m)] = next++;
+  }
+  std::vector<int32_t> mfactor(static_cast<size_t>(N), -1);  // slot of the common factor F_m
+  P.n_slots = next;
+
+  // ---- convolution jobs, each in the earliest layer its operands allow ----
   Builder B;
+  std::vector<int32_t> ready(static_cast<size_t>(next), 0);  // layer after which a slot holds its series
   int32_t max_layer = 0;
+  auto job = [&](int32_t in1, int32_t in2, int32_t out) {
+    const int32_t layer = 1 + std::max(ready[static_cast<size_t>(in1)], ready[static_cast<size_t>(in2)]);
+    B.add(in1, in2, out, layer);
+    ready[static_cast<size_t>(out)] = layer;
+    max_layer = std::max(max_layer, layer);
+  };
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t q = 2; q <= qmax[static_cast<size_t>(v)]; ++q) job(POW(v, q - 1), Z(v), POW(v, q));
+  for (int32_t m = 0; m < N; ++m) {
+    if (acoef[static_cast<size_t>(m)] == A(m + 1)) continue;
+    std::vector<int32_t> factors;
+    for (int32_t t = s.ptr[static_cast<size_t>(m)]; t < s.ptr[static_cast<size_t>(m) + 1]; ++t)
+      if (s.exponent(t) >= 2) factors.push_back(POW(s.idx[static_cast<size_t>(t)], s.exponent(t) - 1));
+    int32_t f = factors[0];
+    for (size_t c = 1; c < factors.size(); ++c) {
+      const int32_t o = fchain[static_cast<size_t>(m)][c - 1];
+      job(f, factors[c], o);
+      f = o;
+    }
+    mfactor[static_cast<size_t>(m)] = f;
+    job(A(m + 1), f, acoef[static_cast<size_t>(m)]);
+  }
+  P.power_jobs = static_cast<int32_t>(B.jobs.size());
   for (int32_t m = 0; m < N; ++m) {
     const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
     const int32_t* v = s.idx.data() + s.ptr[m];
-    const int32_t nk = ms.nk, k = m + 1;
+    const int32_t nk = ms.nk, a = acoef[static_cast<size_t>(m)];
     auto f = [&](int32_t l) { return ms.f0 + l - 1; };  // f_{k,l}, l = 1..nk
     auto b = [&](int32_t l) { return ms.b0 + l - 1; };  // b_{k,l}
     auto c = [&](int32_t l) { return ms.c0 + l - 1; };  // c_{k,l}
-    B.add(A(k), Z(v[0]), f(1), 1);
-    for (int32_t l = 2; l <= nk; ++l) B.add(f(l - 1), Z(v[l - 1]), f(l), l);
+    job(a, Z(v[0]), f(1));
+    for (int32_t l = 2; l <= nk; ++l) job(f(l - 1), Z(v[l - 1]), f(l));
     if (nk == 2) {
-      B.add(Z(v[1]), A(k), b(1), 1);
+      job(Z(v[1]), a, b(1));
     } else if (nk >= 3) {
-      B.add(Z(v[nk - 1]), Z(v[nk - 2]), b(1), 1);
-      for (int32_t l = 2; l <= nk - 2; ++l) B.add(b(l - 1), Z(v[nk - 1 - l]), b(l), l);
-      B.add(b(nk - 2), A(k), ms.bA, nk - 1);
-      for (int32_t j = 1; j <= nk - 3; ++j) B.add(f(j), b(nk - 2 - j), c(j), std::max(j, nk - 2 - j) + 1);
-      B.add(f(nk - 2), Z(v[nk - 1]), c(nk - 2), nk - 1);
+      job(Z(v[nk - 1]), Z(v[nk - 2]), b(1));
+      for (int32_t l = 2; l <= nk - 2; ++l) job(b(l - 1), Z(v[nk - 1 - l]), b(l));
+      job(b(nk - 2), a, ms.bA);
+      for (int32_t j = 1; j <= nk - 3; ++j) job(f(j), b(nk - 2 - j), c(j));
+      job(f(nk - 2), Z(v[nk - 1]), c(nk - 2));
     }
-    max_layer = std::max(max_layer, nk);
   }
   P.jobs = B.jobs;
   finalize(P.jobs, P.n_slots);
@@ -137,28 +207,35 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   for (int32_t L = 1; L <= max_layer; ++L) P.layer_ptr[static_cast<size_t>(L)] += P.layer_ptr[static_cast<size_t>(L) - 1];
 
   // ---- addition stage: value and gradient contributions, monomial order ----
-  std::vector<std::vector<int32_t>> contrib(static_cast<size_t>(n) + 1);
-  contrib[0].push_back(0);  // a_0
+  // (slot, integer factor): the factor of a partial is the variable's exponent
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> contrib(static_cast<size_t>(n) + 1);
+  contrib[0].push_back({0, 1});  // a_0
   for (int32_t m = 0; m < N; ++m) {
     const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
     const int32_t* v = s.idx.data() + s.ptr[m];
-    const int32_t nk = ms.nk, k = m + 1;
-    contrib[0].push_back(ms.f0 + nk - 1);
+    const int32_t nk = ms.nk, t0 = s.ptr[m];
+    auto e = [&](int32_t j) { return s.exponent(t0 + j); };
+    contrib[0].push_back({ms.f0 + nk - 1, 1});
     if (nk == 1) {
-      contrib[1 + static_cast<size_t>(v[0])].push_back(A(k));
+      contrib[1 + static_cast<size_t>(v[0])].push_back({acoef[static_cast<size_t>(m)], e(0)});
     } else if (nk == 2) {
-      contrib[1 + static_cast<size_t>(v[0])].push_back(ms.b0);  // b_1 = z_{i_2} a
-      contrib[1 + static_cast<size_t>(v[1])].push_back(ms.f0);  // f_1 = a z_{i_1}
+      contrib[1 + static_cast<size_t>(v[0])].push_back({ms.b0, e(0)});  // b_1 = z_{i_2} a
+      contrib[1 + static_cast<size_t>(v[1])].push_back({ms.f0, e(1)});  // f_1 = a z_{i_1}
     } else {
-      contrib[1 + static_cast<size_t>(v[0])].push_back(ms.bA);
-      for (int32_t j = 1; j <= nk - 2; ++j) contrib[1 + static_cast<size_t>(v[j])].push_back(ms.c0 + j - 1);
-      contrib[1 + static_cast<size_t>(v[nk - 1])].push_back(ms.f0 + nk - 2);
+      contrib[1 + static_cast<size_t>(v[0])].push_back({ms.bA, e(0)});
+      for (int32_t j = 1; j <= nk - 2; ++j) contrib[1 + static_cast<size_t>(v[j])].push_back({ms.c0 + j - 1, e(j)});
+      contrib[1 + static_cast<size_t>(v[nk - 1])].push_back({ms.f0 + nk - 2, e(nk - 1)});
     }
   }
   P.add_ptr.assign(static_cast<size_t>(n) + 2, 0);
   for (size_t o = 0; o < contrib.size(); ++o) P.add_ptr[o + 1] = P.add_ptr[o] + static_cast<int32_t>(contrib[o].size());
   P.add_src.reserve(static_cast<size_t>(P.add_ptr.back()));
-  for (const auto& cl : contrib) P.add_src.insert(P.add_src.end(), cl.begin(), cl.end());
+  P.add_mult.reserve(static_cast<size_t>(P.add_ptr.back()));
+  for (const auto& cl : contrib)
+    for (const auto& sm : cl) {
+      P.add_src.push_back(sm.first);
+      P.add_mult.push_back(sm.second);
+    }
 
   if (!with_vjp || paper_layout) return P;
 
@@ -170,18 +247,33 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   V.jobs = P.jobs;  // forward products first
   for (ConvJob& j : V.jobs) j.dep1 = j.dep2 = -1;
   P.slot_M0 = nx;
+  // M_m = prod z_v^{e_v}: the product of the variables (b_{k,nk-2} * z_{i_1}),
+  // times the common factor F_m when the monomial has powers
+  ready.resize(static_cast<size_t>(nx) + 2 * static_cast<size_t>(N), 0);
+  auto vjob = [&](int32_t in1, int32_t in2, int32_t out) {
+    const int32_t layer = 1 + std::max(ready[static_cast<size_t>(in1)], ready[static_cast<size_t>(in2)]);
+    V.add(in1, in2, out, layer);
+    ready[static_cast<size_t>(out)] = layer;
+  };
   for (int32_t m = 0; m < N; ++m) {
     const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
     const int32_t* v = s.idx.data() + s.ptr[m];
+    int32_t mv;  // product of the variables, each once
     if (ms.nk == 1) {
-      P.mslot[static_cast<size_t>(m)] = Z(v[0]);
+      mv = Z(v[0]);
     } else if (ms.nk == 2) {
-      P.mslot[static_cast<size_t>(m)] = nx;
-      V.add(Z(v[0]), Z(v[1]), nx++, 1);
+      mv = nx++;
+      vjob(Z(v[0]), Z(v[1]), mv);
     } else {
-      P.mslot[static_cast<size_t>(m)] = nx;
-      V.add(ms.b0 + ms.nk - 3, Z(v[0]), nx++, ms.nk - 1);  // b_{k,nk-2} * z_{i_1}
+      mv = nx++;
+      vjob(ms.b0 + ms.nk - 3, Z(v[0]), mv);  // b_{k,nk-2} * z_{i_1}
     }
+    if (mfactor[static_cast<size_t>(m)] >= 0) {
+      const int32_t o = nx++;
+      vjob(mv, mfactor[static_cast<size_t>(m)], o);
+      mv = o;
+    }
+    P.mslot[static_cast<size_t>(m)] = mv;
   }
   P.slot_g0 = nx;
   nx += n;

@@ -75,11 +75,18 @@ struct MonoSlots {
 struct Supports {
   int32_t N = 0, n = 0;
   std::vector<int32_t> ptr, idx;  // CSR, 0-based, increasing per row
+  std::vector<int32_t> ex;        // exponent of every support entry (empty: all 1)
+  int32_t exponent(int32_t t) const { return ex.empty() ? 1 : ex[static_cast<size_t>(t)]; }
 };
+
+// Largest exponent a monomial may give one variable.
+constexpr int32_t kMaxExponent = 64;
 
 // Returns "" if valid, else a message.  Rules: N >= 0, n >= 1, every monomial
 // non-empty, indices in [0, n), strictly increasing within a monomial.
 std::string validate(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t n);
+// Exponents (one per support entry): "" if every one lies in [1, kMaxExponent].
+std::string validate_exponents(const int32_t* ptr, const int32_t* ex, int32_t N);
 
 // Layout and jobs of one polynomial (slot numbering local to the instance).
 struct Program1 {
@@ -93,6 +100,11 @@ struct Program1 {
   // addition stage: output 0 = value, output 1+i = d p / d x_i
   std::vector<int32_t> add_ptr;        // n+2 entries
   std::vector<int32_t> add_src;        // contributing slots
+  std::vector<int32_t> add_mult;       // integer factor of every contribution (the exponent of the variable)
+  // monomials with powers (Sec. 3): series powers z_v^q, common factors and the
+  // coefficients a'_m = a_m * prod z_v^(e_v - 1) that the reverse mode uses
+  bool has_powers = false;
+  int32_t power_jobs = 0;              // jobs of the power table, the common factors and the a'_m
   // VJP extras (slots after the eval+grad layout)
   int32_t slot_u = -1;                 // upstream series
   int32_t slot_M0 = -1;                // M_k (k = 1..N) at slot_M0 + k - 1 (or an input slot, see mslot)

@@ -732,9 +732,10 @@ __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
       const int sh = gmax - slot[gofs];  // digits below the common grid's top
       if (sh >= L) continue;               // below the last digit
       const int32_t* row = slot + rofs;
+      const long long mu = a.mult ? a.mult[c] : 1;  // the exponent of the variable (Sec. 3)
 #pragma unroll
       for (int q = 0; q < L; ++q)
-        if (q >= sh) acc[q] += row[q - sh];
+        if (q >= sh) acc[q] += mu * row[q - sh];
     }
   }
 #pragma unroll

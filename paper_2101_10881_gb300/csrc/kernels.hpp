@@ -48,6 +48,7 @@ struct AddArgs {
   int32_t to_ws;            // 1: results in digit form into workspace slot dst_off of the instance
   const int64_t* item_ptr;  // nouts + 1 prefix sums of (d + 1) over outputs
   const int32_t* contrib;
+  const int32_t* mult;      // integer factor of every contribution (nullptr: all 1)
   const InstInfo* inst;
   int32_t* ws;
   double* dst[2];           // k-limb results: caller buffers by selector

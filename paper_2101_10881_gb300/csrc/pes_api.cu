@@ -62,6 +62,7 @@ struct AddTable {
   pes::AddOut* outs = nullptr;
   int64_t* item_ptr = nullptr;
   int32_t* contrib = nullptr;
+  int32_t* mult = nullptr;  // integer factor per contribution (nullptr: all 1)
   int32_t nouts = 0;
   int64_t items = 0;
 };
@@ -131,8 +132,9 @@ struct Exec {
     return PES_OK;
   }
 
+  // mult: integer factor of every contribution, or empty when all are 1
   pes_status make_add(AddTable& A, const std::vector<pes::AddOut>& outs, const std::vector<int32_t>& contrib,
-                      const std::vector<pes::InstInfo>& insts) {
+                      const std::vector<pes::InstInfo>& insts, const std::vector<int32_t>& mult = {}) {
     A.nouts = static_cast<int32_t>(outs.size());
     std::vector<int64_t> ip(outs.size() + 1, 0);
     for (size_t o = 0; o < outs.size(); ++o) ip[o + 1] = ip[o] + insts[static_cast<size_t>(outs[o].inst)].d + 1;
@@ -140,6 +142,8 @@ struct Exec {
     pes_status s = put(&A.outs, outs);
     if (s == PES_OK) s = put(&A.item_ptr, ip);
     if (s == PES_OK) s = put(&A.contrib, contrib);
+    const bool ones = std::all_of(mult.begin(), mult.end(), [](int32_t v) { return v == 1; });
+    if (s == PES_OK && !ones) s = put(&A.mult, mult);
     return s;
   }
 
@@ -260,6 +264,7 @@ struct Exec {
     a.to_ws = (dst0 == nullptr && dst1 == nullptr) ? 1 : 0;
     a.item_ptr = A.item_ptr;
     a.contrib = A.contrib;
+    a.mult = A.mult;
     a.inst = inst;
     a.ws = ws;
     a.dst[0] = dst0;
@@ -335,19 +340,40 @@ pes_status parse_options(const pes_options* opt, pes_options& o) {
   return PES_OK;
 }
 
-pes_status build_supports(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t n, pes::Supports& s) {
+pes_status build_supports(const int32_t* ptr, const int32_t* idx, int32_t N, int32_t n, pes::Supports& s,
+                          const int32_t* ex = nullptr) {
   std::string msg = pes::validate(ptr, idx, N, n);
+  if (!msg.empty()) return fail(PES_EINVAL, msg);
+  msg = pes::validate_exponents(ptr, ex, N);
   if (!msg.empty()) return fail(PES_EINVAL, msg);
   s.N = N;
   s.n = n;
   if (N == 0) {
     s.ptr.assign(1, 0);
     s.idx.clear();
+    s.ex.clear();
   } else {
     s.ptr.assign(ptr, ptr + (N + 1));
     s.idx.assign(idx, idx + s.ptr.back());
+    if (ex != nullptr && std::any_of(ex, ex + s.ptr.back(), [](int32_t e) { return e != 1; }))
+      s.ex.assign(ex, ex + s.ptr.back());
+    else
+      s.ex.clear();
   }
   return PES_OK;
+}
+
+// Dependencies of a job list taken out of a larger one: an operand produced by
+// an earlier job of the list waits for it; any other operand is already in
+// the workspace.
+void resolve_local_deps(std::vector<pes::ConvJob>& jobs) {
+  std::map<int32_t, int32_t> producer;
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    auto p1 = producer.find(jobs[j].in1), p2 = producer.find(jobs[j].in2);
+    jobs[j].dep1 = p1 == producer.end() ? -1 : p1->second;
+    jobs[j].dep2 = p2 == producer.end() ? -1 : p2->second;
+    producer[jobs[j].out] = static_cast<int32_t>(j);
+  }
 }
 
 }  // namespace
@@ -507,8 +533,26 @@ extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx,
   return pes_plan_ex(supp_ptr, supp_idx, N, n, d, k, nullptr, out);
 }
 
+namespace {
+pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N, int32_t n,
+                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
+}  // namespace
+
 extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
                                   int32_t k, const pes_options* opt, pes_plan_t* out) {
+  return plan_impl(supp_ptr, supp_idx, nullptr, N, n, d, k, opt, out);
+}
+
+extern "C" pes_status pes_plan_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                      int32_t N, int32_t n, int32_t d, int32_t k, const pes_options* opt,
+                                      pes_plan_t* out) {
+  if (!supp_exp && N > 0) return fail(PES_EINVAL, "supp_exp is NULL");
+  return plan_impl(supp_ptr, supp_idx, supp_exp, N, n, d, k, opt, out);
+}
+
+namespace {
+pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N, int32_t n,
+                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out) {
   if (!out) return fail(PES_EINVAL, "out is NULL");
   *out = nullptr;
   if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
@@ -518,7 +562,7 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
   pes_status s = parse_options(opt, o);
   if (s != PES_OK) return s;
   pes::Supports sup;
-  s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  s = build_supports(supp_ptr, supp_idx, N, n, sup, supp_exp);
   if (s != PES_OK) return s;
 
   std::unique_ptr<pes_plan_s> P(new (std::nothrow) pes_plan_s());
@@ -558,7 +602,7 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
   std::vector<pes::AddOut> outs;
   outs.push_back({0, D1, 0, 0, G.add_ptr[0], G.add_ptr[1]});
   for (int32_t i = 0; i < n; ++i) outs.push_back({i * D1, n * D1, 1, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
-  s = P->ex.make_add(P->add, outs, G.add_src, insts);
+  s = P->ex.make_add(P->add, outs, G.add_src, insts, G.add_mult);
   if (s != PES_OK) return s;
 
   if (P->with_vjp) {
@@ -567,6 +611,7 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
     std::vector<pes::ConvJob> monly;
     for (const auto& j : fwdm)
       if (j.out >= G.slot_M0 && j.out < G.slot_g0) monly.push_back(pes::ConvJob{j.in1, j.in2, j.out, -1, -1, 0, j.kind, j.layer});
+    resolve_local_deps(monly);  // M_m * F_m (monomials with powers) waits for M_m
     s = P->ex.make_joblist(P->vjp_fwd, fwdm);
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_m, monly);
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_corr, corr);
@@ -575,7 +620,7 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
     std::vector<pes::AddOut> gouts;
     for (int32_t i = 0; i < n; ++i)
       gouts.push_back({static_cast<int64_t>(G.slot_g0 + i), 0, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
-    s = P->ex.make_add(P->add_g, gouts, G.add_src, insts);
+    s = P->ex.make_add(P->add_g, gouts, G.add_src, insts, G.add_mult);
     if (s != PES_OK) return s;
     std::vector<pes::CopyRow> urow{{0, D1, 2, 0, G.slot_u, 0}};
     P->pack_u.n = 1;
@@ -593,6 +638,7 @@ extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_i
   *out = P.release();
   return PES_OK;
 }
+}  // namespace
 
 extern "C" void pes_plan_destroy(pes_plan_t plan) { delete plan; }
 
@@ -1145,9 +1191,16 @@ extern "C" pes_status pes_int_peak(int32_t repeats, double* tops) {
 
 extern "C" pes_status pes_jobc_stats(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                                      int32_t paper_layout, int64_t* stats, int32_t* layer_sizes, int32_t cap) {
+  return pes_jobc_stats_powers(supp_ptr, supp_idx, nullptr, N, n, paper_layout, stats, layer_sizes, cap);
+}
+
+extern "C" pes_status pes_jobc_stats_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                            int32_t N, int32_t n, int32_t paper_layout, int64_t* stats,
+                                            int32_t* layer_sizes, int32_t cap) {
   pes::Supports sup;
-  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup, supp_exp);
   if (s != PES_OK) return s;
+  if (paper_layout && !sup.ex.empty()) return fail(PES_EINVAL, "the paper's data array has no powers");
   pes::Program1 G = pes::compile(sup, 0, paper_layout != 0, paper_layout == 0);
   std::vector<int64_t> lv = pes::paper_add_levels(sup);
   if (stats) {
@@ -1170,9 +1223,15 @@ extern "C" pes_status pes_jobc_stats(const int32_t* supp_ptr, const int32_t* sup
 
 extern "C" pes_status pes_jobc_jobs(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                                     int32_t paper_layout, int32_t* jobs, int64_t cap) {
+  return pes_jobc_jobs_powers(supp_ptr, supp_idx, nullptr, N, n, paper_layout, jobs, cap);
+}
+
+extern "C" pes_status pes_jobc_jobs_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                           int32_t N, int32_t n, int32_t paper_layout, int32_t* jobs, int64_t cap) {
   pes::Supports sup;
-  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup, supp_exp);
   if (s != PES_OK) return s;
+  if (paper_layout && !sup.ex.empty()) return fail(PES_EINVAL, "the paper's data array has no powers");
   pes::Program1 G = pes::compile(sup, 0, paper_layout != 0, false);
   for (size_t t = 0; t < G.jobs.size() && static_cast<int64_t>(t) < cap; ++t) {
     jobs[4 * t + 0] = G.jobs[t].in1;
@@ -1196,13 +1255,21 @@ extern "C" pes_status pes_jobc_add_levels(const int32_t* supp_ptr, const int32_t
 
 extern "C" pes_status pes_jobc_add_terms(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                                          int32_t* add_ptr, int32_t* add_src, int64_t cap) {
+  return pes_jobc_add_terms_powers(supp_ptr, supp_idx, nullptr, N, n, add_ptr, add_src, nullptr, cap);
+}
+
+extern "C" pes_status pes_jobc_add_terms_powers(const int32_t* supp_ptr, const int32_t* supp_idx,
+                                                const int32_t* supp_exp, int32_t N, int32_t n, int32_t* add_ptr,
+                                                int32_t* add_src, int32_t* add_mult, int64_t cap) {
   pes::Supports sup;
-  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup);
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup, supp_exp);
   if (s != PES_OK) return s;
   pes::Program1 G = pes::compile(sup, 0, false, false);
   if (add_ptr) std::memcpy(add_ptr, G.add_ptr.data(), G.add_ptr.size() * sizeof(int32_t));
-  if (add_src)
-    for (size_t t = 0; t < G.add_src.size() && static_cast<int64_t>(t) < cap; ++t) add_src[t] = G.add_src[t];
+  for (size_t t = 0; t < G.add_src.size() && static_cast<int64_t>(t) < cap; ++t) {
+    if (add_src) add_src[t] = G.add_src[t];
+    if (add_mult) add_mult[t] = G.add_mult[t];
+  }
   return PES_OK;
 }
 

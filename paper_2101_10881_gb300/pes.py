@@ -25,7 +25,8 @@ STATUS = {0: "PES_OK", 1: "PES_EINVAL", 2: "PES_EUNSUPPORTED_K", 3: "PES_ENOMEM"
 ARITH = {"auto": -1, "fp64": 0, "int": 1}
 
 # every symbol that include/pes.h declares
-EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_destroy", "pes_eval_grad", "pes_vjp",
+EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", "pes_plan_destroy", "pes_eval_grad",
+           "pes_vjp", "pes_jobc_stats_powers", "pes_jobc_jobs_powers", "pes_jobc_add_terms_powers",
            "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
            "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_int_peak", "pes_jobc_stats", "pes_jobc_jobs",
@@ -83,6 +84,8 @@ def lib():
             sig = {
                 "pes_default_options": (None, [ctypes.POINTER(Options)]),
                 "pes_plan_ex": (i32, [ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
+                "pes_plan_powers": (i32, [ip32, ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options),
+                                          ctypes.POINTER(vp)]),
                 "pes_plan_destroy": (None, [vp]),
                 "pes_eval_grad": (i32, [vp, vp, vp, vp, vp, vp]),
                 "pes_vjp": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
@@ -104,6 +107,9 @@ def lib():
                 "pes_int_peak": (i32, [i32, dp]),
                 "pes_jobc_stats": (i32, [ip32, ip32, i32, i32, i32, ip64, ip32, i32]),
                 "pes_jobc_jobs": (i32, [ip32, ip32, i32, i32, i32, ip32, i64]),
+                "pes_jobc_stats_powers": (i32, [ip32, ip32, ip32, i32, i32, i32, ip64, ip32, i32]),
+                "pes_jobc_jobs_powers": (i32, [ip32, ip32, ip32, i32, i32, i32, ip32, i64]),
+                "pes_jobc_add_terms_powers": (i32, [ip32, ip32, ip32, i32, i32, ip32, ip32, ip32, i64]),
                 "pes_jobc_add_levels": (i32, [ip32, ip32, i32, i32, ip64, i32, ip32]),
                 "pes_jobc_add_terms": (i32, [ip32, ip32, i32, i32, ip32, ip32, i64]),
                 "pes_selftest_timeout": (i32, [i64, ip32]),
@@ -176,18 +182,36 @@ def _timing(fn, h, where):
     return {"pack_ms": ms[0], "conv_ms": ms[1], "add_ms": ms[2], "unpack_ms": ms[3], "launches": nl.value}
 
 
-class Plan:
-    """pes_plan: job tables and workspace of one polynomial on the current device."""
+def exponent_array(exponents, supports):
+    """Flat int32 exponents aligned with csr(supports)'s index array."""
+    flat = []
+    assert len(exponents) == len(supports), "one exponent list per monomial"
+    for s, e in zip(supports, exponents):
+        assert len(e) == len(s), "one exponent per variable of the monomial"
+        flat.extend(int(v) for v in e)
+    return np.ascontiguousarray(np.array(flat, dtype=np.int32))
 
-    def __init__(self, supports, n, d, k, **opts):
+
+class Plan:
+    """pes_plan: job tables and workspace of one polynomial on the current device.
+
+    exponents: None (every variable with exponent 1) or, per monomial, one
+    positive exponent per variable of its support (pes_plan_powers)."""
+
+    def __init__(self, supports, n, d, k, exponents=None, **opts):
         self.supports = [list(s) for s in supports]
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.N = len(self.supports)
         ptr, idx = csr(self.supports)
         o = make_options(**opts)
         h = ctypes.c_void_p()
-        _check(lib().pes_plan_ex(_ip32(ptr), _ip32(idx), self.N, self.n, self.d, self.k, ctypes.byref(o),
-                                 ctypes.byref(h)), "pes_plan")
+        if exponents is None:
+            _check(lib().pes_plan_ex(_ip32(ptr), _ip32(idx), self.N, self.n, self.d, self.k, ctypes.byref(o),
+                                     ctypes.byref(h)), "pes_plan")
+        else:
+            ex = exponent_array(exponents, self.supports)
+            _check(lib().pes_plan_powers(_ip32(ptr), _ip32(idx), _ip32(ex), self.N, self.n, self.d, self.k,
+                                         ctypes.byref(o), ctypes.byref(h)), "pes_plan_powers")
         self._h = h
         self.generation = 0  # bumped by every call that overwrites the workspace
 
@@ -339,25 +363,37 @@ def int_peak(repeats=5):
     return t.value
 
 
-def jobc_stats(supports, n, paper_layout=False, max_layers=4096):
+def jobc_stats(supports, n, paper_layout=False, max_layers=4096, exponents=None):
     ptr, idx = csr(supports)
     stats = np.zeros(8, dtype=np.int64)
     layers = np.zeros(max_layers, dtype=np.int32)
-    _check(lib().pes_jobc_stats(_ip32(ptr), _ip32(idx), len(supports), int(n), int(bool(paper_layout)),
-                                stats.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ip32(layers), max_layers),
-           "pes_jobc_stats")
+    sp = stats.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if exponents is None:
+        _check(lib().pes_jobc_stats(_ip32(ptr), _ip32(idx), len(supports), int(n), int(bool(paper_layout)),
+                                    sp, _ip32(layers), max_layers), "pes_jobc_stats")
+    else:
+        ex = exponent_array(exponents, supports)
+        _check(lib().pes_jobc_stats_powers(_ip32(ptr), _ip32(idx), _ip32(ex), len(supports), int(n),
+                                           int(bool(paper_layout)), sp, _ip32(layers), max_layers),
+               "pes_jobc_stats_powers")
     keys = ("conv_jobs", "layers", "add_terms", "paper_add_jobs", "slots", "add_levels", "vjp_conv", "vjp_corr")
     out = {k_: int(v) for k_, v in zip(keys, stats)}
     out["layer_sizes"] = [int(v) for v in layers[: out["layers"]]]
     return out
 
 
-def jobc_jobs(supports, n, paper_layout=False):
-    st = jobc_stats(supports, n, paper_layout)
+def jobc_jobs(supports, n, paper_layout=False, exponents=None):
+    st = jobc_stats(supports, n, paper_layout, exponents=exponents)
     ptr, idx = csr(supports)
     jobs = np.zeros((max(st["conv_jobs"], 1), 4), dtype=np.int32)
-    _check(lib().pes_jobc_jobs(_ip32(ptr), _ip32(idx), len(supports), int(n), int(bool(paper_layout)),
-                               _ip32(jobs), st["conv_jobs"]), "pes_jobc_jobs")
+    if exponents is None:
+        _check(lib().pes_jobc_jobs(_ip32(ptr), _ip32(idx), len(supports), int(n), int(bool(paper_layout)),
+                                   _ip32(jobs), st["conv_jobs"]), "pes_jobc_jobs")
+    else:
+        ex = exponent_array(exponents, supports)
+        _check(lib().pes_jobc_jobs_powers(_ip32(ptr), _ip32(idx), _ip32(ex), len(supports), int(n),
+                                          int(bool(paper_layout)), _ip32(jobs), st["conv_jobs"]),
+               "pes_jobc_jobs_powers")
     return jobs[: st["conv_jobs"]]
 
 
@@ -371,14 +407,22 @@ def jobc_add_levels(supports, n, cap=256):
     return [int(v) for v in lv[: nl.value]]
 
 
-def jobc_add_terms(supports, n):
-    st = jobc_stats(supports, n)
+def jobc_add_terms(supports, n, exponents=None):
+    """(add_ptr, add_src), and add_mult as well when exponents are given."""
+    st = jobc_stats(supports, n, exponents=exponents)
     ptr, idx = csr(supports)
     add_ptr = np.zeros(int(n) + 2, dtype=np.int32)
     add_src = np.zeros(max(st["add_terms"], 1), dtype=np.int32)
-    _check(lib().pes_jobc_add_terms(_ip32(ptr), _ip32(idx), len(supports), int(n), _ip32(add_ptr),
-                                    _ip32(add_src), st["add_terms"]), "pes_jobc_add_terms")
-    return add_ptr, add_src[: st["add_terms"]]
+    if exponents is None:
+        _check(lib().pes_jobc_add_terms(_ip32(ptr), _ip32(idx), len(supports), int(n), _ip32(add_ptr),
+                                        _ip32(add_src), st["add_terms"]), "pes_jobc_add_terms")
+        return add_ptr, add_src[: st["add_terms"]]
+    add_mult = np.zeros(max(st["add_terms"], 1), dtype=np.int32)
+    ex = exponent_array(exponents, supports)
+    _check(lib().pes_jobc_add_terms_powers(_ip32(ptr), _ip32(idx), _ip32(ex), len(supports), int(n),
+                                           _ip32(add_ptr), _ip32(add_src), _ip32(add_mult), st["add_terms"]),
+           "pes_jobc_add_terms_powers")
+    return add_ptr, add_src[: st["add_terms"]], add_mult[: st["add_terms"]]
 
 
 def selftest_timeout(timeout_ms=500):

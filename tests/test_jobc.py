@@ -72,10 +72,10 @@ def test_data_array_count_formula(seed):
     assert st["slots"] == expect
 
 
-def symbolic(supports, n, paper_layout=False):
+def symbolic(supports, n, paper_layout=False, exponents=None):
     """Interpret the job table on multisets of symbols; check the schedule."""
     N = len(supports)
-    jobs = pes.jobc_jobs(supports, n, paper_layout)
+    jobs = pes.jobc_jobs(supports, n, paper_layout, exponents=exponents)
     content = {0: Counter(["a0"])}
     for m in range(1, N + 1):
         content[m] = Counter([f"a{m}"])
@@ -144,3 +144,52 @@ def test_bench_paper_convention_count():
     import bench
     assert bench.paper_convention_ops(PC["p1_convolutions"], PC["p1_additions"], 152, 10) == \
         PC["p1_paper_total_ops_d152"]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_symbolic_powers(seed):
+    """Monomials with powers (Sec. 3): the value term of monomial m is the
+    multiset a_m z_v^{e_v}, the term of the partial for x_i is
+    a_m z_i^{e_i - 1} prod_{v != i} z_v^{e_v} with the integer factor e_i, and the
+    schedule puts every job in its earliest layer after its operands."""
+    rng = np.random.default_rng(300 + seed)
+    n = 7
+    supp = synth.random_supports(rng, n, 12, 1, 5)
+    ex = [[int(e) for e in rng.integers(1, 5, size=len(s_))] for s_ in supp]
+    content = symbolic(supp, n, exponents=ex)
+    add_ptr, add_src, add_mult = pes.jobc_add_terms(supp, n, exponents=ex)
+
+    def terms(o):
+        return sorted((tuple(sorted(content[s_].elements())), int(mu))
+                      for s_, mu in zip(add_src[add_ptr[o]:add_ptr[o + 1]], add_mult[add_ptr[o]:add_ptr[o + 1]]))
+
+    def mono(m, skip=None):
+        out = [f"a{m + 1}"]
+        for v, e in zip(supp[m], ex[m]):
+            out += [f"z{v}"] * (e - (1 if v == skip else 0))
+        return tuple(sorted(out))
+
+    assert terms(0) == sorted([(("a0",), 1)] + [(mono(m), 1) for m in range(len(supp))])
+    for i in range(n):
+        want = sorted((mono(m, i), e) for m in range(len(supp)) for v, e in zip(supp[m], ex[m]) if v == i)
+        assert terms(1 + i) == want
+
+
+def test_powers_job_counts():
+    """x0^3 x1^2 x2: powers z0^2 (1 job); the common factor z0^2 z1 (1 job);
+    a' = a F (1 job); then the 3n - 3 = 6 products of the exponent-one monomial."""
+    st = pes.jobc_stats([[0, 1, 2]], 3, exponents=[[3, 2, 1]])
+    assert st["conv_jobs"] == 1 + 1 + 1 + 6
+    # exponents all 1: exactly the plain tables
+    plain = pes.jobc_stats([[0, 1, 2]], 3)
+    ones = pes.jobc_stats([[0, 1, 2]], 3, exponents=[[1, 1, 1]])
+    assert plain == ones
+
+
+def test_invalid_exponents():
+    for bad in ([[0, 1]], [[1, 65]], [[-1, 2]]):
+        with pytest.raises(pes.PesError) as e:
+            pes.jobc_stats([[0, 1]], 2, exponents=bad)
+        assert e.value.code == 1
+    with pytest.raises(pes.PesError):
+        pes.jobc_stats([[0, 1]], 2, paper_layout=True, exponents=[[2, 1]])
