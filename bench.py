@@ -74,6 +74,8 @@ def parse_args(argv=None):
                          "--workload batch; 0 skips it in the default run)")
     ap.add_argument("--batch-k", type=int, default=2)
     ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--no-powers", action="store_true",
+                    help="skip the measurement of the workload with powers (monomials with exponents 1-3)")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
                     help="variables of the monomial the oracle evaluates as the CPU sample")
     return ap.parse_args(argv)
@@ -481,6 +483,8 @@ def ours_arm(args, world, rank, local):
     }
     if not args.no_autograd:
         out["autograd"] = autograd_measure(args, dev, flush)
+    if args.workload == "p2" and not args.no_powers:
+        out["powers"] = powers_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     count = 256 if args.batch_count is None else args.batch_count
     if count > 0:
         out["batched"] = batch_measure(args, dev, count)
@@ -531,6 +535,46 @@ def autograd_measure(args, dev, flush):
             "forward_ms": f, "backward_ms": b, "backward_over_forward": b / f,
             "backward_reuses_forward_products": True,
             "vjp_jobs": {"monomial_products": info["vjp_conv_jobs"], "correlations": info["vjp_corr_jobs"]}}
+
+
+def powers_measure(args, dev, flush, peak):
+    """Monomials with powers (Sec. 3): the p2-like workload (n=128, 128 monomials
+    of 64 variables, d=152, k=10) with every exponent drawn uniformly from 1-3.
+    Every convolution counts, the power table and the common factors included;
+    ms per eval+grad step with CUDA events and an L2 flush between steps."""
+    import numpy as np
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    prob = synth.config1(seed=args.seed)
+    rng = np.random.default_rng(args.seed + 31)
+    ex = [[int(e) for e in rng.integers(1, 4, size=len(s_))] for s_ in prob.supports]
+    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, exponents=ex, with_vjp=False, profile=True,
+                    autotune=not args.no_autotune)
+    C = torch.from_numpy(prob.coeff).to(dev)
+    Z = torch.from_numpy(prob.inputs).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    times, conv = [], []
+    for it in range(max(args.warmup, 3) + args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval_grad(C, Z)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= max(args.warmup, 3):
+            times.append(e0.elapsed_time(e1))
+            conv.append(plan.last_timing()["conv_ms"])
+    plan.check()
+    info = plan.info()
+    ms, cms = statistics.mean(times), statistics.mean(conv)
+    ops = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], prob.d, prob.k)
+    macs = digit_fma_flops(info["conv_jobs"], prob.d, info["digits"]) / 2
+    plain = pes.jobc_stats(prob.supports, prob.n)["conv_jobs"]
+    return {"workload": "p2-like, n=128, 128 monomials of 64 variables, exponents uniform in 1-3, d=152, k=10",
+            "ms_per_step": ms, "value": ops / (ms * 1e-3) / 1e12, "unit": UNIT,
+            "conv_jobs": info["conv_jobs"], "power_and_factor_jobs": info["conv_jobs"] - plain,
+            "roofline_frac": (macs / (cms * 1e-3) / 1e12) / peak if peak else None,
+            "kernel_ms": cms, "threads_per_cta": info["threads"], "arith": info["arith_name"]}
 
 
 def batch_measure(args, dev, count, small=False):
