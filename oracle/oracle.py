@@ -60,6 +60,7 @@ def _load():
                 "orc_vjp": [c_int, c_int, c_int, c_int, ip, ip, dp, dp, dp, dp, dp, c_int],
                 "orc_eval_grad_pow": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, c_int],
                 "orc_vjp_pow": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, dp, c_int],
+                "orc_eval_grad_complex": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp],
                 "orc_threads": [c_int],
                 "orc_conv_many": [c_int, c_int, c_int, dp, dp, dp, c_int],
             }.items():
@@ -182,6 +183,25 @@ def eval_grad(supports, n, coeff, inputs, nthreads: int = 0, grad: bool = True, 
     else:
         _check(_load().orc_eval_grad_pow(k, s - 1, N, n, _ip(ptr), _ip(idx), _ip(ex), _dp(coeff),
                                          _dp(inputs), _dp(value), gp, nthreads), "eval_grad_pow")
+    return (value, g) if grad else value
+
+
+def eval_grad_complex(supports, n, coeff, inputs, exponents=None, grad: bool = True):
+    """Complex coefficients and inputs: coeff (2, k, N+1, d+1), inputs
+    (2, k, n, d+1), index 0 of the first axis the real part.  Returns value
+    (2, k, d+1) and gradient (2, k, n, d+1)."""
+    coeff, inputs = _f64(coeff), _f64(inputs)
+    two, k, n1, s = coeff.shape
+    N = len(supports)
+    assert two == 2 and n1 == N + 1 and inputs.shape == (2, k, n, s)
+    ptr, idx = _supports(supports)
+    ex = _exponents(exponents, supports)
+    exp_p = _ip(ex) if ex is not None else ctypes.POINTER(ctypes.c_int32)()
+    value = np.empty((2, k, s))
+    g = np.empty((2, k, n, s)) if grad else None
+    gp = _dp(g) if grad else ctypes.POINTER(ctypes.c_double)()
+    _check(_load().orc_eval_grad_complex(k, s - 1, N, n, _ip(ptr), _ip(idx), exp_p, _dp(coeff), _dp(inputs),
+                                         _dp(value), gp), "eval_grad_complex")
     return (value, g) if grad else value
 
 

@@ -652,6 +652,183 @@ int orc_vjp(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *
                        nthreads);
 }
 
+/* ------------------------------------------------------------------------- */
+/* complex series (Re and Im each a k-double series)                          */
+/* ------------------------------------------------------------------------- */
+
+/* e -= x * y exactly (negating a double is exact) */
+static void sub_product(expn *e, int k, const double *x, size_t sx, const double *y, size_t sy)
+{
+    for (int p = 0; p < k; ++p) {
+        double xp = -x[(size_t)p * sx];
+        if (xp == 0.0)
+            continue;
+        for (int q = 0; q < k; ++q) {
+            double yq = y[(size_t)q * sy];
+            if (yq == 0.0)
+                continue;
+            double ph, pl;
+            two_prod(xp, yq, &ph, &pl);
+            grow(e, pl);
+            grow(e, ph);
+        }
+    }
+}
+
+/* A complex series: real and imaginary part, same limb stride. */
+typedef struct {
+    const double *re, *im;
+    size_t ls;
+} ccser;
+
+typedef struct {
+    double *re, *im;
+    size_t ls;
+} cpser;
+
+/* z = x * y truncated at degree d, complex: coefficient j of Re z is the exact
+ * sum of xr_i yr_{j-i} - xi_i yi_{j-i}, of Im z the exact sum of
+ * xr_i yi_{j-i} + xi_i yr_{j-i}, each rounded once to k limbs. */
+static void cconv(int k, int d, ccser x, ccser y, cpser z, expn *e)
+{
+    for (int j = 0; j <= d; ++j) {
+        e->m = 0;
+        for (int i = 0; i <= j; ++i) {
+            add_product(e, k, x.re + i, x.ls, y.re + (j - i), y.ls);
+            sub_product(e, k, x.im + i, x.ls, y.im + (j - i), y.ls);
+        }
+        round_k(e, k, z.re + j, z.ls);
+        e->m = 0;
+        for (int i = 0; i <= j; ++i) {
+            add_product(e, k, x.re + i, x.ls, y.im + (j - i), y.ls);
+            add_product(e, k, x.im + i, x.ls, y.re + (j - i), y.ls);
+        }
+        round_k(e, k, z.im + j, z.ls);
+    }
+}
+
+/* Complex analogue of monomial_product: the start series (a_m, or 1 when
+ * m < 1) times every variable's series as often as its exponent, `skip` once
+ * fewer.  Real and imaginary parts of coeff and input are separate blocks
+ * (cimag / iimag doubles after the real ones).  out: 2 k S doubles (Re, Im). */
+static void cmonomial_product(int k, int d, size_t S, const double *coeff, size_t cstride, size_t cimag,
+                              const double *input, size_t istride, size_t iimag, const int32_t *vars,
+                              const int32_t *ex, int nv, int m, int skip, double *out, double *t0, double *t1,
+                              expn *e)
+{
+    const size_t blk = (size_t)k * S;
+    double *cur = t0, *nxt = t1; /* each: Re block then Im block, limb stride S */
+    if (m >= 1) {
+        for (int l = 0; l < k; ++l) {
+            memcpy(cur + (size_t)l * S, coeff + (size_t)l * cstride + (size_t)m * S, sizeof(double) * S);
+            memcpy(cur + blk + (size_t)l * S, coeff + cimag + (size_t)l * cstride + (size_t)m * S,
+                   sizeof(double) * S);
+        }
+    } else {
+        memset(cur, 0, sizeof(double) * 2 * blk);
+        cur[0] = 1.0;
+    }
+    for (int v = 0; v < nv; ++v) {
+        int reps = (ex ? ex[v] : 1) - (vars[v] == skip ? 1 : 0);
+        for (int r = 0; r < reps; ++r) {
+            ccser a = {cur, cur + blk, S};
+            ccser b = {input + (size_t)vars[v] * S, input + iimag + (size_t)vars[v] * S, istride};
+            cpser c = {nxt, nxt + blk, S};
+            cconv(k, d, a, b, c, e);
+            double *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+    }
+    memcpy(out, cur, sizeof(double) * 2 * blk);
+}
+
+/*
+ * Complex coefficients and inputs (the polynomial of orc_eval_grad_pow over
+ * complex series): coeff [2][k][N+1][d+1], input [2][k][n][d+1], value
+ * [2][k][d+1], grad [2][k][n][d+1], each the real block followed by the
+ * imaginary block.  Every complex product is formed exactly per component and
+ * rounded once; sums are exact per component, rounded once.  supp_exp may be
+ * NULL.  grad may be NULL.
+ */
+int orc_eval_grad_complex(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
+                          const int32_t *supp_exp, const double *coeff, const double *input, double *value,
+                          double *grad)
+{
+    if (!valid_k(k) || d < 0 || check_supports(N, n, supp_ptr, supp_idx) ||
+        check_exponents(N, supp_ptr, supp_exp))
+        return 1;
+    const size_t S = (size_t)d + 1;
+    const size_t cstride = (size_t)(N + 1) * S, cimag = (size_t)k * cstride;
+    const size_t istride = (size_t)n * S, iimag = (size_t)k * istride;
+    const size_t blk = (size_t)k * S;
+    int fail = 0;
+    double *prod = (double *)malloc(sizeof(double) * 6 * blk);
+    expn e;
+    expn *acc = (expn *)calloc(2 * S, sizeof(expn));
+    if (!prod || !acc || !expn_init(&e, 8 * k * k + 64)) {
+        free(prod);
+        free(acc);
+        return 3;
+    }
+    for (size_t j = 0; j < 2 * S; ++j)
+        if (!expn_init(&acc[j], 64))
+            fail = 1;
+    /* value: a_0 plus every monomial */
+    for (size_t j = 0; j < S && !fail; ++j) {
+        add_value(&acc[j], k, coeff + j, cstride);
+        add_value(&acc[S + j], k, coeff + cimag + j, cstride);
+    }
+    for (int m = 0; m < N && !fail; ++m) {
+        const int32_t *vars = supp_idx + supp_ptr[m];
+        const int32_t *ex = supp_exp ? supp_exp + supp_ptr[m] : NULL;
+        int nv = supp_ptr[m + 1] - supp_ptr[m];
+        cmonomial_product(k, d, S, coeff, cstride, cimag, input, istride, iimag, vars, ex, nv, m + 1, -1, prod,
+                          prod + 2 * blk, prod + 4 * blk, &e);
+        for (size_t j = 0; j < S; ++j) {
+            add_value(&acc[j], k, prod + j, S);
+            add_value(&acc[S + j], k, prod + blk + j, S);
+        }
+    }
+    for (size_t j = 0; j < S && !fail; ++j) {
+        round_k(&acc[j], k, value + j, S);
+        round_k(&acc[S + j], k, value + blk + j, S);
+    }
+    /* gradient: every partial afresh, added e_i times */
+    for (int i = 0; i < n && grad && !fail; ++i) {
+        for (size_t j = 0; j < 2 * S; ++j)
+            acc[j].m = 0;
+        for (int m = 0; m < N; ++m) {
+            const int32_t *vars = supp_idx + supp_ptr[m];
+            const int32_t *ex = supp_exp ? supp_exp + supp_ptr[m] : NULL;
+            int nv = supp_ptr[m + 1] - supp_ptr[m];
+            int mult = 0;
+            for (int v = 0; v < nv; ++v)
+                if (vars[v] == i)
+                    mult = ex ? ex[v] : 1;
+            if (!mult)
+                continue;
+            cmonomial_product(k, d, S, coeff, cstride, cimag, input, istride, iimag, vars, ex, nv, m + 1, i,
+                              prod, prod + 2 * blk, prod + 4 * blk, &e);
+            for (int r = 0; r < mult; ++r)
+                for (size_t j = 0; j < S; ++j) {
+                    add_value(&acc[j], k, prod + j, S);
+                    add_value(&acc[S + j], k, prod + blk + j, S);
+                }
+        }
+        for (size_t j = 0; j < S; ++j) {
+            round_k(&acc[j], k, grad + (size_t)i * S + j, istride);
+            round_k(&acc[S + j], k, grad + iimag + (size_t)i * S + j, istride);
+        }
+    }
+    for (size_t j = 0; j < 2 * S; ++j)
+        expn_free(&acc[j]);
+    free(acc);
+    free(prod);
+    expn_free(&e);
+    return fail ? 3 : 0;
+}
+
 /* number of threads the oracle would use for nthreads (for reporting) */
 int orc_threads(int nthreads) { return used_threads(nthreads); }
 

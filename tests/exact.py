@@ -182,3 +182,42 @@ def vjp_fr(supports, n, coeff_fr, input_fr, u_fr):
             mono = conv_fr(mono, input_fr[v])
         gco.append(corr_fr(u_fr, mono))
     return gin, gco
+
+
+# ---------------------------------------------------------------------------
+# complex series as pairs of Fraction lists (tiny cases only)
+# ---------------------------------------------------------------------------
+
+def cconv_fr(x, y):
+    """x, y: (re, im) pairs of Fraction lists; the truncated complex product."""
+    xr, xi = x
+    yr, yi = y
+    d = len(xr) - 1
+    re = [sum((xr[i] * yr[j - i] - xi[i] * yi[j - i] for i in range(j + 1)), Fraction(0)) for j in range(d + 1)]
+    im = [sum((xr[i] * yi[j - i] + xi[i] * yr[j - i] for i in range(j + 1)), Fraction(0)) for j in range(d + 1)]
+    return re, im
+
+
+def eval_grad_complex_fr(supports, exponents, n, coeff_fr, input_fr):
+    """coeff_fr[m] / input_fr[v]: (re, im) pairs of Fraction lists."""
+    S = len(coeff_fr[0][0])
+    zero = [Fraction(0)] * S
+    one = ([Fraction(1)] + [Fraction(0)] * (S - 1), list(zero))
+    exponents = exponents or [[1] * len(s) for s in supports]
+    value = (list(coeff_fr[0][0]), list(coeff_fr[0][1]))
+    grad = [(list(zero), list(zero)) for _ in range(n)]
+
+    def power_product(start, supp, ex, skip):
+        t = start
+        for v, e in zip(supp, ex):
+            for _ in range(e - (1 if v == skip else 0)):
+                t = cconv_fr(t, input_fr[v])
+        return t
+
+    for m, (supp, ex) in enumerate(zip(supports, exponents)):
+        t = power_product(coeff_fr[m + 1], supp, ex, None)
+        value = ([a + b for a, b in zip(value[0], t[0])], [a + b for a, b in zip(value[1], t[1])])
+        for i, e in zip(supp, ex):
+            g = power_product(coeff_fr[m + 1], supp, ex, i)
+            grad[i] = ([a + e * b for a, b in zip(grad[i][0], g[0])], [a + e * b for a, b in zip(grad[i][1], g[1])])
+    return value, grad, one
