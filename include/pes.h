@@ -116,6 +116,17 @@ pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t
  * work as for any plan.  Everything else as pes_plan_ex. */
 pes_status pes_plan_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
                            int32_t n, int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
+
+/* Complex coefficient and input series (Sec. 4 and 5 keep real and imaginary
+ * parts in separate arrays).  pes_eval_grad on such a plan takes
+ *   coeff [2][k][N+1][d+1], input [2][k][n][d+1], value [2][k][d+1], grad [2][k][n][d+1],
+ * the real block followed by the imaginary block.  Every complex product is
+ * four real ones combined exactly (the real part xr yr - xi yi, the imaginary
+ * part xr yi + xi yr); the value and every partial are rounded once per
+ * component.  supp_exp may be NULL (exponents 1) or as in pes_plan_powers.
+ * There are no VJP tables: pes_vjp returns PES_EINVAL on a complex plan. */
+pes_status pes_plan_complex(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
+                            int32_t n, int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
 void pes_plan_destroy(pes_plan_t plan);
 
 /* Value and gradient of the polynomial at the input series (Sec. 4 and 5).
@@ -181,7 +192,7 @@ typedef struct {
   int32_t arith;           /* PES_ARITH_FP64 or PES_ARITH_INT: the pipe the plan uses */
   int32_t staging;         /* staging depth in use (1 or 2) */
   int32_t split;           /* parts per convolution job in use */
-  int32_t pad;
+  int32_t complex_series;  /* 1 for a plan of pes_plan_complex */
 } pes_plan_info;
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);

@@ -290,6 +290,59 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   return P;
 }
 
+Program1 complexify(const Program1& R) {
+  Program1 C;
+  C.N = R.N;
+  C.n = R.n;
+  C.d = R.d;
+  C.has_powers = R.has_powers;
+  C.n_input_slots = 2 * R.n_input_slots;
+  auto re = [](int32_t s) { return 2 * s; };
+  auto im = [](int32_t s) { return 2 * s + 1; };
+  int32_t next = 2 * R.n_slots;
+  std::vector<int32_t> ready(static_cast<size_t>(next) + 4 * R.jobs.size(), 0);
+  Builder B;
+  int32_t max_layer = 0;
+  auto job = [&](int32_t in1, int32_t in2, int32_t out, int32_t kind) {
+    const int32_t layer = 1 + std::max(ready[static_cast<size_t>(in1)], ready[static_cast<size_t>(in2)]);
+    B.add(in1, in2, out, layer, kind);
+    ready[static_cast<size_t>(out)] = layer;
+    max_layer = std::max(max_layer, layer);
+  };
+  for (size_t j = 0; j < R.jobs.size(); ++j) {  // R.jobs: producers before consumers
+    const ConvJob& r = R.jobs[j];
+    const int32_t t = next;
+    next += 4;
+    job(re(r.in1), re(r.in2), t, JOB_CONV);
+    job(im(r.in1), im(r.in2), t + 1, JOB_CONV);
+    job(re(r.in1), im(r.in2), t + 2, JOB_CONV);
+    job(im(r.in1), re(r.in2), t + 3, JOB_CONV);
+    job(t, t + 1, re(r.out), JOB_SUB);
+    job(t + 2, t + 3, im(r.out), JOB_ADD);
+    if (j < static_cast<size_t>(R.power_jobs)) C.power_jobs += 6;
+  }
+  C.n_slots = next;
+  C.jobs = B.jobs;
+  finalize(C.jobs, C.n_slots);
+  C.n_layers = max_layer;
+  C.layer_ptr.assign(static_cast<size_t>(max_layer) + 1, 0);
+  for (const ConvJob& j : C.jobs) C.layer_ptr[static_cast<size_t>(j.layer)]++;
+  for (int32_t L = 1; L <= max_layer; ++L) C.layer_ptr[static_cast<size_t>(L)] += C.layer_ptr[static_cast<size_t>(L) - 1];
+  const size_t nout = R.add_ptr.size() - 1;
+  C.add_ptr.assign(2 * nout + 1, 0);
+  for (size_t o = 0; o < nout; ++o) {
+    for (int part = 0; part < 2; ++part) {
+      for (int32_t t = R.add_ptr[o]; t < R.add_ptr[o + 1]; ++t) {
+        const int32_t s = R.add_src[static_cast<size_t>(t)];
+        C.add_src.push_back(part == 0 ? re(s) : im(s));
+        C.add_mult.push_back(R.add_mult.empty() ? 1 : R.add_mult[static_cast<size_t>(t)]);
+      }
+      C.add_ptr[2 * o + part + 1] = static_cast<int32_t>(C.add_src.size());
+    }
+  }
+  return C;
+}
+
 std::vector<int64_t> paper_add_levels(const Supports& s) {
   std::vector<int64_t> sizes;
   sizes.push_back(static_cast<int64_t>(s.N) + 1);  // value: a_0 and N forward products

@@ -14,7 +14,10 @@
 namespace pes {
 
 // Job kinds.
-enum : int32_t { JOB_CONV = 0, JOB_CORR = 1 };
+// CONV: out = in1 * in2 truncated (Eq. eqconvform); CORR: the truncated
+// correlation of the VJP; ADD / SUB: out = in1 + in2 / in1 - in2, coefficient
+// by coefficient (complex products combine their real products with them).
+enum : int32_t { JOB_CONV = 0, JOB_CORR = 1, JOB_ADD = 2, JOB_SUB = 3 };
 
 // Where instance `inst` keeps series slot s (in int32 words from the workspace
 // base): slot s starts at ws_base + s * ws_sstride and holds S rows of digits
@@ -120,6 +123,15 @@ struct Program1 {
 // array of Eq. (eqcountnum) (b_{k,nk-2} updated in place, no VJP extras); it is
 // used for the offset/count checks against the paper only.
 Program1 compile(const Supports& s, int32_t d, bool paper_layout = false, bool with_vjp = false);
+
+// The same polynomial over complex series: every slot s of the real program
+// becomes the pair (2s, 2s + 1) (real, imaginary part), every product
+// x * y becomes four real products xr yr, xi yi, xr yi, xi yr (four scratch
+// slots) and the ADD / SUB jobs re = xr yr - xi yi, im = xr yi + xi yr; the
+// addition stage sums real and imaginary parts separately, output 2o the real
+// and 2o + 1 the imaginary part of output o of the real program.  No VJP
+// tables.  Every job sits in the earliest layer its operands allow.
+Program1 complexify(const Program1& real);
 
 // Addition-tree level sizes of the paper's pairwise summation (Sec. 5, read with
 // a_0 as one more term of the value sum): each level pairs floor(m/2) of a list

@@ -360,253 +360,293 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
     }
     phase ^= 1u;
 
-    // ---- staged digit rows into the layouts of the multiply-accumulate loop ----
-    if constexpr (INTV) {
-      // X rows behind their zero prefix (the Y rows and both grids are in place)
-      constexpr int V4 = RW / 4;
-      const int4* src = reinterpret_cast<const int4*>(raw);
-      for (int t = tid; t < (d + 1) * V4; t += T) {
-        const int c = t / V4, v = t - c * V4;
-        const int4 q = src[t];
-        int32_t* dst = xdig + c * XS + XOFF + 4 * v;
-        if (4 * v < L) dst[0] = q.x;
-        if (4 * v + 1 < L) dst[1] = q.y;
-        if (4 * v + 2 < L) dst[2] = q.z;
-        if (4 * v + 3 < L) dst[3] = q.w;
+    const bool elementwise = jb.kind == JOB_ADD || jb.kind == JOB_SUB;
+    if (elementwise) {
+      // ---- out = in1 +- in2 coefficient by coefficient, exactly, as L digits ----
+      const int32_t* rx = raw;                                  // X rows (stride RW)
+      const int32_t* ry = INTV ? reinterpret_cast<const int32_t*>(ydig) : raw + S * RW;  // Y rows
+      const long long sgn = jb.kind == JOB_SUB ? -1 : 1;
+      for (int j = tid; j <= d; j += T) {
+        if (!owned(j)) continue;
+        const int32_t g = max(gx[j], gy[j]);
+        int32_t o[L];
+        int32_t gz = GRID_ZERO;
+        if (g < -100000) {
+#pragma unroll
+          for (int p = 0; p < L; ++p) o[p] = 0;
+        } else {
+          const int sx = g - gx[j], sy = g - gy[j];  // digits below the common grid's top
+          int64_t E[L + 1];
+          E[0] = 0;
+#pragma unroll
+          for (int q = 0; q < L; ++q) {
+            const long long xv = q >= sx ? rx[j * RW + q - sx] : 0;
+            const long long yv = q >= sy ? ry[j * RW + q - sy] : 0;
+            E[q + 1] = xv + sgn * yv;
+          }
+          gz = sum_to_digits<L, B>(E, g + 1, o);
+        }
+        int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j) * RW);
+#pragma unroll
+        for (int v = 0; v < RW / 4; ++v)
+          dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
+                             4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
+        zgrid[j] = gz;
+      }
+      __syncthreads();  // the staged rows are read: the next job may be staged
+      if (ahead && tid == stager) {
+        claim();
+        stage(false);
       }
     } else {
-      const int32_t* rx = raw;
-      const int32_t* ry = raw + S * RW;
-      for (int t = tid; t < (d + 1) * L; t += T) {
-        const int c = t / L, p = t - c * L;
-        xdig[c * XS + p] = static_cast<double>(rx[c * RW + p]);
-        ydig[c * YS + p] = static_cast<double>(ry[c * RW + p]);
-      }
-    }
-    __syncthreads();
-
-    // ---- zero the exchange rows, reference grid of every output coefficient ----
-    const int rows = (d + 1) * (L + 1);
-    for (int t = tid; t < rows; t += T) exch[t] = 0ull;
-    for (int j = tid; j <= d; j += T) {
-      if (!owned(j)) continue;
-      int32_t m = 2 * GRID_ZERO;
-      if (jb.kind == JOB_CONV) {
-        for (int i = 0; i <= j; ++i) m = max(m, gx[i] + gy[j - i]);
-      } else {
-        for (int i = 0; i <= d - j; ++i) m = max(m, gx[j + i] + gy[i]);
-      }
-      gs[j] = m;
-    }
-    __syncthreads();
-
-    // ---- multiply-accumulate ----
-    {
-      const bool conv = jb.kind == JOB_CONV;
-      AccT A[L];
-#pragma unroll
-      for (int t = 0; t < L; ++t) A[t] = 0;
-      // Add the accumulators into the exchange row of coefficient jj: A[t]
-      // belongs to word t+1 (word 0 is headroom above the grid's top digit).
-      // One flush may carry up to 2^63 per accumulator, so the values are first
-      // carried in registers: word t+1 takes the low B bits of A[t] plus the
-      // part of A[t+1] above its low B bits, word 0 the part of A[0] above B
-      // bits.  No word then takes more than about 2^(64-B) per flush, and the
-      // words stay exact however many flushes they receive.
-      auto flush = [&](int jj) {
-        unsigned long long* row = exch + jj * (L + 1);
-        long long hi_next = 0;  // part of A[t+1] above its low B bits
-#pragma unroll
-        for (int t = L - 1; t >= 0; --t) {
-          long long v;
-          if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
-          const long long w = (v & ((1LL << B) - 1)) + hi_next;
-          hi_next = v >> B;  // arithmetic shift: v = hi * 2^B + lo
-          if (w != 0) atomicAdd(row + t + 1, static_cast<unsigned long long>(w));
-          A[t] = 0;
-        }
-        if (hi_next != 0) atomicAdd(row, static_cast<unsigned long long>(hi_next));
-      };
-      // one term x_ix * y_iy of output coefficient j, delta digits below its grid
-      auto term = [&](int ix, int iy, int delta) {
-        if constexpr (INTV) {
-          if (delta < L) {
-            // zero prefix: digit p of the shifted term is xs[p], no select
-            const int32_t* xs = xdig + ix * XS + XOFF - delta;
-            const int4* y4 = reinterpret_cast<const int4*>(ydig + iy * YS);
-            int32_t Y[YS];
-#pragma unroll
-            for (int v = 0; v < YS / 4; ++v) {
-              const int4 t4 = y4[v];
-              Y[4 * v] = t4.x;
-              Y[4 * v + 1] = t4.y;
-              Y[4 * v + 2] = t4.z;
-              Y[4 * v + 3] = t4.w;
-            }
-#pragma unroll
-            for (int p = 0; p < L; ++p) {
-              const int32_t xv = xs[p];
-#pragma unroll
-              for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
-            }
-          }
-        } else {
-          if (delta < L) {
-            const DigitT* yr = ydig + iy * YS;
-            const DigitT* xr = xdig + ix * XS;
-            DigitT Y[L];
-#pragma unroll
-            for (int q = 0; q < L; ++q) Y[q] = yr[q];
-#pragma unroll
-            for (int p = 0; p < L; ++p) {
-              const int id = p - delta;
-              DigitT xv = xr[id < 0 ? 0 : id];
-              xv = id < 0 ? DigitT(0) : xv;
-#pragma unroll
-              for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
-            }
-          }
-        }
-      };
+      // ---- staged digit rows into the layouts of the multiply-accumulate loop ----
       if constexpr (INTV) {
-        // Coefficients j and d-j share d+2 terms (the middle coefficient d/2,
-        // when d+1 is odd, forms a group of its own, the last one).  Every lane
-        // of the CTA belongs to a group: each group gets Q = T / groups
-        // consecutive lanes, and the first T mod groups groups one more, so no
-        // lane idles.  The lanes of a group split its terms, walked as: the
-        // short coefficient from its first term, then the long one from its last
-        // term backwards.  At every step all lanes with the same rank q inside
-        // groups of the same size read the same X row (a broadcast) and
-        // consecutive Y rows.  Only the lane holding a group's short-to-long
-        // switch flushes there; the periodic flushes fall on the same steps in
-        // every lane, so a warp runs them together.
-        const int P = npairs;                      // pairs (j, d - j), j < d - j
-        const bool has_mid = ngroups > P;          // the middle coefficient d/2 pairs with itself
-        const int Gp = g_hi - g_lo;                // groups of this part
-        int grp = g_hi, q = 0, Q = 1;              // lanes without a group run no terms
-        if (Gp > 0) {
-          const int Qb = T / Gp;                   // lanes per group (>= 1: the plan sizes T)
-          const int extra = T - Qb * Gp;           // the first `extra` groups have Qb + 1 lanes
-          if (tid < extra * (Qb + 1)) {
-            Q = Qb + 1;
-            grp = g_lo + tid / Q;
-            q = tid - (grp - g_lo) * Q;
-          } else {
-            Q = Qb;
-            const int t2 = tid - extra * (Qb + 1);
-            grp = g_lo + extra + t2 / Q;
-            q = t2 - (grp - g_lo - extra) * Q;
-          }
+        // X rows behind their zero prefix (the Y rows and both grids are in place)
+        constexpr int V4 = RW / 4;
+        const int4* src = reinterpret_cast<const int4*>(raw);
+        for (int t = tid; t < (d + 1) * V4; t += T) {
+          const int c = t / V4, v = t - c * V4;
+          const int4 q = src[t];
+          int32_t* dst = xdig + c * XS + XOFF + 4 * v;
+          if (4 * v < L) dst[0] = q.x;
+          if (4 * v + 1 < L) dst[1] = q.y;
+          if (4 * v + 2 < L) dst[2] = q.z;
+          if (4 * v + 3 < L) dst[3] = q.w;
         }
-        int cs = 0, cl = 0, ns = 0, nl = 0, tp = 0;
-        if (grp >= g_hi) {
-          // no group: no terms
-        } else if (grp < P) {
-          cs = conv ? grp : d - grp;               // short coefficient: grp + 1 terms
-          cl = conv ? d - grp : grp;               // long coefficient: d - grp + 1 terms
-          ns = grp + 1;
-          nl = d - grp + 1;
-          tp = d + 2;
-        } else if (grp == P && has_mid) {
-          cs = cl = d / 2;
-          ns = d / 2 + 1;
-          tp = ns;
-        }
-        const int H = tp > 0 ? (tp + Q - 1) / Q : 0;
-        const int p0 = q * H;
-        const int p1 = min(p0 + H, tp);
-        int jcur = p0 < ns ? cs : cl;
-        int left = R;  // terms the accumulators take before the next flush
-        for (int pos = p0; pos < p1; ++pos) {
-          int j, i;
-          if (pos < ns) {
-            j = cs;
-            i = pos;
-          } else {
-            j = cl;
-            i = nl - 1 - (pos - ns);
-          }
-          const int ix = conv ? i : j + i;
-          const int iy = conv ? j - i : i;
-          term(ix, iy, gs[j] - gx[ix] - gy[iy]);
-          --left;
-          if (pos == ns - 1 && pos + 1 < p1) {
-            flush(cs);  // this lane leaves the short coefficient
-            jcur = cl;
-          }
-          if (left == 0) {  // the same steps in every lane (not reset by the switch)
-            flush(jcur);
-            left = R;
-          }
-        }
-        if (p1 > p0) flush(jcur);
       } else {
-        // Every thread runs the same number of consecutive terms of the
-        // concatenated term sequence; partial sums of a coefficient split between
-        // threads meet exactly in the shared exchange row.
-        const long long W = static_cast<long long>(d + 1) * (d + 2) / 2;
-        const long long g0 = W * tid / T;
-        const long long g1 = W * (tid + 1) / T;
-        const int cnt = static_cast<int>(g1 - g0);
-        int j = 0, i = 0;
-        if (cnt > 0) {
-          int lo = 0, hi = d;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            const long long st = conv ? conv_start(mid) : corr_start(mid, d);
-            if (st <= g0) lo = mid; else hi = mid - 1;
-          }
-          j = lo;
-          i = static_cast<int>(g0 - (conv ? conv_start(j) : corr_start(j, d)));
+        const int32_t* rx = raw;
+        const int32_t* ry = raw + S * RW;
+        for (int t = tid; t < (d + 1) * L; t += T) {
+          const int c = t / L, p = t - c * L;
+          xdig[c * XS + p] = static_cast<double>(rx[c * RW + p]);
+          ydig[c * YS + p] = static_cast<double>(ry[c * RW + p]);
         }
-        int nt = conv ? j + 1 : d - j + 1;
-        int gsj = cnt > 0 ? gs[j] : 0;
-        for (int s = 0; s < cnt; ++s) {
-          const int ix = conv ? i : j + i;
-          const int iy = conv ? j - i : i;
-          term(ix, iy, gsj - gx[ix] - gy[iy]);
-          ++i;
-          const bool end_coef = (i == nt);
-          if (end_coef || ((s + 1) % R == 0)) flush(j);
-          if (end_coef) {
-            ++j;
-            i = 0;
-            if (j <= d) {
-              nt = conv ? j + 1 : d - j + 1;
-              gsj = gs[j];
+      }
+      __syncthreads();
+
+      // ---- zero the exchange rows, reference grid of every output coefficient ----
+      const int rows = (d + 1) * (L + 1);
+      for (int t = tid; t < rows; t += T) exch[t] = 0ull;
+      for (int j = tid; j <= d; j += T) {
+        if (!owned(j)) continue;
+        int32_t m = 2 * GRID_ZERO;
+        if (jb.kind == JOB_CONV) {
+          for (int i = 0; i <= j; ++i) m = max(m, gx[i] + gy[j - i]);
+        } else {
+          for (int i = 0; i <= d - j; ++i) m = max(m, gx[j + i] + gy[i]);
+        }
+        gs[j] = m;
+      }
+      __syncthreads();
+
+      // ---- multiply-accumulate ----
+      {
+        const bool conv = jb.kind == JOB_CONV;
+        AccT A[L];
+  #pragma unroll
+        for (int t = 0; t < L; ++t) A[t] = 0;
+        // Add the accumulators into the exchange row of coefficient jj: A[t]
+        // belongs to word t+1 (word 0 is headroom above the grid's top digit).
+        // One flush may carry up to 2^63 per accumulator, so the values are first
+        // carried in registers: word t+1 takes the low B bits of A[t] plus the
+        // part of A[t+1] above its low B bits, word 0 the part of A[0] above B
+        // bits.  No word then takes more than about 2^(64-B) per flush, and the
+        // words stay exact however many flushes they receive.
+        auto flush = [&](int jj) {
+          unsigned long long* row = exch + jj * (L + 1);
+          long long hi_next = 0;  // part of A[t+1] above its low B bits
+  #pragma unroll
+          for (int t = L - 1; t >= 0; --t) {
+            long long v;
+            if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
+            const long long w = (v & ((1LL << B) - 1)) + hi_next;
+            hi_next = v >> B;  // arithmetic shift: v = hi * 2^B + lo
+            if (w != 0) atomicAdd(row + t + 1, static_cast<unsigned long long>(w));
+            A[t] = 0;
+          }
+          if (hi_next != 0) atomicAdd(row, static_cast<unsigned long long>(hi_next));
+        };
+        // one term x_ix * y_iy of output coefficient j, delta digits below its grid
+        auto term = [&](int ix, int iy, int delta) {
+          if constexpr (INTV) {
+            if (delta < L) {
+              // zero prefix: digit p of the shifted term is xs[p], no select
+              const int32_t* xs = xdig + ix * XS + XOFF - delta;
+              const int4* y4 = reinterpret_cast<const int4*>(ydig + iy * YS);
+              int32_t Y[YS];
+  #pragma unroll
+              for (int v = 0; v < YS / 4; ++v) {
+                const int4 t4 = y4[v];
+                Y[4 * v] = t4.x;
+                Y[4 * v + 1] = t4.y;
+                Y[4 * v + 2] = t4.z;
+                Y[4 * v + 3] = t4.w;
+              }
+  #pragma unroll
+              for (int p = 0; p < L; ++p) {
+                const int32_t xv = xs[p];
+  #pragma unroll
+                for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+              }
+            }
+          } else {
+            if (delta < L) {
+              const DigitT* yr = ydig + iy * YS;
+              const DigitT* xr = xdig + ix * XS;
+              DigitT Y[L];
+  #pragma unroll
+              for (int q = 0; q < L; ++q) Y[q] = yr[q];
+  #pragma unroll
+              for (int p = 0; p < L; ++p) {
+                const int id = p - delta;
+                DigitT xv = xr[id < 0 ? 0 : id];
+                xv = id < 0 ? DigitT(0) : xv;
+  #pragma unroll
+                for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+              }
             }
           }
+        };
+        if constexpr (INTV) {
+          // Coefficients j and d-j share d+2 terms (the middle coefficient d/2,
+          // when d+1 is odd, forms a group of its own, the last one).  Every lane
+          // of the CTA belongs to a group: each group gets Q = T / groups
+          // consecutive lanes, and the first T mod groups groups one more, so no
+          // lane idles.  The lanes of a group split its terms, walked as: the
+          // short coefficient from its first term, then the long one from its last
+          // term backwards.  At every step all lanes with the same rank q inside
+          // groups of the same size read the same X row (a broadcast) and
+          // consecutive Y rows.  Only the lane holding a group's short-to-long
+          // switch flushes there; the periodic flushes fall on the same steps in
+          // every lane, so a warp runs them together.
+          const int P = npairs;                      // pairs (j, d - j), j < d - j
+          const bool has_mid = ngroups > P;          // the middle coefficient d/2 pairs with itself
+          const int Gp = g_hi - g_lo;                // groups of this part
+          int grp = g_hi, q = 0, Q = 1;              // lanes without a group run no terms
+          if (Gp > 0) {
+            const int Qb = T / Gp;                   // lanes per group (>= 1: the plan sizes T)
+            const int extra = T - Qb * Gp;           // the first `extra` groups have Qb + 1 lanes
+            if (tid < extra * (Qb + 1)) {
+              Q = Qb + 1;
+              grp = g_lo + tid / Q;
+              q = tid - (grp - g_lo) * Q;
+            } else {
+              Q = Qb;
+              const int t2 = tid - extra * (Qb + 1);
+              grp = g_lo + extra + t2 / Q;
+              q = t2 - (grp - g_lo - extra) * Q;
+            }
+          }
+          int cs = 0, cl = 0, ns = 0, nl = 0, tp = 0;
+          if (grp >= g_hi) {
+            // no group: no terms
+          } else if (grp < P) {
+            cs = conv ? grp : d - grp;               // short coefficient: grp + 1 terms
+            cl = conv ? d - grp : grp;               // long coefficient: d - grp + 1 terms
+            ns = grp + 1;
+            nl = d - grp + 1;
+            tp = d + 2;
+          } else if (grp == P && has_mid) {
+            cs = cl = d / 2;
+            ns = d / 2 + 1;
+            tp = ns;
+          }
+          const int H = tp > 0 ? (tp + Q - 1) / Q : 0;
+          const int p0 = q * H;
+          const int p1 = min(p0 + H, tp);
+          int jcur = p0 < ns ? cs : cl;
+          int left = R;  // terms the accumulators take before the next flush
+          for (int pos = p0; pos < p1; ++pos) {
+            int j, i;
+            if (pos < ns) {
+              j = cs;
+              i = pos;
+            } else {
+              j = cl;
+              i = nl - 1 - (pos - ns);
+            }
+            const int ix = conv ? i : j + i;
+            const int iy = conv ? j - i : i;
+            term(ix, iy, gs[j] - gx[ix] - gy[iy]);
+            --left;
+            if (pos == ns - 1 && pos + 1 < p1) {
+              flush(cs);  // this lane leaves the short coefficient
+              jcur = cl;
+            }
+            if (left == 0) {  // the same steps in every lane (not reset by the switch)
+              flush(jcur);
+              left = R;
+            }
+          }
+          if (p1 > p0) flush(jcur);
+        } else {
+          // Every thread runs the same number of consecutive terms of the
+          // concatenated term sequence; partial sums of a coefficient split between
+          // threads meet exactly in the shared exchange row.
+          const long long W = static_cast<long long>(d + 1) * (d + 2) / 2;
+          const long long g0 = W * tid / T;
+          const long long g1 = W * (tid + 1) / T;
+          const int cnt = static_cast<int>(g1 - g0);
+          int j = 0, i = 0;
+          if (cnt > 0) {
+            int lo = 0, hi = d;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              const long long st = conv ? conv_start(mid) : corr_start(mid, d);
+              if (st <= g0) lo = mid; else hi = mid - 1;
+            }
+            j = lo;
+            i = static_cast<int>(g0 - (conv ? conv_start(j) : corr_start(j, d)));
+          }
+          int nt = conv ? j + 1 : d - j + 1;
+          int gsj = cnt > 0 ? gs[j] : 0;
+          for (int s = 0; s < cnt; ++s) {
+            const int ix = conv ? i : j + i;
+            const int iy = conv ? j - i : i;
+            term(ix, iy, gsj - gx[ix] - gy[iy]);
+            ++i;
+            const bool end_coef = (i == nt);
+            if (end_coef || ((s + 1) % R == 0)) flush(j);
+            if (end_coef) {
+              ++j;
+              i = 0;
+              if (j <= d) {
+                nt = conv ? j + 1 : d - j + 1;
+                gsj = gs[j];
+              }
+            }
+          }
+          if (i > 0) flush(j);
         }
-        if (i > 0) flush(j);
       }
-    }
-    __syncthreads();
-    if (ahead && tid == stager) {
-      claim();
-      stage(false);
-    }
+      __syncthreads();
+      if (ahead && tid == stager) {
+        claim();
+        stage(false);
+      }
 
-    // ---- one output coefficient per thread: the exact sum as L digits on its grid ----
-    for (int j = tid; j <= d; j += T) {
-      if (!owned(j)) continue;
-      const int32_t g = gs[j];
-      int32_t o[L];
-      int32_t gz = GRID_ZERO;
-      if (g < -100000) {
-#pragma unroll
-        for (int p = 0; p < L; ++p) o[p] = 0;
-      } else {
-        int64_t E[L + 1];
-#pragma unroll
-        for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
-        gz = sum_to_digits<L, B>(E, g, o);
+      // ---- one output coefficient per thread: the exact sum as L digits on its grid ----
+      for (int j = tid; j <= d; j += T) {
+        if (!owned(j)) continue;
+        const int32_t g = gs[j];
+        int32_t o[L];
+        int32_t gz = GRID_ZERO;
+        if (g < -100000) {
+  #pragma unroll
+          for (int p = 0; p < L; ++p) o[p] = 0;
+        } else {
+          int64_t E[L + 1];
+  #pragma unroll
+          for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
+          gz = sum_to_digits<L, B>(E, g, o);
+        }
+        int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j) * RW);
+  #pragma unroll
+        for (int v = 0; v < RW / 4; ++v)
+          dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
+                             4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
+        zgrid[j] = gz;
       }
-      int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j) * RW);
-#pragma unroll
-      for (int v = 0; v < RW / 4; ++v)
-        dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
-                           4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
-      zgrid[j] = gz;
     }
     __syncthreads();
     if (tid == 0) {

@@ -512,6 +512,7 @@ struct pes_plan_s {
   AddTable add, add_g;
   CopyTable pack, pack_u, unpack;
   bool with_vjp = false;
+  bool complex_series = false;
   int64_t ws_bytes = 0;
 };
 
@@ -535,7 +536,7 @@ extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx,
 
 namespace {
 pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N, int32_t n,
-                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
+                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out, bool complex_series = false);
 }  // namespace
 
 extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -550,9 +551,15 @@ extern "C" pes_status pes_plan_powers(const int32_t* supp_ptr, const int32_t* su
   return plan_impl(supp_ptr, supp_idx, supp_exp, N, n, d, k, opt, out);
 }
 
+extern "C" pes_status pes_plan_complex(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                       int32_t N, int32_t n, int32_t d, int32_t k, const pes_options* opt,
+                                       pes_plan_t* out) {
+  return plan_impl(supp_ptr, supp_idx, supp_exp, N, n, d, k, opt, out, true);
+}
+
 namespace {
 pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N, int32_t n,
-                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out) {
+                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out, bool complex_series) {
   if (!out) return fail(PES_EINVAL, "out is NULL");
   *out = nullptr;
   if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
@@ -567,8 +574,10 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
 
   std::unique_ptr<pes_plan_s> P(new (std::nothrow) pes_plan_s());
   if (!P) return fail(PES_ENOMEM, "plan");
-  P->with_vjp = o.with_vjp != 0;
+  P->with_vjp = o.with_vjp != 0 && !complex_series;  // complex plans have no VJP tables
+  P->complex_series = complex_series;
   P->prog = pes::compile(sup, d, false, P->with_vjp);
+  if (complex_series) P->prog = pes::complexify(P->prog);
   const pes::Program1& G = P->prog;
   const int32_t S = pes::series_stride(d);
   const int32_t slots = P->with_vjp ? G.n_slots_vjp : G.n_slots;
@@ -589,19 +598,44 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
     fnv_mix(P->signature, j.dep2);
   }
 
-  // pack rows: coefficients (buffer 0), inputs (buffer 1)
+  // pack rows: coefficients (buffer 0), inputs (buffer 1); complex series: the
+  // real part from the first block of the buffer, the imaginary part from the
+  // second, into slots 2s and 2s + 1
   const int64_t D1 = d + 1;
+  const int64_t cim = static_cast<int64_t>(k) * (N + 1) * D1, iim = static_cast<int64_t>(k) * n * D1;
   std::vector<pes::CopyRow> rows;
-  for (int32_t m = 0; m <= N; ++m) rows.push_back({m * D1, (N + 1) * D1, 0, 0, m, 0});
-  for (int32_t i = 0; i < n; ++i) rows.push_back({i * D1, n * D1, 1, 0, 1 + N + i, 0});
+  if (!complex_series) {
+    for (int32_t m = 0; m <= N; ++m) rows.push_back({m * D1, (N + 1) * D1, 0, 0, m, 0});
+    for (int32_t i = 0; i < n; ++i) rows.push_back({i * D1, n * D1, 1, 0, 1 + N + i, 0});
+  } else {
+    for (int32_t m = 0; m <= N; ++m) {
+      rows.push_back({m * D1, (N + 1) * D1, 0, 0, 2 * m, 0});
+      rows.push_back({cim + m * D1, (N + 1) * D1, 0, 0, 2 * m + 1, 0});
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      rows.push_back({i * D1, n * D1, 1, 0, 2 * (1 + N + i), 0});
+      rows.push_back({iim + i * D1, n * D1, 1, 0, 2 * (1 + N + i) + 1, 0});
+    }
+  }
   P->pack.n = static_cast<int32_t>(rows.size());
   s = P->ex.put(&P->pack.rows, rows);
   if (s != PES_OK) return s;
 
-  // addition: value (buffer 0) and gradients (buffer 1)
+  // addition: value (buffer 0) and gradients (buffer 1); complex series: output
+  // 2o the real part (first block), 2o + 1 the imaginary part (second block)
   std::vector<pes::AddOut> outs;
-  outs.push_back({0, D1, 0, 0, G.add_ptr[0], G.add_ptr[1]});
-  for (int32_t i = 0; i < n; ++i) outs.push_back({i * D1, n * D1, 1, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+  if (!complex_series) {
+    outs.push_back({0, D1, 0, 0, G.add_ptr[0], G.add_ptr[1]});
+    for (int32_t i = 0; i < n; ++i) outs.push_back({i * D1, n * D1, 1, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+  } else {
+    const int64_t vim = static_cast<int64_t>(k) * D1;
+    outs.push_back({0, D1, 0, 0, G.add_ptr[0], G.add_ptr[1]});
+    outs.push_back({vim, D1, 0, 0, G.add_ptr[1], G.add_ptr[2]});
+    for (int32_t i = 0; i < n; ++i) {
+      outs.push_back({i * D1, n * D1, 1, 0, G.add_ptr[2 + 2 * i], G.add_ptr[3 + 2 * i]});
+      outs.push_back({iim + i * D1, n * D1, 1, 0, G.add_ptr[3 + 2 * i], G.add_ptr[4 + 2 * i]});
+    }
+  }
   s = P->ex.make_add(P->add, outs, G.add_src, insts, G.add_mult);
   if (s != PES_OK) return s;
 
@@ -681,6 +715,7 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
 extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double* input, const double* upstream,
                               double* grad_input, double* grad_coeff, int32_t reuse_forward, void* stream) {
   if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  if (plan->complex_series) return fail(PES_EINVAL, "no VJP for complex series");
   if (!plan->with_vjp) return fail(PES_EINVAL, "plan was built without with_vjp");
   if (!upstream || !grad_input || !grad_coeff || (!reuse_forward && (!coeff || !input)))
     return fail(PES_EINVAL, "NULL buffer");
@@ -750,6 +785,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->arith = plan->ex.arith;
   info->staging = plan->ex.depth;
   info->split = plan->ex.split;
+  info->complex_series = plan->complex_series ? 1 : 0;
   return PES_OK;
 }
 

@@ -25,7 +25,8 @@ STATUS = {0: "PES_OK", 1: "PES_EINVAL", 2: "PES_EUNSUPPORTED_K", 3: "PES_ENOMEM"
 ARITH = {"auto": -1, "fp64": 0, "int": 1}
 
 # every symbol that include/pes.h declares
-EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", "pes_plan_destroy", "pes_eval_grad",
+EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", "pes_plan_complex", "pes_plan_destroy",
+           "pes_eval_grad",
            "pes_vjp", "pes_jobc_stats_powers", "pes_jobc_jobs_powers", "pes_jobc_add_terms_powers",
            "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
@@ -52,7 +53,7 @@ class PlanInfo(ctypes.Structure):
                 ("vjp_conv_jobs", ctypes.c_int64), ("vjp_corr_jobs", ctypes.c_int64),
                 ("digits", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("arith", ctypes.c_int32), ("staging", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("complex_series", ctypes.c_int32)]
 
     def as_dict(self):
         d = {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "pad"}
@@ -86,6 +87,8 @@ def lib():
                 "pes_plan_ex": (i32, [ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
                 "pes_plan_powers": (i32, [ip32, ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options),
                                           ctypes.POINTER(vp)]),
+                "pes_plan_complex": (i32, [ip32, ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options),
+                                           ctypes.POINTER(vp)]),
                 "pes_plan_destroy": (None, [vp]),
                 "pes_eval_grad": (i32, [vp, vp, vp, vp, vp, vp]),
                 "pes_vjp": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
@@ -196,16 +199,24 @@ class Plan:
     """pes_plan: job tables and workspace of one polynomial on the current device.
 
     exponents: None (every variable with exponent 1) or, per monomial, one
-    positive exponent per variable of its support (pes_plan_powers)."""
+    positive exponent per variable of its support (pes_plan_powers).
+    complex_series: complex coefficients and inputs (pes_plan_complex); every
+    buffer then has a leading axis of 2 (real part, imaginary part)."""
 
-    def __init__(self, supports, n, d, k, exponents=None, **opts):
+    def __init__(self, supports, n, d, k, exponents=None, complex_series=False, **opts):
         self.supports = [list(s) for s in supports]
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.N = len(self.supports)
+        self.complex_series = bool(complex_series)
         ptr, idx = csr(self.supports)
         o = make_options(**opts)
         h = ctypes.c_void_p()
-        if exponents is None:
+        if self.complex_series:
+            ex = exponent_array(exponents, self.supports) if exponents is not None else None
+            _check(lib().pes_plan_complex(_ip32(ptr), _ip32(idx), _ip32(ex) if ex is not None else None, self.N,
+                                          self.n, self.d, self.k, ctypes.byref(o), ctypes.byref(h)),
+                   "pes_plan_complex")
+        elif exponents is None:
             _check(lib().pes_plan_ex(_ip32(ptr), _ip32(idx), self.N, self.n, self.d, self.k, ctypes.byref(o),
                                      ctypes.byref(h)), "pes_plan")
         else:
@@ -227,7 +238,10 @@ class Plan:
 
     def shapes(self):
         k, N, n, S = self.k, self.N, self.n, self.d + 1
-        return {"coeff": (k, N + 1, S), "input": (k, n, S), "value": (k, S), "grad": (k, n, S)}
+        sh = {"coeff": (k, N + 1, S), "input": (k, n, S), "value": (k, S), "grad": (k, n, S)}
+        if getattr(self, "complex_series", False):
+            sh = {key: (2,) + v for key, v in sh.items()}
+        return sh
 
     def eval_grad(self, coeff, inputs, value=None, grad=None, stream=None):
         import torch
