@@ -74,6 +74,8 @@ def parse_args(argv=None):
                          "--workload batch; 0 skips it in the default run)")
     ap.add_argument("--batch-k", type=int, default=2)
     ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--no-complex", action="store_true",
+                    help="skip the measurement of the workload with complex series")
     ap.add_argument("--no-powers", action="store_true",
                     help="skip the measurement of the workload with powers (monomials with exponents 1-3)")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
@@ -485,6 +487,8 @@ def ours_arm(args, world, rank, local):
         out["autograd"] = autograd_measure(args, dev, flush)
     if args.workload == "p2" and not args.no_powers:
         out["powers"] = powers_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
+    if args.workload == "p2" and not args.no_complex:
+        out["complex"] = complex_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     count = 256 if args.batch_count is None else args.batch_count
     if count > 0:
         out["batched"] = batch_measure(args, dev, count)
@@ -575,6 +579,51 @@ def powers_measure(args, dev, flush, peak):
             "conv_jobs": info["conv_jobs"], "power_and_factor_jobs": info["conv_jobs"] - plain,
             "roofline_frac": (macs / (cms * 1e-3) / 1e12) / peak if peak else None,
             "kernel_ms": cms, "threads_per_cta": info["threads"], "arith": info["arith_name"]}
+
+
+def complex_measure(args, dev, flush, peak):
+    """Complex coefficient and input series: the p2-like workload (n=128, 128
+    monomials of 64 variables, d=152, k=10) with random complex series.  Every
+    complex product is 4 real convolutions and 2 series additions (the paper's
+    count for a complex multiplication: 4 multiplications and 2 additions);
+    ms per eval+grad step with CUDA events and an L2 flush between steps."""
+    import numpy as np
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    prob = synth.config1(seed=args.seed)
+    rng = np.random.default_rng(args.seed + 41)
+    coeff = np.stack([prob.coeff, synth.random_md(rng, prob.k, prob.coeff.shape[1:])])
+    inputs = np.stack([prob.inputs, synth.random_md(rng, prob.k, prob.inputs.shape[1:])])
+    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, complex_series=True, with_vjp=False, profile=True,
+                    autotune=not args.no_autotune)
+    C = torch.from_numpy(coeff).to(dev)
+    Z = torch.from_numpy(inputs).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    times, conv = [], []
+    for it in range(max(args.warmup, 3) + args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval_grad(C, Z)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= max(args.warmup, 3):
+            times.append(e0.elapsed_time(e1))
+            conv.append(plan.last_timing()["conv_ms"])
+    plan.check()
+    info = plan.info()
+    ms, cms = statistics.mean(times), statistics.mean(conv)
+    jobs = info["conv_jobs"]               # 6 per complex product: 4 convolutions, 2 additions
+    products, series_adds = jobs * 4 // 6, jobs * 2 // 6
+    cm, ca = md_costs(prob.k)
+    ops = dp_equiv_ops(products, info["add_jobs"], prob.d, prob.k) + series_adds * (prob.d + 1) * ca
+    macs = digit_fma_flops(products, prob.d, info["digits"]) / 2
+    return {"workload": "p2-like, n=128, 128 monomials of 64 variables, complex series, d=152, k=10",
+            "ms_per_step": ms, "value": ops / (ms * 1e-3) / 1e12, "unit": UNIT,
+            "real_convolutions": products, "series_additions": series_adds,
+            "roofline_frac": (macs / (cms * 1e-3) / 1e12) / peak if peak else None,
+            "kernel_ms": cms, "threads_per_cta": info["threads"], "arith": info["arith_name"],
+            "workspace_bytes": info["workspace_bytes"]}
 
 
 def batch_measure(args, dev, count, small=False):
