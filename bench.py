@@ -76,6 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--no-complex", action="store_true",
                     help="skip the measurement of the workload with complex series")
+    ap.add_argument("--no-system", action="store_true",
+                    help="skip the measurement of the 64 x 64 system (values and Jacobian in one plan)")
     ap.add_argument("--no-powers", action="store_true",
                     help="skip the measurement of the workload with powers (monomials with exponents 1-3)")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
@@ -489,6 +491,8 @@ def ours_arm(args, world, rank, local):
         out["powers"] = powers_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     if args.workload == "p2" and not args.no_complex:
         out["complex"] = complex_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
+    if args.workload == "p2" and not args.no_system:
+        out["system"] = system_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     count = 256 if args.batch_count is None else args.batch_count
     if count > 0:
         out["batched"] = batch_measure(args, dev, count)
@@ -624,6 +628,67 @@ def complex_measure(args, dev, flush, peak):
             "roofline_frac": (macs / (cms * 1e-3) / 1e12) / peak if peak else None,
             "kernel_ms": cms, "threads_per_cta": info["threads"], "arith": info["arith_name"],
             "workspace_bytes": info["workspace_bytes"]}
+
+
+def system_measure(args, dev, flush, peak):
+    """A system of 64 polynomials in 64 variables, each 512 monomials of 4-16
+    variables, inputs exp(a_i t), d=152, k=10: the 64 values and the 64 x 64
+    Jacobian matrix series in one plan (pes_plan_system, one P x n matrix per
+    power of t) against one plan per polynomial (64 eval+grad calls), both
+    without autotuning; ms per step with CUDA events and an L2 flush between
+    steps; the two results compared bit for bit."""
+    import numpy as np
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    sysc = synth.config4(152, 10, seed=args.seed)
+    polys = [s_ for s_, _ in sysc.polys]
+    sysp = pes.System(polys, sysc.n, sysc.d, sysc.k, profile=True)
+    C = torch.from_numpy(np.concatenate([c for _, c in sysc.polys], axis=1)).to(dev)
+    Z = torch.from_numpy(sysc.inputs).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        out = []
+        for it in range(2 + reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if it >= 2:
+                out.append(e0.elapsed_time(e1))
+        return statistics.mean(out)
+
+    res = {}
+    res["system"] = timed(lambda: res.__setitem__("sys_out", sysp.eval_system(C, Z, "matrix")), 3)
+    conv_ms = sysp.last_timing()["conv_ms"]
+    sysp.check()
+    info = sysp.info()
+    v, J = res.pop("sys_out")
+    plans = [pes.Plan(s_, sysc.n, sysc.d, sysc.k, with_vjp=False) for s_ in polys]
+    Cs = [torch.from_numpy(c).to(dev) for _, c in sysc.polys]
+    outs = [None] * len(plans)
+
+    def separate():
+        for q, (pl, c) in enumerate(zip(plans, Cs)):
+            outs[q] = pl.eval_grad(c, Z)
+
+    res["plans"] = timed(separate, 3)
+    for pl in plans:
+        pl.check()
+    same = all(torch.equal(v[:, :, q], outs[q][0]) and torch.equal(J[:, :, q], outs[q][1].permute(0, 2, 1))
+               for q in range(len(plans)))
+    ops = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], sysc.d, sysc.k)
+    macs = digit_fma_flops(info["conv_jobs"], sysc.d, info["digits"]) / 2
+    return {"workload": "system of 64 polynomials in 64 variables, 512 monomials of 4-16 variables each, "
+                        "inputs exp(a_i t), d=152, k=10: values + 64 x 64 Jacobian series",
+            "ms_per_step": res["system"], "value": ops / (res["system"] * 1e-3) / 1e12, "unit": UNIT,
+            "plans_ms_per_step": res["plans"], "plans_over_system": res["plans"] / res["system"],
+            "conv_jobs": info["conv_jobs"], "jacobian_layout": "matrix [k][d+1][P][n]",
+            "roofline_frac": (macs / (conv_ms * 1e-3) / 1e12) / peak if peak else None,
+            "kernel_ms": conv_ms, "workspace_bytes": info["workspace_bytes"],
+            "system_equals_plans_bitwise": bool(same), "launches_system": 4, "launches_plans": 4 * len(plans)}
 
 
 def batch_measure(args, dev, count, small=False):
@@ -790,9 +855,6 @@ def sweep_arm(args, world, rank):
                       "max_backward_over_forward": max(r["backward_over_forward"] or 0 for r in rows)}), flush=True)
     return 0
 
-
-def main():
-    args = parse_args()
 
 def main():
     args = parse_args()

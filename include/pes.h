@@ -127,6 +127,22 @@ pes_status pes_plan_powers(const int32_t* supp_ptr, const int32_t* supp_idx, con
  * There are no VJP tables: pes_vjp returns PES_EINVAL on a complex plan. */
 pes_status pes_plan_complex(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
                             int32_t n, int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
+
+/* A system of P polynomials in the same n variables, and its Jacobian matrix
+ * (the value and Jacobian series that a Newton step on power series needs;
+ * every entry is the gradient of Sec. 4 of one polynomial).  Polynomial p owns
+ * the monomials poly_ptr[p] .. poly_ptr[p+1]-1 of supp_ptr / supp_idx /
+ * supp_exp (exactly as in pes_plan_powers, N = poly_ptr[P] monomials in all,
+ * supp_exp may be NULL) plus its own constant series.  All polynomials share
+ * the input series and one job table; the products of every monomial are the
+ * ones its own plan would compute, so every output is bit-identical to a plan
+ * of that polynomial alone.  Evaluate with pes_eval_system (pes_eval_grad is
+ * pes_eval_system with PES_LAYOUT_SERIES).  There are no VJP tables.
+ *   P >= 1, poly_ptr: P+1 non-decreasing entries, poly_ptr[0] == 0.
+ * Errors as pes_plan_ex, and PES_EINVAL for a bad poly_ptr. */
+pes_status pes_plan_system(int32_t P, const int32_t* poly_ptr, const int32_t* supp_ptr, const int32_t* supp_idx,
+                           const int32_t* supp_exp, int32_t n, int32_t d, int32_t k, const pes_options* opt,
+                           pes_plan_t* out);
 void pes_plan_destroy(pes_plan_t plan);
 
 /* Value and gradient of the polynomial at the input series (Sec. 4 and 5).
@@ -137,6 +153,24 @@ void pes_plan_destroy(pes_plan_t plan);
  * Asynchronous on `stream`. */
 pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const double* input, double* value, double* grad,
                          void* stream);
+
+/* Output layouts of pes_eval_system. */
+#define PES_LAYOUT_SERIES 0 /* value [k][P][d+1], jac [k][P][n][d+1]: one series per entry */
+#define PES_LAYOUT_MATRIX 1 /* value [k][d+1][P], jac [k][d+1][P][n]: one row-major P x n matrix
+                               (and P-vector) per power of t and limb, as a linearised
+                               Newton step J_0 dx_j = r_j - sum_{i>=1} J_i dx_{j-i} reads them */
+
+/* Values and Jacobian of a system plan (pes_plan_system) at the input series.
+ *   coeff: device, [k][N+P][d+1]: for each polynomial p in order its constant
+ *          series, then the coefficient series of its monomials (the constant
+ *          of p at index poly_ptr[p] + p, monomial m of p at index m + p + 1);
+ *   input: device, [k][n][d+1];
+ *   value, jac: device, written in the chosen layout; jac entry (p, i) is
+ *          d p / d x_i.
+ * Asynchronous on `stream`.  PES_EINVAL for a plan that is not a system or an
+ * unknown layout. */
+pes_status pes_eval_system(pes_plan_t plan, const double* coeff, const double* input, double* value, double* jac,
+                           int32_t layout, void* stream);
 
 /* Vector-Jacobian product of the value series with an upstream series u:
  * for L = sum_j u_j v_j (v the value series),
@@ -193,6 +227,7 @@ typedef struct {
   int32_t staging;         /* staging depth in use (1 or 2) */
   int32_t split;           /* parts per convolution job in use */
   int32_t complex_series;  /* 1 for a plan of pes_plan_complex */
+  int32_t system_P;        /* polynomials of a plan of pes_plan_system, else 0 */
 } pes_plan_info;
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);

@@ -207,26 +207,31 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   for (int32_t L = 1; L <= max_layer; ++L) P.layer_ptr[static_cast<size_t>(L)] += P.layer_ptr[static_cast<size_t>(L) - 1];
 
   // ---- addition stage: value and gradient contributions, monomial order ----
-  // (slot, integer factor): the factor of a partial is the variable's exponent
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> contrib(static_cast<size_t>(n) + 1);
-  contrib[0].push_back({0, 1});  // a_0
+  // every monomial's terms (output, slot, integer factor): the factor of a
+  // partial is the variable's exponent
+  P.mono_terms.assign(static_cast<size_t>(N), {});
   for (int32_t m = 0; m < N; ++m) {
     const MonoSlots& ms = P.mono[static_cast<size_t>(m)];
     const int32_t* v = s.idx.data() + s.ptr[m];
     const int32_t nk = ms.nk, t0 = s.ptr[m];
     auto e = [&](int32_t j) { return s.exponent(t0 + j); };
-    contrib[0].push_back({ms.f0 + nk - 1, 1});
+    auto& tm = P.mono_terms[static_cast<size_t>(m)];
+    tm.push_back({0, ms.f0 + nk - 1, 1});
     if (nk == 1) {
-      contrib[1 + static_cast<size_t>(v[0])].push_back({acoef[static_cast<size_t>(m)], e(0)});
+      tm.push_back({1 + v[0], acoef[static_cast<size_t>(m)], e(0)});
     } else if (nk == 2) {
-      contrib[1 + static_cast<size_t>(v[0])].push_back({ms.b0, e(0)});  // b_1 = z_{i_2} a
-      contrib[1 + static_cast<size_t>(v[1])].push_back({ms.f0, e(1)});  // f_1 = a z_{i_1}
+      tm.push_back({1 + v[0], ms.b0, e(0)});  // b_1 = z_{i_2} a
+      tm.push_back({1 + v[1], ms.f0, e(1)});  // f_1 = a z_{i_1}
     } else {
-      contrib[1 + static_cast<size_t>(v[0])].push_back({ms.bA, e(0)});
-      for (int32_t j = 1; j <= nk - 2; ++j) contrib[1 + static_cast<size_t>(v[j])].push_back({ms.c0 + j - 1, e(j)});
-      contrib[1 + static_cast<size_t>(v[nk - 1])].push_back({ms.f0 + nk - 2, e(nk - 1)});
+      tm.push_back({1 + v[0], ms.bA, e(0)});
+      for (int32_t j = 1; j <= nk - 2; ++j) tm.push_back({1 + v[j], ms.c0 + j - 1, e(j)});
+      tm.push_back({1 + v[nk - 1], ms.f0 + nk - 2, e(nk - 1)});
     }
   }
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> contrib(static_cast<size_t>(n) + 1);
+  contrib[0].push_back({0, 1});  // a_0
+  for (int32_t m = 0; m < N; ++m)
+    for (const auto& t : P.mono_terms[static_cast<size_t>(m)]) contrib[static_cast<size_t>(t[0])].push_back({t[1], t[2]});
   P.add_ptr.assign(static_cast<size_t>(n) + 2, 0);
   for (size_t o = 0; o < contrib.size(); ++o) P.add_ptr[o + 1] = P.add_ptr[o] + static_cast<int32_t>(contrib[o].size());
   P.add_src.reserve(static_cast<size_t>(P.add_ptr.back()));
@@ -287,6 +292,34 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   for (int32_t i = 0; i < n; ++i)
     V.jobs.push_back(ConvJob{P.slot_u, P.slot_g0 + i, P.slot_r0 + N + i, -1, -1, 0, JOB_CORR, 1});
   P.vjp_jobs = V.jobs;
+  return P;
+}
+
+Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr, int32_t d) {
+  Program1 P = compile(s, d, false, false);
+  const int32_t np = static_cast<int32_t>(poly_ptr.size()) - 1, n = s.n;
+  P.system_P = np;
+  P.const0 = P.n_slots;
+  P.n_slots += np;
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> contrib(static_cast<size_t>(np) * (1 + n));
+  for (int32_t p = 0; p < np; ++p) {
+    contrib[static_cast<size_t>(p)].push_back({P.const0 + p, 1});
+    for (int32_t m = poly_ptr[static_cast<size_t>(p)]; m < poly_ptr[static_cast<size_t>(p) + 1]; ++m)
+      for (const auto& t : P.mono_terms[static_cast<size_t>(m)]) {
+        const size_t o = t[0] == 0 ? static_cast<size_t>(p) : static_cast<size_t>(np + p * n + t[0] - 1);
+        contrib[o].push_back({t[1], t[2]});
+      }
+  }
+  P.add_ptr.assign(contrib.size() + 1, 0);
+  P.add_src.clear();
+  P.add_mult.clear();
+  for (size_t o = 0; o < contrib.size(); ++o) {
+    for (const auto& sm : contrib[o]) {
+      P.add_src.push_back(sm.first);
+      P.add_mult.push_back(sm.second);
+    }
+    P.add_ptr[o + 1] = static_cast<int32_t>(P.add_src.size());
+  }
   return P;
 }
 

@@ -7,6 +7,7 @@
 // one polynomial or a batch of them: a batch is the concatenation of the
 // instances' tables, each instance with its own workspace region and degree.
 #pragma once
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -50,6 +51,7 @@ struct AddOut {
   int32_t dst_sel;
   int32_t inst;
   int32_t cbeg, cend;
+  int64_t dst_jstride = 1;  // distance between coefficients j and j+1 in the destination
 };
 
 // One series copy between a caller buffer and the workspace.  For a pack (caller
@@ -104,6 +106,11 @@ struct Program1 {
   std::vector<int32_t> add_ptr;        // n+2 entries
   std::vector<int32_t> add_src;        // contributing slots
   std::vector<int32_t> add_mult;       // integer factor of every contribution (the exponent of the variable)
+  // per monomial: its terms of the addition stage, (output, slot, factor) with
+  // output 0 the value and 1 + i the partial for x_i
+  std::vector<std::vector<std::array<int32_t, 3>>> mono_terms;
+  // systems (compile_system): P polynomials, constant term of polynomial p in slot const0 + p
+  int32_t system_P = 0, const0 = -1;
   // monomials with powers (Sec. 3): series powers z_v^q, common factors and the
   // coefficients a'_m = a_m * prod z_v^(e_v - 1) that the reverse mode uses
   bool has_powers = false;
@@ -123,6 +130,14 @@ struct Program1 {
 // array of Eq. (eqcountnum) (b_{k,nk-2} updated in place, no VJP extras); it is
 // used for the offset/count checks against the paper only.
 Program1 compile(const Supports& s, int32_t d, bool paper_layout = false, bool with_vjp = false);
+
+// A system of P polynomials in the same n variables (Newton's method on series
+// evaluates one): monomials poly_ptr[p] .. poly_ptr[p+1]-1 of s belong to
+// polynomial p.  The products are those of compile(s, d); the addition stage
+// has P value outputs (the constant term of polynomial p in slot const0 + p,
+// then its monomials) followed by the P x n Jacobian entries, output
+// P + p * n + i = d p_p / d x_i.  No VJP tables.
+Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr, int32_t d);
 
 // The same polynomial over complex series: every slot s of the real program
 // becomes the pair (2s, 2s + 1) (real, imaginary part), every product

@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
     slot[gofs] = gz;
     return;
   }
-  double* dst = a.dst[ao.dst_sel] + ao.dst_off + j;
+  double* dst = a.dst[ao.dst_sel] + ao.dst_off + j * ao.dst_jstride;
   if (gmax < -100000) {
 #pragma unroll
     for (int l = 0; l < K; ++l) dst[l * ao.dst_lstride] = 0.0;

@@ -513,6 +513,7 @@ struct pes_plan_s {
   CopyTable pack, pack_u, unpack;
   bool with_vjp = false;
   bool complex_series = false;
+  AddTable add_mat;  // systems: values and Jacobian with one P x n matrix per power of t
   int64_t ws_bytes = 0;
 };
 
@@ -536,7 +537,8 @@ extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx,
 
 namespace {
 pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N, int32_t n,
-                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out, bool complex_series = false);
+                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out, bool complex_series = false,
+                     const std::vector<int32_t>* poly_ptr = nullptr);
 }  // namespace
 
 extern "C" pes_status pes_plan_ex(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -557,9 +559,21 @@ extern "C" pes_status pes_plan_complex(const int32_t* supp_ptr, const int32_t* s
   return plan_impl(supp_ptr, supp_idx, supp_exp, N, n, d, k, opt, out, true);
 }
 
+extern "C" pes_status pes_plan_system(int32_t P, const int32_t* poly_ptr, const int32_t* supp_ptr,
+                                      const int32_t* supp_idx, const int32_t* supp_exp, int32_t n, int32_t d,
+                                      int32_t k, const pes_options* opt, pes_plan_t* out) {
+  if (P < 1 || !poly_ptr) return fail(PES_EINVAL, "a system needs P >= 1 polynomials and poly_ptr");
+  if (poly_ptr[0] != 0) return fail(PES_EINVAL, "poly_ptr[0] must be 0");
+  for (int32_t p = 0; p < P; ++p)
+    if (poly_ptr[p + 1] < poly_ptr[p]) return fail(PES_EINVAL, "poly_ptr must not decrease");
+  std::vector<int32_t> pp(poly_ptr, poly_ptr + P + 1);
+  return plan_impl(supp_ptr, supp_idx, supp_exp, poly_ptr[P], n, d, k, opt, out, false, &pp);
+}
+
 namespace {
 pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N, int32_t n,
-                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out, bool complex_series) {
+                     int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out, bool complex_series,
+                     const std::vector<int32_t>* poly_ptr) {
   if (!out) return fail(PES_EINVAL, "out is NULL");
   *out = nullptr;
   if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
@@ -574,10 +588,15 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
 
   std::unique_ptr<pes_plan_s> P(new (std::nothrow) pes_plan_s());
   if (!P) return fail(PES_ENOMEM, "plan");
-  P->with_vjp = o.with_vjp != 0 && !complex_series;  // complex plans have no VJP tables
+  // complex plans and systems have no VJP tables
+  P->with_vjp = o.with_vjp != 0 && !complex_series && poly_ptr == nullptr;
   P->complex_series = complex_series;
-  P->prog = pes::compile(sup, d, false, P->with_vjp);
-  if (complex_series) P->prog = pes::complexify(P->prog);
+  if (poly_ptr != nullptr) {
+    P->prog = pes::compile_system(sup, *poly_ptr, d);
+  } else {
+    P->prog = pes::compile(sup, d, false, P->with_vjp);
+    if (complex_series) P->prog = pes::complexify(P->prog);
+  }
   const pes::Program1& G = P->prog;
   const int32_t S = pes::series_stride(d);
   const int32_t slots = P->with_vjp ? G.n_slots_vjp : G.n_slots;
@@ -604,7 +623,18 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
   const int64_t D1 = d + 1;
   const int64_t cim = static_cast<int64_t>(k) * (N + 1) * D1, iim = static_cast<int64_t>(k) * n * D1;
   std::vector<pes::CopyRow> rows;
-  if (!complex_series) {
+  const int32_t np = G.system_P;
+  if (np > 0) {
+    // system: coefficient series of polynomial p at (its constant, its monomials),
+    // consecutive: constant at poly_ptr[p] + p, monomial m at m + p + 1
+    const int64_t cl = static_cast<int64_t>(N + np) * D1;
+    for (int32_t p = 0; p < np; ++p) {
+      const int32_t m0 = (*poly_ptr)[static_cast<size_t>(p)], m1 = (*poly_ptr)[static_cast<size_t>(p) + 1];
+      rows.push_back({static_cast<int64_t>(m0 + p) * D1, cl, 0, 0, G.const0 + p, 0});
+      for (int32_t m = m0; m < m1; ++m) rows.push_back({static_cast<int64_t>(m + p + 1) * D1, cl, 0, 0, m + 1, 0});
+    }
+    for (int32_t i = 0; i < n; ++i) rows.push_back({i * D1, n * D1, 1, 0, 1 + N + i, 0});
+  } else if (!complex_series) {
     for (int32_t m = 0; m <= N; ++m) rows.push_back({m * D1, (N + 1) * D1, 0, 0, m, 0});
     for (int32_t i = 0; i < n; ++i) rows.push_back({i * D1, n * D1, 1, 0, 1 + N + i, 0});
   } else {
@@ -624,7 +654,26 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
   // addition: value (buffer 0) and gradients (buffer 1); complex series: output
   // 2o the real part (first block), 2o + 1 the imaginary part (second block)
   std::vector<pes::AddOut> outs;
-  if (!complex_series) {
+  if (np > 0) {
+    // system: values [k][P][d+1] (buffer 0), Jacobian [k][P][n][d+1] (buffer 1);
+    // and the same sums into one P-vector / P x n matrix per power of t
+    // ([k][d+1][P], [k][d+1][P][n]) for pes_eval_system's matrix layout
+    std::vector<pes::AddOut> mat;
+    for (int32_t p = 0; p < np; ++p) {
+      outs.push_back({p * D1, np * D1, 0, 0, G.add_ptr[static_cast<size_t>(p)], G.add_ptr[static_cast<size_t>(p) + 1]});
+      mat.push_back({p, D1 * np, 0, 0, G.add_ptr[static_cast<size_t>(p)], G.add_ptr[static_cast<size_t>(p) + 1], np});
+    }
+    for (int32_t p = 0; p < np; ++p)
+      for (int32_t i = 0; i < n; ++i) {
+        const size_t o = static_cast<size_t>(np + p * n + i);
+        outs.push_back({static_cast<int64_t>(p * n + i) * D1, static_cast<int64_t>(np) * n * D1, 1, 0,
+                        G.add_ptr[o], G.add_ptr[o + 1]});
+        mat.push_back({static_cast<int64_t>(p) * n + i, D1 * np * n, 1, 0, G.add_ptr[o], G.add_ptr[o + 1],
+                       static_cast<int64_t>(np) * n});
+      }
+    s = P->ex.make_add(P->add_mat, mat, G.add_src, insts, G.add_mult);
+    if (s != PES_OK) return s;
+  } else if (!complex_series) {
     outs.push_back({0, D1, 0, 0, G.add_ptr[0], G.add_ptr[1]});
     for (int32_t i = 0; i < n; ++i) outs.push_back({i * D1, n * D1, 1, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
   } else {
@@ -712,10 +761,46 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
   return PES_OK;
 }
 
+extern "C" pes_status pes_eval_system(pes_plan_t plan, const double* coeff, const double* input, double* value,
+                                      double* jac, int32_t layout, void* stream) {
+  if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  if (plan->prog.system_P == 0) return fail(PES_EINVAL, "plan is not a system (pes_plan_system)");
+  if (layout != PES_LAYOUT_SERIES && layout != PES_LAYOUT_MATRIX) return fail(PES_EINVAL, "unknown layout");
+  if (layout == PES_LAYOUT_SERIES) return pes_eval_grad(plan, coeff, input, value, jac, stream);
+  if (!coeff || !input || !value || !jac) return fail(PES_EINVAL, "NULL buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Exec& E = plan->ex;
+  if (plan->autotune && !plan->tuned) {
+    // tune on the series layout; both layouts share the job list
+    plan->tuned = true;
+    auto run = [&](cudaStream_t s2) -> pes_status {
+      PES_CUDA(pes::launch_prologue(E.ctrl, s2));
+      PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, s2));
+      PES_CUDA(E.run_dag(plan->fwd, 0, s2));
+      PES_CUDA(E.run_add(plan->add_mat, value, jac, s2));
+      return PES_OK;
+    };
+    pes_status ts = tune_launch(E, plan->fwd, tune_key(E, plan->fwd.n, plan->signature), run, st);
+    if (ts != PES_OK) return ts;
+  }
+  PES_CUDA(E.mark(0, st));
+  PES_CUDA(pes::launch_prologue(E.ctrl, st));
+  PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
+  PES_CUDA(E.mark(1, st));
+  PES_CUDA(E.run_dag(plan->fwd, 0, st));
+  PES_CUDA(E.mark(2, st));
+  PES_CUDA(E.run_add(plan->add_mat, value, jac, st));
+  PES_CUDA(E.mark(3, st));
+  PES_CUDA(E.mark(4, st));
+  E.last_launches = 4;
+  return PES_OK;
+}
+
 extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double* input, const double* upstream,
                               double* grad_input, double* grad_coeff, int32_t reuse_forward, void* stream) {
   if (!plan) return fail(PES_EINVAL, "plan is NULL");
   if (plan->complex_series) return fail(PES_EINVAL, "no VJP for complex series");
+  if (plan->prog.system_P > 0) return fail(PES_EINVAL, "no VJP for systems");
   if (!plan->with_vjp) return fail(PES_EINVAL, "plan was built without with_vjp");
   if (!upstream || !grad_input || !grad_coeff || (!reuse_forward && (!coeff || !input)))
     return fail(PES_EINVAL, "NULL buffer");
@@ -786,6 +871,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->staging = plan->ex.depth;
   info->split = plan->ex.split;
   info->complex_series = plan->complex_series ? 1 : 0;
+  info->system_P = plan->prog.system_P;
   return PES_OK;
 }
 

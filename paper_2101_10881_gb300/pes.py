@@ -26,7 +26,7 @@ ARITH = {"auto": -1, "fp64": 0, "int": 1}
 
 # every symbol that include/pes.h declares
 EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", "pes_plan_complex", "pes_plan_destroy",
-           "pes_eval_grad",
+           "pes_eval_grad", "pes_plan_system", "pes_eval_system",
            "pes_vjp", "pes_jobc_stats_powers", "pes_jobc_jobs_powers", "pes_jobc_add_terms_powers",
            "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
@@ -53,7 +53,7 @@ class PlanInfo(ctypes.Structure):
                 ("vjp_conv_jobs", ctypes.c_int64), ("vjp_corr_jobs", ctypes.c_int64),
                 ("digits", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("arith", ctypes.c_int32), ("staging", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("complex_series", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("complex_series", ctypes.c_int32), ("system_P", ctypes.c_int32)]
 
     def as_dict(self):
         d = {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "pad"}
@@ -89,6 +89,9 @@ def lib():
                                           ctypes.POINTER(vp)]),
                 "pes_plan_complex": (i32, [ip32, ip32, ip32, i32, i32, i32, i32, ctypes.POINTER(Options),
                                            ctypes.POINTER(vp)]),
+                "pes_plan_system": (i32, [i32, ip32, ip32, ip32, ip32, i32, i32, i32, ctypes.POINTER(Options),
+                                          ctypes.POINTER(vp)]),
+                "pes_eval_system": (i32, [vp, vp, vp, vp, vp, i32, vp]),
                 "pes_plan_destroy": (None, [vp]),
                 "pes_eval_grad": (i32, [vp, vp, vp, vp, vp, vp]),
                 "pes_vjp": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
@@ -288,6 +291,74 @@ class Plan:
         pi = PlanInfo()
         _check(lib().pes_get_plan_info(self._h, ctypes.byref(pi)), "pes_get_plan_info")
         return pi.as_dict()
+
+
+LAYOUTS = {"series": 0, "matrix": 1}
+
+
+class System(Plan):
+    """pes_plan_system: P polynomials in the same n variables, their values and
+    their Jacobian matrix at the input series in one job table.
+
+    polys: list of P polynomials, each a list of supports (variable-index
+    lists); exponents: None or, per polynomial, per monomial, one positive
+    exponent per variable.  The coefficient buffer is [k][N+P][d+1]: each
+    polynomial's constant series, then its monomials' coefficient series."""
+
+    def __init__(self, polys, n, d, k, exponents=None, **opts):
+        self.polys = [[list(m) for m in p_] for p_ in polys]
+        self.P = len(self.polys)
+        self.supports = [m for p_ in self.polys for m in p_]
+        self.n, self.d, self.k = int(n), int(d), int(k)
+        self.N = len(self.supports)
+        self.complex_series = False
+        self.poly_ptr = np.zeros(self.P + 1, dtype=np.int32)
+        self.poly_ptr[1:] = np.cumsum([len(p_) for p_ in self.polys])
+        ptr, idx = csr(self.supports)
+        ex = None
+        if exponents is not None:
+            ex = exponent_array([e for pe in exponents for e in pe], self.supports)
+        o = make_options(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().pes_plan_system(self.P, _ip32(self.poly_ptr), _ip32(ptr), _ip32(idx),
+                                     _ip32(ex) if ex is not None and ex.size else None, self.n, self.d, self.k,
+                                     ctypes.byref(o), ctypes.byref(h)), "pes_plan_system")
+        self._h = h
+        self.generation = 0
+
+    def coeff_index(self, p, m=None):
+        """Row of the coefficient buffer: polynomial p's constant (m None) or
+        its monomial m (0-based within p)."""
+        base = int(self.poly_ptr[p]) + p
+        return base if m is None else base + 1 + m
+
+    def shapes(self, layout="series"):
+        k, N, n, P, S = self.k, self.N, self.n, self.P, self.d + 1
+        sh = {"coeff": (k, N + P, S), "input": (k, n, S)}
+        if layout == "series":
+            sh.update(value=(k, P, S), jac=(k, P, n, S))
+        else:
+            sh.update(value=(k, S, P), jac=(k, S, P, n))
+        return sh
+
+    def eval_system(self, coeff, inputs, layout="series", value=None, jac=None, stream=None):
+        import torch
+        sh = self.shapes(layout)
+        if value is None:
+            value = torch.empty(sh["value"], dtype=torch.float64, device=coeff.device)
+        if jac is None:
+            jac = torch.empty(sh["jac"], dtype=torch.float64, device=coeff.device)
+        _check(lib().pes_eval_system(self._h, _ptr(coeff, sh["coeff"], "coeff"), _ptr(inputs, sh["input"], "input"),
+                                     _ptr(value, sh["value"], "value"), _ptr(jac, sh["jac"], "jac"),
+                                     LAYOUTS[layout], _stream(stream)), "pes_eval_system")
+        self.generation += 1
+        return value, jac
+
+    def eval_grad(self, coeff, inputs, value=None, grad=None, stream=None):
+        return self.eval_system(coeff, inputs, "series", value, grad, stream)
+
+    def vjp(self, *a, **kw):
+        raise PesError(1, "System.vjp", "no VJP for systems")
 
 
 class Batch:

@@ -44,3 +44,21 @@ def test_md_costs():
         assert m >= a >= 1
     with pytest.raises(pes.PesError):
         pes.md_costs(6)
+
+
+def test_system_arguments_checked_on_host():
+    """pes_plan_system rejects a bad poly_ptr (and bad supports) before it
+    touches the device; pes_eval_system rejects a NULL plan."""
+    import ctypes
+
+    import numpy as np
+
+    L = pes.lib()
+    ptr, idx = pes.csr([[0, 1], [1], [0, 2]])
+    h = ctypes.c_void_p()
+    for P, pp in ((0, [0]), (2, [1, 3, 3]), (2, [0, 2, 1]), (1, [0, 3])):
+        pp = np.asarray(pp, dtype=np.int32)
+        rc = L.pes_plan_system(P, pes._ip32(pp), pes._ip32(ptr), pes._ip32(idx), None, 3 if pp[-1] != 3 else 2, 4,
+                               2, None, ctypes.byref(h))
+        assert rc == 1, (P, list(pp))
+    assert L.pes_eval_system(None, None, None, None, None, 0, None) == 1

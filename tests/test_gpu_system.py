@@ -1,0 +1,177 @@
+"""Systems of polynomials and their Jacobian matrix (the value and Jacobian
+series a Newton step on power series needs) on the GPU, through the C-ABI
+(pes_plan_system / pes_eval_system), against the oracle polynomial by
+polynomial; bit-identity with one plan per polynomial; the two output layouts."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2101_10881_gb300 import pes, synth
+from paper_2101_10881_gb300.synth import KS, random_md
+from tests.exact import TOL, normwise_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    pes.build()
+    assert _t.cuda.is_available()
+    return _t
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def case(k, d, seed, n=7, P=4, N=6, powers=False):
+    rng = np.random.default_rng(seed)
+    polys, coeffs, exps = [], [], []
+    for p in range(P):
+        supp = synth.random_supports(rng, n, N + p, 1, 5)
+        polys.append(supp)
+        coeffs.append(random_md(rng, k, (len(supp) + 1, d + 1)))
+        exps.append([[int(e) for e in rng.integers(1, 4, size=len(s))] for s in supp])
+    inputs = random_md(rng, k, (n, d + 1))
+    return polys, (exps if powers else None), n, coeffs, inputs
+
+
+def check_against_oracle(torch, polys, exps, n, coeffs, inputs, k, d, **opts):
+    sysp = pes.System(polys, n, d, k, exponents=exps, **opts)
+    C = dev(torch, np.concatenate(coeffs, axis=1))
+    v, J = sysp.eval_system(C, dev(torch, inputs))
+    sysp.check()
+    v, J = v.cpu().numpy(), J.cpu().numpy()
+    for p, supp in enumerate(polys):
+        rv, rg = O.eval_grad(supp, n, coeffs[p], inputs, exponents=exps[p] if exps else None)
+        assert normwise_err(v[:, p], rv) <= TOL[k], p
+        assert normwise_err(J[:, p], rg) <= TOL[k], p
+    return sysp, C
+
+
+@pytest.mark.parametrize("arith", ["int", "fp64"])
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("d", [0, 9, 40])
+def test_system_matches_oracle(torch, k, d, arith):
+    polys, _, n, coeffs, inputs = case(k, d, 1100 + 10 * k + d)
+    check_against_oracle(torch, polys, None, n, coeffs, inputs, k, d, arith=arith)
+
+
+@pytest.mark.parametrize("k", [2, 10])
+def test_system_with_powers_matches_oracle(torch, k):
+    d = 24
+    polys, exps, n, coeffs, inputs = case(k, d, 1200 + k, powers=True)
+    check_against_oracle(torch, polys, exps, n, coeffs, inputs, k, d)
+
+
+@pytest.mark.parametrize("powers", [False, True])
+@pytest.mark.parametrize("arith", ["int", "fp64"])
+def test_system_bit_identical_to_separate_plans(torch, arith, powers):
+    """Every monomial's products are the ones its own plan computes, and every
+    output is one exact sum rounded once: the system's values and Jacobian rows
+    equal, bit for bit, those of one plan per polynomial."""
+    k, d = 4, 33
+    polys, exps, n, coeffs, inputs = case(k, d, 1300, P=5, powers=powers)
+    sysp = pes.System(polys, n, d, k, exponents=exps, arith=arith)
+    Z = dev(torch, inputs)
+    v, J = sysp.eval_system(dev(torch, np.concatenate(coeffs, axis=1)), Z)
+    for p, supp in enumerate(polys):
+        plan = pes.Plan(supp, n, d, k, exponents=exps[p] if exps else None, arith=arith)
+        pv, pg = plan.eval_grad(dev(torch, coeffs[p]), Z)
+        assert torch.equal(v[:, p], pv) and torch.equal(J[:, p], pg), p
+    sysp.check()
+
+
+@pytest.mark.parametrize("k", [1, 5, 8])
+def test_system_layouts_agree(torch, k):
+    """The matrix layout [k][d+1][P][n] holds exactly the series layout's
+    numbers, one P x n matrix per power of t."""
+    d = 20
+    polys, _, n, coeffs, inputs = case(k, d, 1400 + k)
+    sysp = pes.System(polys, n, d, k)
+    C, Z = dev(torch, np.concatenate(coeffs, axis=1)), dev(torch, inputs)
+    v0, J0 = sysp.eval_system(C, Z, "series")
+    v1, J1 = sysp.eval_system(C, Z, "matrix")
+    sysp.check()
+    assert v1.shape == (k, d + 1, len(polys)) and J1.shape == (k, d + 1, len(polys), n)
+    assert torch.equal(v1, v0.permute(0, 2, 1)) and torch.equal(J1, J0.permute(0, 3, 1, 2))
+    v2, J2 = sysp.eval_grad(C, Z)
+    assert torch.equal(v2, v0) and torch.equal(J2, J0)
+
+
+def test_system_degenerate_cases(torch):
+    """A polynomial with no monomial (its value is its constant, its Jacobian
+    row zero), a variable in no polynomial (a zero column), one polynomial
+    (the plain plan), d = 0."""
+    k, n = 3, 5
+    for d in (0, 11):
+        rng = np.random.default_rng(1500 + d)
+        polys = [[[0, 1], [1, 2, 3]], [], [[0, 3], [3]]]   # x_4 appears nowhere
+        coeffs = [random_md(rng, k, (len(s) + 1, d + 1)) for s in polys]
+        inputs = random_md(rng, k, (n, d + 1))
+        sysp, C = check_against_oracle(torch, polys, None, n, coeffs, inputs, k, d)
+        v, J = sysp.eval_system(C, dev(torch, inputs))
+        assert torch.equal(v[:, 1], dev(torch, coeffs[1][:, 0]))
+        assert not J[:, 1].any() and not J[:, :, 4].any()
+        one = pes.System(polys[:1], n, d, k)
+        plan = pes.Plan(polys[0], n, d, k)
+        Z = dev(torch, inputs)
+        v1, J1 = one.eval_system(dev(torch, coeffs[0]), Z)
+        pv, pg = plan.eval_grad(dev(torch, coeffs[0]), Z)
+        assert torch.equal(v1[:, 0], pv) and torch.equal(J1[:, 0], pg)
+
+
+def test_system_exp_inputs_closed_form(torch):
+    """Inputs z_i = exp(a_i t) and degree-0 coefficients: every value and every
+    Jacobian entry is a sum of exponentials with a closed form; one shared
+    system of 8 polynomials at k = 10, d = 60 against the oracle, which is
+    itself pinned to those closed forms."""
+    k, d = 10, 60
+    sysc = synth.config4(d, k, seed=3, npoly=8, n=16, N=24, lo=2, hi=6)
+    polys = [s for s, _ in sysc.polys]
+    coeffs = [c for _, c in sysc.polys]
+    check_against_oracle(torch, polys, None, sysc.n, coeffs, sysc.inputs, k, d)
+
+
+def truncated_value_err(got, ref):
+    """Normwise error of limb-major series against exact Fractions."""
+    from fractions import Fraction
+    g = [sum((Fraction(float(x)) for x in got[:, j]), Fraction(0)) for j in range(got.shape[1])]
+    den = max(abs(r) for r in ref)
+    return float(max(abs(a - b) for a, b in zip(g, ref)) / den)
+
+
+def test_system_full_size_sampled(torch):
+    """The 64 x 64 system of 512 monomials of 4-16 variables per polynomial at
+    d = 152, k = 10, in the matrix layout: for sampled polynomials the first
+    four coefficients of the value and of sampled Jacobian entries against the
+    oracle on the truncated inputs (coefficient j of a product depends only on
+    coefficients 0..j of its factors), and the whole value series against its
+    exact closed form (inputs exp(a_i t), degree-0 coefficients)."""
+    from fractions import Fraction
+    k, d, dd = 10, 152, 3
+    sysc = synth.config4(d, k, seed=0)
+    polys = [s for s, _ in sysc.polys]
+    sysp = pes.System(polys, sysc.n, d, k)
+    C = dev(torch, np.concatenate([c for _, c in sysc.polys], axis=1))
+    v, J = sysp.eval_system(C, dev(torch, sysc.inputs), "matrix")
+    sysp.check()
+    v, J = v.cpu().numpy(), J.cpu().numpy()
+    z = np.ascontiguousarray(sysc.inputs[:, :, : dd + 1])
+    for p in (0, 37, 63):
+        supp, c = sysc.polys[p]
+        rv, rg = O.eval_grad(supp, sysc.n, np.ascontiguousarray(c[:, :, : dd + 1]), z)
+        assert normwise_err(v[:, : dd + 1, p], rv) <= TOL[k]
+        for i in (0, 21, 63):
+            assert normwise_err(J[:, : dd + 1, p, i], rg[:, i]) <= TOL[k]
+        cs = [sum((Fraction(float(x)) for x in c[:, m, 0]), Fraction(0)) for m in range(c.shape[1])]
+        ref = synth.closed_form_value(supp, cs, sysc.avals, d)
+        assert truncated_value_err(v[:, :, p], ref) <= TOL[k]
+
+
+def test_system_rejects_vjp(torch):
+    sysp = pes.System([[[0, 1]], [[1]]], 2, 3, 2)
+    with pytest.raises(pes.PesError) as e:
+        pes._check(pes.lib().pes_vjp(sysp.handle, None, None, None, None, None, 1, None), "pes_vjp")
+    assert e.value.code == 1
