@@ -47,8 +47,8 @@ typedef enum {
   PES_ECUDA = 4,             /* a CUDA runtime call failed */
   PES_ETIMEOUT = 5,          /* a device-side wait gave up (see pes_check) */
   PES_EINTERNAL = 6,         /* inconsistent internal state */
-  PES_EUNSUPPORTED_SIZE = 7  /* degree too large for the shared-memory staging of both operand series
-                                (or for the threads requested) */
+  PES_EUNSUPPORTED_SIZE = 7  /* degree above 16383, a tile or thread count that does not fit, or a
+                                problem above the static array of pes_eval_grad_static */
 } pes_status;
 
 typedef struct pes_plan_s* pes_plan_t;
@@ -58,8 +58,7 @@ typedef struct pes_batch_s* pes_batch_t;
  * digit products of every output coefficient exactly and round the sum once to
  * k limbs (24-bit digits on the FP64 FMA pipe, 28-bit digits with 32x32->64-bit
  * integer multiply-add); results agree to within the last limb's rounding.
- * PES_ARITH_AUTO takes the integer pipe whenever the degree allows one thread
- * per output coefficient (see PES_EUNSUPPORTED_SIZE), else the FP64 pipe. */
+ * PES_ARITH_AUTO takes the integer pipe. */
 enum { PES_ARITH_AUTO = -1, PES_ARITH_FP64 = 0, PES_ARITH_INT = 1 };
 
 typedef struct {
@@ -85,6 +84,13 @@ typedef struct {
                           output coefficients of a contiguous range of coefficient pairs (j, d-j), so a
                           job's dependants wait for all its parts; more parts shorten the chains of long
                           monomials; 0 = automatic (1, and 1 and 2 are tried when autotuning) */
+  int32_t tile;        /* 0 = automatic: the whole series of a job's operands are staged in shared memory
+                          when they fit (integer / FP64 pipe: d <= 487 / 359 at k=10, 591 / 447 at k=8,
+                          879 / 607 at k=5, 999 / 815 at k=4, 1159 / 919 at k=3, 1379 / 1231 at k=2,
+                          1535 / 1487 at k=1), else the tiled kernel with tiles of 128 coefficients.  > 0 (a multiple of 8 in [16, 1024]): always the
+                          tiled kernel with tiles of this many coefficients: every job is split into output
+                          tiles, each accumulated tile pair by tile pair from staged tiles of its operands
+                          (any degree up to 16383; the same bits as the whole-series kernel) */
 } pes_options;
 
 /* Fill *opt with the defaults. */
@@ -97,7 +103,7 @@ void pes_default_options(pes_options* opt);
  *   supp_ptr: N+1 row pointers into supp_idx (supp_ptr[0] == 0);
  *   supp_idx: 0-based variable indices of monomials 1..N, strictly increasing
  *             within a monomial (the paper's i_1 < ... < i_{n_k}, 1-based);
- *   N >= 0 monomials (a_0 is implicit), n >= 1 variables, d >= 0, k as above.
+ *   N >= 0 monomials (a_0 is implicit), n >= 1 variables, 0 <= d <= 16383, k as above.
  * Errors: PES_EINVAL (bad sizes, empty monomial, index out of range, unsorted or
  * repeated index), PES_EUNSUPPORTED_K, PES_EUNSUPPORTED_SIZE, PES_ENOMEM,
  * PES_ECUDA.  The supports are copied; the caller keeps ownership. */
@@ -228,6 +234,7 @@ typedef struct {
   int32_t split;           /* parts per convolution job in use */
   int32_t complex_series;  /* 1 for a plan of pes_plan_complex */
   int32_t system_P;        /* polynomials of a plan of pes_plan_system, else 0 */
+  int32_t tile;            /* coefficients per output tile of the tiled kernel; 0: whole-series kernel */
 } pes_plan_info;
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);

@@ -220,6 +220,86 @@ __host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int sma
 __device__ __forceinline__ long long conv_start(long long j) { return j * (j + 1) / 2; }
 __device__ __forceinline__ long long corr_start(long long j, long long d) { return j * (d + 1) - j * (j - 1) / 2; }
 
+// The multiply-accumulate of one term into L accumulators and the flush of the
+// accumulators into an exchange row, shared by the whole-series and the tiled
+// convolution kernels.
+template <int K, bool INTV>
+struct DigitMac {
+  using DigitT = typename std::conditional<INTV, int32_t, double>::type;
+  using AccT = typename std::conditional<INTV, long long, double>::type;
+  static constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
+  static constexpr int L = digits_for_k(K, B);
+  static constexpr int XS = x_stride(L, INTV);
+  static constexpr int YS = y_stride(L, INTV);
+  static constexpr int XOFF = INTV ? L : 0;  // digits start after the zero prefix
+
+  // acc += the term x_ix * y_iy of an output coefficient whose grid lies delta
+  // digits above the term's: the products of digits p of x and q of y with
+  // p + delta + q < L (digit positions below the grid's L digits are dropped)
+  __device__ __forceinline__ static void term(const DigitT* xdig, const DigitT* ydig, int ix, int iy, int delta,
+                                              AccT (&A)[L]) {
+    if constexpr (INTV) {
+      if (delta < L) {
+        // zero prefix: digit p of the shifted term is xs[p], no select
+        const int32_t* xs = xdig + ix * XS + XOFF - delta;
+        const int4* y4 = reinterpret_cast<const int4*>(ydig + iy * YS);
+        int32_t Y[YS];
+#pragma unroll
+        for (int v = 0; v < YS / 4; ++v) {
+          const int4 t4 = y4[v];
+          Y[4 * v] = t4.x;
+          Y[4 * v + 1] = t4.y;
+          Y[4 * v + 2] = t4.z;
+          Y[4 * v + 3] = t4.w;
+        }
+#pragma unroll
+        for (int p = 0; p < L; ++p) {
+          const int32_t xv = xs[p];
+#pragma unroll
+          for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+        }
+      }
+    } else {
+      if (delta < L) {
+        const DigitT* yr = ydig + iy * YS;
+        const DigitT* xr = xdig + ix * XS;
+        DigitT Y[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) Y[q] = yr[q];
+#pragma unroll
+        for (int p = 0; p < L; ++p) {
+          const int id = p - delta;
+          DigitT xv = xr[id < 0 ? 0 : id];
+          xv = id < 0 ? DigitT(0) : xv;
+#pragma unroll
+          for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
+        }
+      }
+    }
+  }
+
+  // Add the accumulators into an exchange row (L + 1 words): A[t] belongs to
+  // word t+1 (word 0 is headroom above the grid's top digit).  One flush may
+  // carry up to 2^63 per accumulator, so the values are first carried in
+  // registers: word t+1 takes the low B bits of A[t] plus the part of A[t+1]
+  // above its low B bits, word 0 the part of A[0] above B bits.  No word then
+  // takes more than about 2^(64-B) per flush, and the words stay exact however
+  // many flushes they receive.
+  __device__ __forceinline__ static void flush(unsigned long long* row, AccT (&A)[L]) {
+    long long hi_next = 0;  // part of A[t+1] above its low B bits
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      long long v;
+      if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
+      const long long w = (v & ((1LL << B) - 1)) + hi_next;
+      hi_next = v >> B;  // arithmetic shift: v = hi * 2^B + lo
+      if (w != 0) atomicAdd(row + t + 1, static_cast<unsigned long long>(w));
+      A[t] = 0;
+    }
+    if (hi_next != 0) atomicAdd(row, static_cast<unsigned long long>(hi_next));
+  }
+};
+
 template <int K, bool INTV>
 __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1) dag_kernel(DagArgs a) {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
@@ -445,68 +525,9 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
         AccT A[L];
   #pragma unroll
         for (int t = 0; t < L; ++t) A[t] = 0;
-        // Add the accumulators into the exchange row of coefficient jj: A[t]
-        // belongs to word t+1 (word 0 is headroom above the grid's top digit).
-        // One flush may carry up to 2^63 per accumulator, so the values are first
-        // carried in registers: word t+1 takes the low B bits of A[t] plus the
-        // part of A[t+1] above its low B bits, word 0 the part of A[0] above B
-        // bits.  No word then takes more than about 2^(64-B) per flush, and the
-        // words stay exact however many flushes they receive.
-        auto flush = [&](int jj) {
-          unsigned long long* row = exch + jj * (L + 1);
-          long long hi_next = 0;  // part of A[t+1] above its low B bits
-  #pragma unroll
-          for (int t = L - 1; t >= 0; --t) {
-            long long v;
-            if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
-            const long long w = (v & ((1LL << B) - 1)) + hi_next;
-            hi_next = v >> B;  // arithmetic shift: v = hi * 2^B + lo
-            if (w != 0) atomicAdd(row + t + 1, static_cast<unsigned long long>(w));
-            A[t] = 0;
-          }
-          if (hi_next != 0) atomicAdd(row, static_cast<unsigned long long>(hi_next));
-        };
+        auto flush = [&](int jj) { DigitMac<K, INTV>::flush(exch + jj * (L + 1), A); };
         // one term x_ix * y_iy of output coefficient j, delta digits below its grid
-        auto term = [&](int ix, int iy, int delta) {
-          if constexpr (INTV) {
-            if (delta < L) {
-              // zero prefix: digit p of the shifted term is xs[p], no select
-              const int32_t* xs = xdig + ix * XS + XOFF - delta;
-              const int4* y4 = reinterpret_cast<const int4*>(ydig + iy * YS);
-              int32_t Y[YS];
-  #pragma unroll
-              for (int v = 0; v < YS / 4; ++v) {
-                const int4 t4 = y4[v];
-                Y[4 * v] = t4.x;
-                Y[4 * v + 1] = t4.y;
-                Y[4 * v + 2] = t4.z;
-                Y[4 * v + 3] = t4.w;
-              }
-  #pragma unroll
-              for (int p = 0; p < L; ++p) {
-                const int32_t xv = xs[p];
-  #pragma unroll
-                for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
-              }
-            }
-          } else {
-            if (delta < L) {
-              const DigitT* yr = ydig + iy * YS;
-              const DigitT* xr = xdig + ix * XS;
-              DigitT Y[L];
-  #pragma unroll
-              for (int q = 0; q < L; ++q) Y[q] = yr[q];
-  #pragma unroll
-              for (int p = 0; p < L; ++p) {
-                const int id = p - delta;
-                DigitT xv = xr[id < 0 ? 0 : id];
-                xv = id < 0 ? DigitT(0) : xv;
-  #pragma unroll
-                for (int q = 0; q < L - p; ++q) mac(xv, Y[q], A[p + q]);
-              }
-            }
-          }
-        };
+        auto term = [&](int ix, int iy, int delta) { DigitMac<K, INTV>::term(xdig, ydig, ix, iy, delta, A); };
         if constexpr (INTV) {
           // Coefficients j and d-j share d+2 terms (the middle coefficient d/2,
           // when d+1 is odd, forms a group of its own, the last one).  Every lane
@@ -655,6 +676,373 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       st_release(a.flags + sj, epoch);
     }
     claimed = ahead;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tiled convolution kernel (degrees whose whole series do not fit in shared
+// memory)
+// ---------------------------------------------------------------------------
+
+// Shared-memory layout of the tiled kernel for tiles of D coefficients: the
+// exchange rows of the output tile; the X rows of one tile of the first
+// operand and the window of 2D + 4 rows of the second operand they meet; the
+// grids of those rows and the reference grid of every output coefficient.
+struct TileLayout {
+  size_t exch, raw, xdig, ydig, gx, gy, gs, bar, misc, total;
+};
+
+__host__ __device__ constexpr int tile_window(int D) { return 2 * D + 4; }
+
+__host__ __device__ inline TileLayout tile_layout(int L, bool intv, int D) {
+  const int digit_bytes = intv ? 4 : 8;
+  const int W = tile_window(D);
+  TileLayout o;
+  size_t off = 0;
+  o.exch = off;
+  off = align_up(off + size_t(D) * (L + 1) * sizeof(unsigned long long), 128);
+  o.raw = off;  // X rows as copied (FP64 variant: then the Y window)
+  off = align_up(off + size_t(intv ? D : D + W) * row_words(L, intv) * sizeof(int32_t), 128);
+  o.xdig = off;
+  off = align_up(off + size_t(D) * x_stride(L, intv) * digit_bytes, 16);
+  o.ydig = off;  // integer variant: the Y window lands here as copied
+  off = align_up(off + size_t(W) * y_stride(L, intv) * digit_bytes, 16);
+  o.gx = off;
+  off = align_up(off + size_t(D) * 4, 16);
+  o.gy = off;
+  off = align_up(off + size_t(W) * 4, 16);
+  o.gs = off;
+  off = align_up(off + size_t(D) * 4, 16);
+  o.bar = off;
+  off += 16;
+  o.misc = off;
+  off += 64;
+  o.total = align_up(off, 128);
+  return o;
+}
+
+// Every job is split into output tiles of D = a.tile coefficients; sub-job
+// j * a.split + t computes coefficients [tD, tD + D) of job j (a.split tiles
+// per job cover the largest degree).  Output coefficient c_j = sum_i x_i y_{j-i}
+// (Eq. eqconvform; the correlation sums x_{j+i} y_i) is accumulated tile pair
+// by tile pair: for every tile I of the first operand that meets the output
+// tile, its D rows and the window of the second operand's rows they pair with
+// are staged by TMA bulk copies, and every term of the pair adds into the
+// output tile's exchange rows, which stay in shared memory until the last
+// tile pair.  The reference grid of each output coefficient is the largest
+// grid of its terms over all tiles, taken before the first tile pair, so that
+// the exact sums and the L digits they are cut to are those of the
+// whole-series kernel, bit for bit.
+template <int K, bool INTV>
+__global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1) dag_tiled_kernel(DagArgs a) {
+  using M = DigitMac<K, INTV>;
+  using DigitT = typename M::DigitT;
+  using AccT = typename M::AccT;
+  constexpr int B = M::B;
+  constexpr int L = M::L;
+  constexpr int XS = M::XS;
+  constexpr int YS = M::YS;
+  constexpr int XOFF = M::XOFF;
+  constexpr int RW = row_words(L, INTV);
+  constexpr int R = INTV ? static_cast<int>((1LL << (63 - 2 * (B - 1))) / L) : 128 / L;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int D = a.tile;
+  const TileLayout lay = tile_layout(L, INTV, D);
+  unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.exch);
+  int32_t* raw = reinterpret_cast<int32_t*>(smem + lay.raw);
+  DigitT* xdig = reinterpret_cast<DigitT*>(smem + lay.xdig);
+  DigitT* ydig = reinterpret_cast<DigitT*>(smem + lay.ydig);
+  int32_t* gx = reinterpret_cast<int32_t*>(smem + lay.gx);
+  int32_t* gy = reinterpret_cast<int32_t*>(smem + lay.gy);
+  int32_t* gs = reinterpret_cast<int32_t*>(smem + lay.gs);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
+  int32_t* misc = reinterpret_cast<int32_t*>(smem + lay.misc);
+
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
+  const uint32_t bar_addr = smem_u32(bar);
+  if (tid == 0) {
+    mbar_init(bar_addr, 1);
+    fence_mbar_init();
+  }
+  if constexpr (INTV) {
+    for (int t = tid; t < D * XS; t += T) xdig[t] = 0;  // zero prefixes of the X rows
+  }
+  __syncthreads();
+  const int epoch = *reinterpret_cast<volatile int32_t*>(&a.ctrl->epoch);
+  uint32_t phase = 0;
+  const int tiles = parts(a);
+  const int nsub = a.njobs * tiles;
+
+  // bulk copies of rows [c0, c0 + cnt) of a series (digit rows to `rows`, grids
+  // to `grid`); cnt and c0 are multiples of 4, so every copy is a multiple of
+  // 16 bytes from a 16-byte boundary
+  auto copy_rows = [&](const int32_t* series, int S, int c0, int cnt, void* rows, int32_t* grid) {
+    bulk_g2s(smem_u32(rows), series + static_cast<long long>(c0) * RW, static_cast<uint32_t>(cnt) * RW * 4u,
+             bar_addr);
+    bulk_g2s(smem_u32(grid), series + static_cast<long long>(S) * RW + c0, static_cast<uint32_t>(cnt) * 4u,
+             bar_addr);
+  };
+  // bounded wait for the copies of the current stage; false: timed out (the
+  // copies in flight are then given their own bounded wait before the exit)
+  auto landed = [&]() {
+    const bool ok = __syncthreads_and(mbar_wait(bar_addr, phase, a.timeout_ns));
+    if (!ok) mbar_wait(bar_addr, phase, a.timeout_ns);
+    phase ^= 1u;
+    return ok;
+  };
+
+  for (;;) {
+    if (tid == 0) {
+      misc[0] = atomicAdd(&a.ctrl->next[a.counter], 1);
+      misc[1] = 0;
+    }
+    __syncthreads();
+    const int sj = misc[0];
+    if (sj >= nsub) break;
+    const int job = sj / tiles;
+    const int tile = sj - job * tiles;
+    const ConvJob jb = a.jobs[job];
+    const InstInfo in = a.inst[jb.inst];
+    const int d = in.d, S = in.S;
+    const int j0 = tile * D;
+    const int jn = min(D, d + 1 - j0);  // output coefficients of this tile (<= 0: none)
+    const bool elementwise = jb.kind == JOB_ADD || jb.kind == JOB_SUB;
+    const bool conv = jb.kind == JOB_CONV;
+    const int last = d / D;  // last tile of this instance's series
+    if (jn > 0) {
+      // ---- operands: the tiles this output tile reads ----
+      if (tid == 0) {
+        const int t_lo = elementwise ? tile : 0;
+        const int t_hi = (elementwise || conv) ? tile : last;
+        bool ok = true;
+        for (int t = t_lo; ok && t <= t_hi; ++t) {
+          if (jb.dep1 >= 0) ok = wait_flag(a, jb.dep1 * tiles + t, epoch, job);
+          if (ok && jb.dep2 >= 0) ok = wait_flag(a, jb.dep2 * tiles + t, epoch, job);
+        }
+        misc[1] = ok ? 0 : 1;
+        fence_proxy_async_global();
+        fence_proxy_async_shared();
+      }
+      __syncthreads();
+      if (misc[1]) break;
+      const int32_t* xs = a.ws + in.ws_base + static_cast<long long>(jb.in1) * in.ws_sstride;
+      const int32_t* ys = a.ws + in.ws_base + static_cast<long long>(jb.in2) * in.ws_sstride;
+      int32_t* zrows = a.ws + in.ws_base + static_cast<long long>(jb.out) * in.ws_sstride;
+      int32_t* zgrid = zrows + static_cast<long long>(S) * RW;
+      int32_t* ywin = INTV ? reinterpret_cast<int32_t*>(ydig) : raw + D * RW;  // Y rows as copied
+
+      if (elementwise) {
+        // ---- out = in1 +- in2 on the rows of this tile, exactly, as L digits ----
+        const int cnt = min(D, S - j0);
+        if (tid == 0) {
+          fence_proxy_async_shared();
+          mbar_expect_tx(bar_addr, 2u * static_cast<uint32_t>(cnt) * (RW + 1) * 4u);
+          copy_rows(xs, S, j0, cnt, raw, gx);
+          copy_rows(ys, S, j0, cnt, ywin, gy);
+        }
+        if (!landed()) {
+          if (tid == 0) set_error(a.ctrl, kStatusTimeout, job, -2);
+          break;
+        }
+        const long long sgn = jb.kind == JOB_SUB ? -1 : 1;
+        for (int t = tid; t < jn; t += T) {
+          const int32_t g = max(gx[t], gy[t]);
+          int32_t o[L];
+          int32_t gz = GRID_ZERO;
+          if (g < -100000) {
+#pragma unroll
+            for (int p = 0; p < L; ++p) o[p] = 0;
+          } else {
+            const int sx = g - gx[t], sy = g - gy[t];
+            int64_t E[L + 1];
+            E[0] = 0;
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+              const long long xv = q >= sx ? raw[t * RW + q - sx] : 0;
+              const long long yv = q >= sy ? ywin[t * RW + q - sy] : 0;
+              E[q + 1] = xv + sgn * yv;
+            }
+            gz = sum_to_digits<L, B>(E, g + 1, o);
+          }
+          int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j0 + t) * RW);
+#pragma unroll
+          for (int v = 0; v < RW / 4; ++v)
+            dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
+                               4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
+          zgrid[j0 + t] = gz;
+        }
+      } else {
+        // ---- reference grid of every output coefficient: the largest grid
+        // of its terms, a warp per coefficient over the operands' grids ----
+        const int32_t* gX = xs + static_cast<long long>(S) * RW;
+        const int32_t* gY = ys + static_cast<long long>(S) * RW;
+        for (int t = warp; t < D; t += nwarps) {
+          const int j = j0 + t;
+          int32_t m = 2 * GRID_ZERO;
+          if (t < jn) {
+            const int n = conv ? j + 1 : d - j + 1;
+            for (int i = lane; i < n; i += 32)
+              m = max(m, conv ? __ldcg(gX + i) + __ldcg(gY + j - i) : __ldcg(gX + j + i) + __ldcg(gY + i));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+          if (lane == 0) gs[t] = m;
+        }
+        for (int t = tid; t < D * (L + 1); t += T) exch[t] = 0ull;
+
+        // Lanes: the output tile's coefficients a = j0 + g and b = j0 + D-1-g
+        // form group g (D/2 groups); each group gets T / (D/2) consecutive lanes
+        // (the first T mod (D/2) groups one more), which split the group's terms
+        // of the tile pair.  In a full tile pair every coefficient has D terms;
+        // in the diagonal one a and b have D + 1 together.  One of the two is
+        // walked forwards and the other backwards, so that lanes of the same
+        // rank read the same X row in every group (a broadcast) and consecutive
+        // Y rows.
+        const int G = D / 2;
+        const int Qb = T / G, extra = T - Qb * G;
+        int grp, q, Q;
+        if (tid < extra * (Qb + 1)) {
+          Q = Qb + 1;
+          grp = tid / Q;
+          q = tid - grp * Q;
+        } else {
+          Q = Qb;
+          const int t2 = tid - extra * (Qb + 1);
+          grp = extra + t2 / Q;
+          q = t2 - (grp - extra) * Q;
+        }
+        const int ca = j0 + grp, cb = j0 + D - 1 - grp;  // the group's two coefficients
+        const int i_first = conv ? 0 : tile, i_last = conv ? tile : last;
+        bool ok = true;
+        for (int I = i_first; I <= i_last; ++I) {
+          const int i0 = I * D;
+          // first-operand index range of every coefficient of the tile pair
+          auto range = [&](int j, int& lo, int& hi) {
+            if (j > d) {
+              lo = hi = 0;
+            } else if (conv) {
+              lo = i0;
+              hi = min(i0 + D, j + 1);
+            } else {
+              lo = max(i0, j);
+              hi = min(i0 + D, d + 1);
+            }
+            if (hi < lo) hi = lo;
+          };
+          // second-operand window: conv j - i, corr i - j, over the tile pair
+          const int ymin = conv ? j0 - (i0 + D - 1) : i0 - (j0 + jn - 1);
+          const int ymax = min(d, conv ? j0 + jn - 1 - i0 : i0 + D - 1 - j0);
+          const int y0 = max(0, ymin) & ~3;
+          const int ycnt = min((ymax - y0 + 1 + 3) & ~3, S - y0);
+          const int xcnt = min(D, S - i0);
+          __syncthreads();  // the previous tile pair's rows are no longer read
+          if (tid == 0) {
+            fence_proxy_async_shared();
+            mbar_expect_tx(bar_addr, static_cast<uint32_t>(xcnt + ycnt) * (RW + 1) * 4u);
+            copy_rows(xs, S, i0, xcnt, raw, gx);
+            copy_rows(ys, S, y0, ycnt, ywin, gy);
+          }
+          if (!landed()) {
+            if (tid == 0) set_error(a.ctrl, kStatusTimeout, job, -2);
+            ok = false;
+            break;
+          }
+          // ---- staged digit rows into the layouts of the multiply-accumulate loop ----
+          if constexpr (INTV) {
+            constexpr int V4 = RW / 4;
+            const int4* src = reinterpret_cast<const int4*>(raw);
+            for (int t = tid; t < xcnt * V4; t += T) {
+              const int c = t / V4, v = t - c * V4;
+              const int4 qv = src[t];
+              int32_t* dst = xdig + c * XS + XOFF + 4 * v;
+              if (4 * v < L) dst[0] = qv.x;
+              if (4 * v + 1 < L) dst[1] = qv.y;
+              if (4 * v + 2 < L) dst[2] = qv.z;
+              if (4 * v + 3 < L) dst[3] = qv.w;
+            }
+          } else {
+            for (int t = tid; t < xcnt * L; t += T) {
+              const int c = t / L, p = t - c * L;
+              xdig[c * XS + p] = static_cast<double>(raw[c * RW + p]);
+            }
+            for (int t = tid; t < ycnt * L; t += T) {
+              const int c = t / L, p = t - c * L;
+              ydig[c * YS + p] = static_cast<double>(ywin[c * RW + p]);
+            }
+          }
+          __syncthreads();
+
+          // ---- multiply-accumulate the group's terms of this tile pair ----
+          int lo_a, hi_a, lo_b, hi_b;
+          range(ca, lo_a, hi_a);
+          range(cb, lo_b, hi_b);
+          const int na = hi_a - lo_a, tp = na + (hi_b - lo_b);
+          const int H = (tp + Q - 1) / Q;
+          const int p0 = min(q * H, tp), p1 = min(p0 + H, tp);
+          AccT A[L];
+#pragma unroll
+          for (int t = 0; t < L; ++t) A[t] = 0;
+          int jcur = p0 < na ? ca : cb;
+          int left = R;
+          for (int pos = p0; pos < p1; ++pos) {
+            int j, x;
+            if (pos < na) {
+              j = ca;
+              x = conv ? lo_a + pos : hi_a - 1 - pos;
+            } else {
+              j = cb;
+              x = conv ? hi_b - 1 - (pos - na) : lo_b + (pos - na);
+            }
+            const int iy = conv ? j - x : x - j;
+            const int lx = x - i0, ly = iy - y0;
+            M::term(xdig, ydig, lx, ly, gs[j - j0] - gx[lx] - gy[ly], A);
+            --left;
+            if (pos == na - 1 && pos + 1 < p1) {
+              M::flush(exch + (ca - j0) * (L + 1), A);  // this lane leaves coefficient a
+              jcur = cb;
+            }
+            if (left == 0) {
+              M::flush(exch + (jcur - j0) * (L + 1), A);
+              left = R;
+            }
+          }
+          if (p1 > p0) M::flush(exch + (jcur - j0) * (L + 1), A);
+        }
+        if (!ok) break;
+        __syncthreads();
+
+        // ---- one output coefficient per thread: the exact sum as L digits on its grid ----
+        for (int t = tid; t < jn; t += T) {
+          const int32_t g = gs[t];
+          int32_t o[L];
+          int32_t gz = GRID_ZERO;
+          if (g < -100000) {
+#pragma unroll
+            for (int p = 0; p < L; ++p) o[p] = 0;
+          } else {
+            int64_t E[L + 1];
+#pragma unroll
+            for (int u = 0; u <= L; ++u) E[u] = static_cast<int64_t>(exch[t * (L + 1) + u]);
+            gz = sum_to_digits<L, B>(E, g, o);
+          }
+          int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j0 + t) * RW);
+#pragma unroll
+          for (int v = 0; v < RW / 4; ++v)
+            dst[v] = make_int4(4 * v < L ? o[4 * v] : 0, 4 * v + 1 < L ? o[4 * v + 1] : 0,
+                               4 * v + 2 < L ? o[4 * v + 2] : 0, 4 * v + 3 < L ? o[4 * v + 3] : 0);
+          zgrid[j0 + t] = gz;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      fence_proxy_async_global();
+      st_release(a.flags + sj, epoch);
+    }
   }
 }
 
@@ -884,20 +1272,20 @@ __global__ void __launch_bounds__(256) int_peak_kernel(long long* sink, int iter
 }
 
 template <int K, bool INTV>
-void* dag_fn() {
-  return reinterpret_cast<void*>(&dag_kernel<K, INTV>);
+void* dag_fn(bool tiled) {
+  return tiled ? reinterpret_cast<void*>(&dag_tiled_kernel<K, INTV>) : reinterpret_cast<void*>(&dag_kernel<K, INTV>);
 }
 
-void* dag_kernel_ptr(int k, int arith) {
+void* dag_kernel_ptr(int k, int arith, bool tiled) {
   const bool iv = arith == ARITH_INT;
   switch (k) {
-    case 1: return iv ? dag_fn<1, true>() : dag_fn<1, false>();
-    case 2: return iv ? dag_fn<2, true>() : dag_fn<2, false>();
-    case 3: return iv ? dag_fn<3, true>() : dag_fn<3, false>();
-    case 4: return iv ? dag_fn<4, true>() : dag_fn<4, false>();
-    case 5: return iv ? dag_fn<5, true>() : dag_fn<5, false>();
-    case 8: return iv ? dag_fn<8, true>() : dag_fn<8, false>();
-    case 10: return iv ? dag_fn<10, true>() : dag_fn<10, false>();
+    case 1: return iv ? dag_fn<1, true>(tiled) : dag_fn<1, false>(tiled);
+    case 2: return iv ? dag_fn<2, true>(tiled) : dag_fn<2, false>(tiled);
+    case 3: return iv ? dag_fn<3, true>(tiled) : dag_fn<3, false>(tiled);
+    case 4: return iv ? dag_fn<4, true>(tiled) : dag_fn<4, false>(tiled);
+    case 5: return iv ? dag_fn<5, true>(tiled) : dag_fn<5, false>(tiled);
+    case 8: return iv ? dag_fn<8, true>(tiled) : dag_fn<8, false>(tiled);
+    case 10: return iv ? dag_fn<10, true>(tiled) : dag_fn<10, false>(tiled);
     default: return nullptr;
   }
 }
@@ -912,35 +1300,40 @@ size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth) {
   return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax, depth).total;
 }
 
+size_t dag_tiled_smem_bytes(int k, int arith, int tile) {
+  return tile_layout(digits_of_k(k, arith), arith == ARITH_INT, tile).total;
+}
+
 // The dynamic shared-memory limit is a property of the kernel function on a
 // device, shared by every plan: raise it, never lower it, so that a plan built
 // later for a smaller degree cannot break the launches of an earlier one.
-cudaError_t dag_prepare(int k, int arith, size_t smem) {
-  void* fn = dag_kernel_ptr(k, arith);
+cudaError_t dag_prepare(int k, int arith, size_t smem, bool tiled) {
+  void* fn = dag_kernel_ptr(k, arith, tiled);
   if (!fn) return cudaErrorInvalidValue;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int>, size_t> granted;
+  static std::map<std::tuple<int, int, int, bool>, size_t> granted;
   std::lock_guard<std::mutex> lock(mu);
-  size_t& cur = granted[std::make_tuple(dev, k, arith)];
+  size_t& cur = granted[std::make_tuple(dev, k, arith, tiled)];
   if (smem <= cur) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e == cudaSuccess) cur = smem;
   return e;
 }
 
-cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm) {
-  void* fn = dag_kernel_ptr(k, arith);
+cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm, bool tiled) {
+  void* fn = dag_kernel_ptr(k, arith, tiled);
   if (!fn) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st) {
-  void* fn = dag_kernel_ptr(k, arith);
+  const bool tiled = a.tile > 0;
+  void* fn = dag_kernel_ptr(k, arith, tiled);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = dag_smem_bytes(k, arith, a.smax, a.dmax, a.depth);
+  const size_t smem = tiled ? dag_tiled_smem_bytes(k, arith, a.tile) : dag_smem_bytes(k, arith, a.smax, a.dmax, a.depth);
   DagArgs copy = a;
   void* args[] = {&copy};
   return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);

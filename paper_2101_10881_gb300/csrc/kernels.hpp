@@ -40,6 +40,8 @@ struct DagArgs {
   int32_t split;            // parts per job (integer variant: 1, 2 or 4): part p of job j is
                             // dispatched, flagged and waited for as j * split + p
   long long timeout_ns;     // bound on every wait
+  int32_t tile;             // > 0: the tiled kernel, output tiles of `tile` coefficients, `split`
+                            // tiles per job (sub-job j * split + t is tile t of job j)
 };
 
 struct AddArgs {
@@ -75,6 +77,11 @@ constexpr int kMaxSplit = 4;  // largest number of parts a convolution job is sp
 // Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax) at
 // staging depth 1 or 2.
 size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth);
+// Shared-memory footprint of the tiled DAG kernel (degrees whose whole series
+// do not fit) for output tiles of `tile` coefficients, any degree.
+size_t dag_tiled_smem_bytes(int k, int arith, int tile);
+constexpr int kDefaultTile = 128;  // coefficients per output tile of the tiled kernel
+constexpr int kMaxDegree = 16383;  // largest degree the API accepts
 int digits_of_k(int k, int arith);
 // int32 words of one workspace row (the digits of one coefficient, padded) and
 // of one workspace slot (a series of S coefficients: S rows, then S grids).
@@ -89,8 +96,8 @@ cudaError_t launch_pack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_unpack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st);
 cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaStream_t st);
-cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm);
-cudaError_t dag_prepare(int k, int arith, size_t smem);
+cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm, bool tiled = false);
+cudaError_t dag_prepare(int k, int arith, size_t smem, bool tiled = false);
 cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out,
                              int64_t count, cudaStream_t st);
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters, cudaStream_t st);

@@ -11,6 +11,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pes.h"
@@ -72,19 +73,53 @@ struct CopyTable {
   int32_t n = 0;
 };
 
-// Device state shared by single plans and batches.
 // The arithmetic a launch shape uses: PES_ARITH_AUTO takes the integer pipe
-// when one lane per coefficient pair of the largest degree fits in a CTA.
+// (whole series in shared memory where they fit, else output tiles).
 int32_t resolve_arith(int32_t k, int32_t requested, int32_t dmax) {
-  if (requested != PES_ARITH_AUTO) return requested;
-  return (dmax + 2) / 2 <= pes::dag_max_threads(k) ? pes::ARITH_INT : pes::ARITH_FP64;
+  (void)k;
+  (void)dmax;
+  return requested != PES_ARITH_AUTO ? requested : pes::ARITH_INT;
 }
+
+// Threads per CTA of the whole-series kernel for the largest degree dmax
+// (`requested` 0: automatic), or 0 when no CTA shape within the cap holds one
+// lane per coefficient pair (integer variant).
+int32_t whole_series_threads(int32_t k, int32_t arith, int32_t dmax, int32_t requested) {
+  int32_t t = requested;
+  if (arith == pes::ARITH_INT) {
+    // by default two lanes per coefficient pair (one per output coefficient),
+    // whole warps; at least one lane per pair
+    const int32_t pairs = (dmax + 2) / 2;
+    const int32_t least = (pairs + 31) / 32 * 32;
+    t = t == 0 ? std::max(least, std::min((2 * pairs + 31) / 32 * 32, pes::dag_max_threads(k))) : std::max(t, least);
+  } else if (t == 0) {
+    t = 128;  // FP64 variant: 128 threads share the terms evenly
+  }
+  return t <= pes::dag_max_threads(k) ? t : 0;
+}
+
+// The whole-series kernel runs degree dmax (lanes and shared memory at staging
+// depth 1); otherwise the tiled kernel takes it.
+bool whole_series_fits(int32_t k, int32_t arith, int32_t dmax, int32_t requested, int optin) {
+  return whole_series_threads(k, arith, dmax, requested) > 0 &&
+         pes::dag_smem_bytes(k, arith, pes::series_stride(dmax), dmax, 1) <= static_cast<size_t>(optin);
+}
+
+int device_optin() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  return optin;
+}
+
+// Device state shared by single plans and batches.
 
 struct Exec {
   int32_t k = 0, arith = 0, threads = 128, ctas_per_sm = 0;
   int32_t smax = 0, dmax = 0;
   int32_t depth = 1, staging = 0;  // staging depth in use; requested (0 = automatic)
   int32_t split = 1, split_req = 0;  // parts per convolution job in use; requested (0 = automatic)
+  int32_t tile = 0;  // > 0: the tiled kernel, output tiles of this many coefficients (split = tiles per job)
   size_t smem = 0;
   int32_t blocks_per_sm = 0, nsm = 0, optin = 0;
   long long timeout_ns = 0;
@@ -120,8 +155,10 @@ struct Exec {
     pes_status s = put(&L.jobs, jobs);
     if (s != PES_OK) return s;
     if (L.n > 0) {
-      // one flag per part of every job, for the largest split
-      const size_t nf = static_cast<size_t>(L.n) * pes::kMaxSplit;
+      // one flag per part of every job, for the largest split (tiled kernel: per tile)
+      if (static_cast<int64_t>(L.n) * std::max(split, pes::kMaxSplit) >= (1LL << 31))
+        return fail(PES_EUNSUPPORTED_SIZE, "jobs x tiles per job exceed 2^31");
+      const size_t nf = static_cast<size_t>(L.n) * std::max(split, pes::kMaxSplit);
       cudaError_t e = cudaMalloc(&L.flags, sizeof(int32_t) * nf);
       if (e != cudaSuccess) return fail(PES_ENOMEM, "job flags");
       owned.push_back(L.flags);
@@ -165,32 +202,36 @@ struct Exec {
     PES_CUDA(cudaGetDevice(&dev));
     PES_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     PES_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // integer variant: by default two lanes per coefficient pair (one lane per
-    // output coefficient) of the largest degree, whole warps; at least one lane
-    // per pair; FP64 variant: 128 threads share the terms evenly
-    if (arith == pes::ARITH_INT) {
-      const int32_t pairs = (dmax + 2) / 2;
-      const int32_t least = (pairs + 31) / 32 * 32;
-      threads = threads == 0 ? std::max(least, std::min((2 * pairs + 31) / 32 * 32, pes::dag_max_threads(k)))
-                             : std::max(threads, least);
-    } else if (threads == 0) {
-      threads = 128;
-    }
-    if (threads > pes::dag_max_threads(k))
-      return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(threads) +
-                                             " threads per CTA; at most " + std::to_string(pes::dag_max_threads(k)) +
-                                             " at k=" + std::to_string(k));
-    // staging depth: 2 only when asked for and it fits (the autotuner tries both)
     staging = o.staging;
     split_req = o.split;
-    split = (arith == pes::ARITH_INT && o.split > 0) ? o.split : 1;
-    depth = (staging == 2 && pes::dag_smem_bytes(k, arith, smax, dmax, 2) <= static_cast<size_t>(optin)) ? 2 : 1;
-    smem = pes::dag_smem_bytes(k, arith, smax, dmax, depth);
+    if (o.tile == 0 && whole_series_fits(k, arith, dmax, threads, optin)) {
+      // whole series in shared memory; staging depth 2 only when asked for and
+      // it fits (the autotuner tries both)
+      tile = 0;
+      threads = whole_series_threads(k, arith, dmax, threads);
+      split = (arith == pes::ARITH_INT && o.split > 0) ? o.split : 1;
+      depth = (staging == 2 && pes::dag_smem_bytes(k, arith, smax, dmax, 2) <= static_cast<size_t>(optin)) ? 2 : 1;
+      smem = pes::dag_smem_bytes(k, arith, smax, dmax, depth);
+    } else {
+      // output tiles: at least one lane per pair of coefficients of a tile; by
+      // default two per pair (integer variant) or 128 threads (FP64 variant)
+      tile = o.tile > 0 ? o.tile : pes::kDefaultTile;
+      if (threads == 0)
+        threads = arith == pes::ARITH_INT ? std::min(2 * tile, pes::dag_max_threads(k)) : 128;
+      threads = std::max(threads, (tile / 2 + 31) / 32 * 32);
+      if (threads > pes::dag_max_threads(k))
+        return fail(PES_EUNSUPPORTED_SIZE, "tiles of " + std::to_string(tile) + " coefficients need " +
+                                               std::to_string(threads) + " threads per CTA; at most " +
+                                               std::to_string(pes::dag_max_threads(k)) + " at k=" + std::to_string(k));
+      split = (dmax + tile) / tile;
+      depth = 1;
+      smem = pes::dag_tiled_smem_bytes(k, arith, tile);
+    }
     if (smem > static_cast<size_t>(optin))
       return fail(PES_EUNSUPPORTED_SIZE, "degree " + std::to_string(dmax) + " needs " + std::to_string(smem) +
                                              " bytes of shared memory at k=" + std::to_string(k));
-    PES_CUDA(pes::dag_prepare(k, arith, smem));
-    PES_CUDA(pes::dag_occupancy(k, arith, threads, smem, &blocks_per_sm));
+    PES_CUDA(pes::dag_prepare(k, arith, smem, tile > 0));
+    PES_CUDA(pes::dag_occupancy(k, arith, threads, smem, &blocks_per_sm, tile > 0));
     if (blocks_per_sm < 1) return fail(PES_EUNSUPPORTED_SIZE, "convolution kernel does not fit on an SM");
     if (ctas_per_sm > 0) blocks_per_sm = std::min(blocks_per_sm, ctas_per_sm);
     pes_status s = upload(&inst, insts);
@@ -210,22 +251,25 @@ struct Exec {
 
   // shared memory of the convolution kernel at staging depth `dp`, or 0 if it does not fit
   size_t smem_at(int32_t dp) const {
+    if (tile > 0) return dp == 1 ? pes::dag_tiled_smem_bytes(k, arith, tile) : 0;
     const size_t b = pes::dag_smem_bytes(k, arith, smax, dmax, dp);
     return b <= static_cast<size_t>(optin) ? b : 0;
   }
 
   // threads per CTA, a cap on CTAs per SM (0: as many as fit), the staging
-  // depth and the parts per job (integer variant only) for later launches
+  // depth and the parts per job (integer variant only; the tiled kernel keeps
+  // its tiles per job) for later launches
   pes_status configure(int32_t t, int32_t ctas_cap, int32_t dp, int32_t sp, JobList& L) {
     const size_t b = smem_at(dp);
     if (b == 0) return fail(PES_EUNSUPPORTED_SIZE, "staging depth does not fit in shared memory");
-    PES_CUDA(pes::dag_prepare(k, arith, b));
+    if (tile > 0 && t < tile / 2) return fail(PES_EUNSUPPORTED_SIZE, "fewer lanes than pairs of a tile");
+    PES_CUDA(pes::dag_prepare(k, arith, b, tile > 0));
     int bps = 0;
-    PES_CUDA(pes::dag_occupancy(k, arith, t, b, &bps));
+    PES_CUDA(pes::dag_occupancy(k, arith, t, b, &bps, tile > 0));
     if (bps < 1) return fail(PES_EUNSUPPORTED_SIZE, "configuration does not fit on an SM");
     smem = b;
     depth = dp;
-    split = arith == pes::ARITH_INT ? std::max(1, sp) : 1;
+    if (tile == 0) split = arith == pes::ARITH_INT ? std::max(1, sp) : 1;
     threads = t;
     blocks_per_sm = ctas_cap > 0 ? std::min(bps, ctas_cap) : bps;
     L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(
@@ -247,6 +291,7 @@ struct Exec {
     a.depth = depth;
     a.split = split;
     a.timeout_ns = timeout_ns;
+    a.tile = tile;
     return a;
   }
 
@@ -337,6 +382,8 @@ pes_status parse_options(const pes_options* opt, pes_options& o) {
   if (o.staging < 0 || o.staging > 2) return fail(PES_EINVAL, "staging must be 0, 1 or 2");
   if (!(o.split == 0 || o.split == 1 || o.split == 2 || o.split == 4))
     return fail(PES_EINVAL, "split must be 0, 1, 2 or 4");
+  if (o.tile != 0 && (o.tile < 16 || o.tile > 1024 || o.tile % 8 != 0))
+    return fail(PES_EINVAL, "tile must be 0 (automatic) or a multiple of 8 in [16, 1024]");
   return PES_OK;
 }
 
@@ -446,7 +493,7 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
     std::vector<int32_t> depths{E.depth};
     if (E.staging == 0) depths = {1, 2};
     std::vector<int32_t> splits{E.split};
-    if (E.split_req == 0 && E.arith == pes::ARITH_INT) splits = {1, 2};
+    if (E.split_req == 0 && E.arith == pes::ARITH_INT && E.tile == 0) splits = {1, 2};
     cudaEvent_t e0, e1;
     PES_CUDA(cudaEventCreate(&e0));
     PES_CUDA(cudaEventCreate(&e1));
@@ -491,8 +538,8 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
 
 std::string tune_key(const Exec& E, int64_t njobs, uint64_t signature) {
   char key[200];
-  std::snprintf(key, sizeof(key), "v3_k%d_a%d_t%d_s%d_p%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads, E.staging,
-                E.split_req, E.dmax,
+  std::snprintf(key, sizeof(key), "v4_k%d_a%d_t%d_s%d_p%d_T%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads,
+                E.staging, E.split_req, E.tile, E.dmax,
                 static_cast<long long>(njobs), static_cast<unsigned long long>(signature));
   return key;
 }
@@ -528,6 +575,7 @@ extern "C" void pes_default_options(pes_options* opt) {
   opt->autotune = 0;
   opt->staging = 0;
   opt->split = 0;
+  opt->tile = 0;
 }
 
 extern "C" pes_status pes_plan(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n, int32_t d,
@@ -578,7 +626,7 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
   *out = nullptr;
   if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
   if (d < 0) return fail(PES_EINVAL, "d must be >= 0");
-  if (d > 1023) return fail(PES_EUNSUPPORTED_SIZE, "d must be <= 1023");
+  if (d > pes::kMaxDegree) return fail(PES_EUNSUPPORTED_SIZE, "d must be <= " + std::to_string(pes::kMaxDegree));
   pes_options o;
   pes_status s = parse_options(opt, o);
   if (s != PES_OK) return s;
@@ -872,6 +920,7 @@ extern "C" pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info) {
   info->split = plan->ex.split;
   info->complex_series = plan->complex_series ? 1 : 0;
   info->system_P = plan->prog.system_P;
+  info->tile = plan->ex.tile;
   return PES_OK;
 }
 
@@ -950,10 +999,13 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
   B->input_off.assign(static_cast<size_t>(count) + 1, 0);
   B->value_off.assign(static_cast<size_t>(count) + 1, 0);
   B->grad_off.assign(static_cast<size_t>(count) + 1, 0);
-  std::map<std::pair<int32_t, int32_t>, std::vector<int32_t>> classes;  // (arith, threads) -> instances
+  // (arith, threads, tiled) -> instances; the tiled kernel takes the degrees
+  // whose whole series do not fit in shared memory
+  std::map<std::tuple<int32_t, int32_t, int32_t>, std::vector<int32_t>> classes;
+  const int optin = device_optin();
   int64_t prow = 0, qidx = 0;
   for (int32_t b = 0; b < count; ++b) {
-    if (d[b] < 0 || d[b] > 1023) return fail(PES_EINVAL, "instance " + std::to_string(b) + ": bad degree");
+    if (d[b] < 0 || d[b] > pes::kMaxDegree) return fail(PES_EINVAL, "instance " + std::to_string(b) + ": bad degree");
     pes::Supports sup;
     const int32_t* bp = supp_ptr + prow;
     const int32_t* bi = supp_idx ? supp_idx + qidx : nullptr;
@@ -967,9 +1019,11 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     B->grad_off[static_cast<size_t>(b) + 1] = B->grad_off[static_cast<size_t>(b)] + k * n[b] * D1;
     prow += N[b] + 1;
     qidx += sup.ptr.back();
-    const int32_t T = (2 * ((d[b] + 2) / 2) + 31) / 32 * 32;  // default CTA: one lane per coefficient
     const int32_t ar = resolve_arith(k, o.arith, d[b]);
-    classes[{ar, ar == pes::ARITH_INT ? T : 0}].push_back(b);
+    const bool tiled = o.tile > 0 || !whole_series_fits(k, ar, d[b], o.threads, optin);
+    // default CTA: one lane per coefficient within the cap
+    const int32_t T = std::min((2 * ((d[b] + 2) / 2) + 31) / 32 * 32, pes::dag_max_threads(k));
+    classes[std::make_tuple(ar, ar == pes::ARITH_INT && !tiled ? T : 0, tiled ? 1 : 0)].push_back(b);
   }
 
   for (auto& cls : classes) {
@@ -983,13 +1037,14 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
       const int32_t b = G->members[u];
       const int32_t S = pes::series_stride(d[b]);
       const int64_t slots = progs[static_cast<size_t>(b)].n_slots;
-      const int64_t sstride = pes::ws_slot_words(k, cls.first.first, S);
+      const int64_t sstride = pes::ws_slot_words(k, std::get<0>(cls.first), S);
       insts[u] = pes::InstInfo{wsbase, sstride, S, d[b]};
       wsbase += slots * sstride;
     }
     pes_options og = o;
-    og.arith = cls.first.first;
-    og.threads = std::max(o.threads, cls.first.second);
+    og.arith = std::get<0>(cls.first);
+    og.threads = std::max(o.threads, std::get<1>(cls.first));
+    if (std::get<2>(cls.first)) og.tile = o.tile > 0 ? o.tile : pes::kDefaultTile;
     s = G->ex.init(k, og, insts, static_cast<size_t>(wsbase));
     if (s != PES_OK) return s;
 
@@ -1199,6 +1254,7 @@ extern "C" pes_status pes_get_batch_info(pes_batch_t batch, pes_plan_info* info)
   info->arith = E0.arith;
   info->staging = E0.depth;
   info->split = E0.split;
+  for (auto& G : batch->groups) info->tile = std::max(info->tile, G->ex.tile);  // tiled groups, if any
   return PES_OK;
 }
 

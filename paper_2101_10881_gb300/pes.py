@@ -44,7 +44,8 @@ class PesError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("arith", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("with_vjp", ctypes.c_int32), ("timeout_ms", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("staging", ctypes.c_int32), ("split", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("staging", ctypes.c_int32), ("split", ctypes.c_int32),
+                ("tile", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -53,7 +54,8 @@ class PlanInfo(ctypes.Structure):
                 ("vjp_conv_jobs", ctypes.c_int64), ("vjp_corr_jobs", ctypes.c_int64),
                 ("digits", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("arith", ctypes.c_int32), ("staging", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("complex_series", ctypes.c_int32), ("system_P", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("complex_series", ctypes.c_int32), ("system_P", ctypes.c_int32),
+                ("tile", ctypes.c_int32)]
 
     def as_dict(self):
         d = {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "pad"}
@@ -166,7 +168,7 @@ def _ptr(t, shape, name):
 
 
 def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False,
-                 autotune=False, staging=0, split=0):
+                 autotune=False, staging=0, split=0, tile=0):
     o = Options()
     lib().pes_default_options(ctypes.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
@@ -178,6 +180,7 @@ def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_
     o.autotune = int(bool(autotune))
     o.staging = int(staging)
     o.split = int(split)
+    o.tile = int(tile)
     return o
 
 

@@ -105,25 +105,22 @@ def test_ragged_degree_several_tiles(torch, threads):
     assert info["conv_jobs"] == 12 + 3 + 1 + 6 + 9
 
 
-@pytest.mark.parametrize("k,dmax", [(10, 487), (8, 591), (2, 1023)])
+@pytest.mark.parametrize("k,dmax", [(10, 487), (8, 591), (2, 1379)])
 def test_maximum_degree(torch, k, dmax):
-    """The largest degree one job's staging takes in the integer variant (both
-    operand series, their digits and the exchange rows in one CTA's shared
-    memory; the API caps d at 1023), every output coefficient against the
-    oracle; one degree more is rejected."""
+    """The largest degree whose whole operand series one job stages in the
+    integer variant (both series, their digits and the exchange rows in one
+    CTA's shared memory), every output coefficient against the oracle; one
+    degree more goes to the tiled kernel, against the oracle too."""
     rng = np.random.default_rng(4000 + k)
     supp, n = [[0, 1], [1, 2, 3]], 4
-    prob = synth.Problem("dmax", n, dmax, k, supp, random_md(rng, k, (3, dmax + 1)),
-                         random_md(rng, k, (n, dmax + 1)))
-    v, g, plan = run(torch, prob)
-    assert plan.info()["arith_name"] == "int"
-    rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
-    assert normwise_err(v, rv) <= TOL[k]
-    assert normwise_err(g, rg) <= TOL[k]
-    assert normalised(v) and normalised(g)
-    with pytest.raises(pes.PesError) as e:
-        pes.Plan(supp, n, dmax + 1, k)
-    assert e.value.code == 7
+    for d, tile in ((dmax, 0), (dmax + 1, 128)):
+        prob = synth.Problem("dmax", n, d, k, supp, random_md(rng, k, (3, d + 1)), random_md(rng, k, (n, d + 1)))
+        v, g, plan = run(torch, prob)
+        assert plan.info()["arith_name"] == "int" and plan.info()["tile"] == tile
+        rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
+        assert normwise_err(v, rv) <= TOL[k]
+        assert normwise_err(g, rg) <= TOL[k]
+        assert normalised(v) and normalised(g)
 
 
 @pytest.mark.parametrize("threads", [96, 192, 256])
@@ -411,8 +408,12 @@ def test_invalid_arguments(torch):
         pes.Plan([[1, 0]], 2, 4, 2)
     assert e.value.code == 1
     with pytest.raises(pes.PesError) as e:
-        pes.Plan([[0]], 1, 4000, 2)
+        pes.Plan([[0]], 1, 16384, 2)  # above the largest degree
     assert e.value.code == 7
     with pytest.raises(pes.PesError) as e:
-        pes.Plan([[0]], 1, 900, 10)  # beyond the shared-memory staging at k=10
+        pes.Plan([[0, 1]], 2, 900, 10, tile=512)  # 256 pairs per tile: more than 256 lanes at k=10
     assert e.value.code == 7
+    for bad in (12, 20, 2048):
+        with pytest.raises(pes.PesError) as e:
+            pes.Plan([[0, 1]], 2, 40, 2, tile=bad)
+        assert e.value.code == 1
