@@ -59,6 +59,8 @@ def parse_args(argv=None):
                     help="staging depth of the convolution kernel (0: automatic / autotuned)")
     ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4],
                     help="parts per convolution job (0: automatic / autotuned)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="coefficients per output tile of the tiled kernel (0: whole series where they fit)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["p2", "p1", "p3", "sweep", "batch", "batch-small"], default="p2",
@@ -76,6 +78,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--no-complex", action="store_true",
                     help="skip the measurement of the workload with complex series")
+    ap.add_argument("--no-large-degree", action="store_true",
+                    help="skip the measurement of the tiled kernel (p2-like at d=1023, and d=487 with both kernels)")
     ap.add_argument("--no-system", action="store_true",
                     help="skip the measurement of the 64 x 64 system (values and Jacobian in one plan)")
     ap.add_argument("--no-powers", action="store_true",
@@ -342,7 +346,7 @@ def ours_arm(args, world, rank, local):
                              prob.coeff[:, : args.monomials + 1].copy(), prob.inputs)
     plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, arith=args.arith, threads=args.threads,
                     with_vjp=False, profile=True, autotune=not args.no_autotune and args.threads == 0,
-                    staging=args.staging, split=args.split)
+                    staging=args.staging, split=args.split, tile=args.tile)
     info = plan.info()
     C = torch.from_numpy(prob.coeff).to(dev)
     Z = torch.from_numpy(prob.inputs).to(dev)
@@ -483,7 +487,7 @@ def ours_arm(args, world, rank, local):
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],
                  "staging_depth": plan.info()["staging"], "split": plan.info()["split"],
-                 "smem_bytes": plan.info()["smem_bytes"], "digits": info["digits"]},
+                 "smem_bytes": plan.info()["smem_bytes"], "digits": info["digits"], "tile": plan.info()["tile"]},
     }
     if not args.no_autograd:
         out["autograd"] = autograd_measure(args, dev, flush)
@@ -491,6 +495,8 @@ def ours_arm(args, world, rank, local):
         out["powers"] = powers_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     if args.workload == "p2" and not args.no_complex:
         out["complex"] = complex_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
+    if args.workload == "p2" and not args.no_large_degree:
+        out["large_degree"] = large_degree_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     if args.workload == "p2" and not args.no_system:
         out["system"] = system_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     count = 256 if args.batch_count is None else args.batch_count
@@ -689,6 +695,52 @@ def system_measure(args, dev, flush, peak):
             "roofline_frac": (macs / (conv_ms * 1e-3) / 1e12) / peak if peak else None,
             "kernel_ms": conv_ms, "workspace_bytes": info["workspace_bytes"],
             "system_equals_plans_bitwise": bool(same), "launches_system": 4, "launches_plans": 4 * len(plans)}
+
+
+def large_degree_measure(args, dev, flush, peak):
+    """Degrees beyond the whole-series staging: the p2-like polynomial (n=128,
+    128 monomials of 64 variables, k=10) at d=1023, where the tiled kernel
+    runs (tiles of 128 coefficients), and at d=487, the largest degree the
+    whole-series kernel takes, once with each kernel; ms per eval+grad step
+    with CUDA events and an L2 flush between steps."""
+    import numpy as np
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    base = synth.config1(seed=args.seed)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, d, tile in (("d1023_tiled", 1023, 0), ("d487_whole", 487, 0), ("d487_tiled", 487, 128)):
+        rng = np.random.default_rng(args.seed + d)
+        coeff = synth.random_md(rng, base.k, (base.N + 1, d + 1))
+        inputs = synth.random_md(rng, base.k, (base.n, d + 1))
+        plan = pes.Plan(base.supports, base.n, d, base.k, with_vjp=False, profile=True, tile=tile)
+        C = torch.from_numpy(coeff).to(dev)
+        Z = torch.from_numpy(inputs).to(dev)
+        times, conv = [], []
+        for it in range(2 + max(2, min(args.steps, 3))):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.eval_grad(C, Z)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= 2:
+                times.append(e0.elapsed_time(e1))
+                conv.append(plan.last_timing()["conv_ms"])
+        plan.check()
+        info = plan.info()
+        ms, cms = statistics.mean(times), statistics.mean(conv)
+        ops = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], d, base.k)
+        macs = digit_fma_flops(info["conv_jobs"], d, info["digits"]) / 2
+        out[name] = {"d": d, "tile": info["tile"], "ms_per_step": ms, "value": ops / (ms * 1e-3) / 1e12,
+                     "unit": UNIT, "kernel_ms": cms,
+                     "roofline_frac": (macs / (cms * 1e-3) / 1e12) / peak if peak else None,
+                     "threads_per_cta": info["threads"], "grid": info["grid"],
+                     "workspace_bytes": info["workspace_bytes"]}
+        del plan, C, Z
+    out["workload"] = "p2-like, n=128, 128 monomials of 64 variables, k=10, random series"
+    out["tiled_over_whole_at_d487"] = out["d487_tiled"]["ms_per_step"] / out["d487_whole"]["ms_per_step"]
+    return out
 
 
 def batch_measure(args, dev, count, small=False):
