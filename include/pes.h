@@ -330,6 +330,14 @@ pes_status pes_jobc_add_terms(const int32_t* supp_ptr, const int32_t* supp_idx, 
 pes_status pes_jobc_add_terms_powers(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
                                      int32_t N, int32_t n, int32_t* add_ptr, int32_t* add_src, int32_t* add_mult,
                                      int64_t cap);
+/* The same for a system (pes_plan_system): output p < P is the value of
+ * polynomial p, output P + p*n + i the Jacobian entry d p / d x_i; *const0
+ * receives the slot of the constant series of polynomial 0 (polynomial p's
+ * is const0 + p); the other slots are those of pes_jobc_jobs_powers on the
+ * concatenated supports.  add_ptr: P + P*n + 1 entries. */
+pes_status pes_jobc_add_terms_system(int32_t P, const int32_t* poly_ptr, const int32_t* supp_ptr,
+                                     const int32_t* supp_idx, const int32_t* supp_exp, int32_t n, int32_t* const0,
+                                     int32_t* add_ptr, int32_t* add_src, int32_t* add_mult, int64_t cap);
 
 /* Self-test of the failure path: runs the convolution kernel on one job that
  * waits for a completion flag nobody sets, with the given bound (ms).  Returns

@@ -1451,6 +1451,26 @@ extern "C" pes_status pes_jobc_add_terms_powers(const int32_t* supp_ptr, const i
   return PES_OK;
 }
 
+extern "C" pes_status pes_jobc_add_terms_system(int32_t P, const int32_t* poly_ptr, const int32_t* supp_ptr,
+                                                const int32_t* supp_idx, const int32_t* supp_exp, int32_t n,
+                                                int32_t* const0, int32_t* add_ptr, int32_t* add_src,
+                                                int32_t* add_mult, int64_t cap) {
+  if (P < 1 || !poly_ptr || poly_ptr[0] != 0) return fail(PES_EINVAL, "bad poly_ptr");
+  for (int32_t p = 0; p < P; ++p)
+    if (poly_ptr[p + 1] < poly_ptr[p]) return fail(PES_EINVAL, "poly_ptr must not decrease");
+  pes::Supports sup;
+  pes_status s = build_supports(supp_ptr, supp_idx, poly_ptr[P], n, sup, supp_exp);
+  if (s != PES_OK) return s;
+  pes::Program1 G = pes::compile_system(sup, std::vector<int32_t>(poly_ptr, poly_ptr + P + 1), 0);
+  if (const0) *const0 = G.const0;
+  if (add_ptr) std::memcpy(add_ptr, G.add_ptr.data(), G.add_ptr.size() * sizeof(int32_t));
+  for (size_t t = 0; t < G.add_src.size() && static_cast<int64_t>(t) < cap; ++t) {
+    if (add_src) add_src[t] = G.add_src[t];
+    if (add_mult) add_mult[t] = G.add_mult[t];
+  }
+  return PES_OK;
+}
+
 extern "C" pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status) {
   if (timeout_ms <= 0 || timeout_ms > 60000) return fail(PES_EINVAL, "timeout_ms must be in (0, 60000]");
   // one monomial x_0 of degree 0: a single job, made to wait on its own flag

@@ -26,7 +26,7 @@ ARITH = {"auto": -1, "fp64": 0, "int": 1}
 
 # every symbol that include/pes.h declares
 EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", "pes_plan_complex", "pes_plan_destroy",
-           "pes_eval_grad", "pes_plan_system", "pes_eval_system",
+           "pes_eval_grad", "pes_plan_system", "pes_eval_system", "pes_jobc_add_terms_system",
            "pes_vjp", "pes_jobc_stats_powers", "pes_jobc_jobs_powers", "pes_jobc_add_terms_powers",
            "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
@@ -118,6 +118,8 @@ def lib():
                 "pes_jobc_stats_powers": (i32, [ip32, ip32, ip32, i32, i32, i32, ip64, ip32, i32]),
                 "pes_jobc_jobs_powers": (i32, [ip32, ip32, ip32, i32, i32, i32, ip32, i64]),
                 "pes_jobc_add_terms_powers": (i32, [ip32, ip32, ip32, i32, i32, ip32, ip32, ip32, i64]),
+                "pes_jobc_add_terms_system": (i32, [i32, ip32, ip32, ip32, ip32, i32, ip32, ip32, ip32, ip32,
+                                                    i64]),
                 "pes_jobc_add_levels": (i32, [ip32, ip32, i32, i32, ip64, i32, ip32]),
                 "pes_jobc_add_terms": (i32, [ip32, ip32, i32, i32, ip32, ip32, i64]),
                 "pes_selftest_timeout": (i32, [i64, ip32]),
@@ -511,6 +513,29 @@ def jobc_add_terms(supports, n, exponents=None):
                                            _ip32(add_ptr), _ip32(add_src), _ip32(add_mult), st["add_terms"]),
            "pes_jobc_add_terms_powers")
     return add_ptr, add_src[: st["add_terms"]], add_mult[: st["add_terms"]]
+
+
+def jobc_add_terms_system(polys, n, exponents=None):
+    """(const0, add_ptr, add_src, add_mult) of a system (pes_jobc_add_terms_system):
+    outputs p < P the values, P + p*n + i the Jacobian entries."""
+    supports = [m for p_ in polys for m in p_]
+    P = len(polys)
+    poly_ptr = np.zeros(P + 1, dtype=np.int32)
+    poly_ptr[1:] = np.cumsum([len(p_) for p_ in polys])
+    flat_ex = [e for pe in exponents for e in pe] if exponents is not None else None
+    cap = jobc_stats(supports, n, exponents=flat_ex)["add_terms"] + P
+    ptr, idx = csr(supports)
+    ex = exponent_array(flat_ex, supports) if flat_ex is not None else None
+    const0 = ctypes.c_int32()
+    add_ptr = np.zeros(P + P * int(n) + 1, dtype=np.int32)
+    add_src = np.zeros(cap, dtype=np.int32)
+    add_mult = np.zeros(cap, dtype=np.int32)
+    _check(lib().pes_jobc_add_terms_system(P, _ip32(poly_ptr), _ip32(ptr), _ip32(idx),
+                                           _ip32(ex) if ex is not None and ex.size else None, int(n),
+                                           ctypes.byref(const0), _ip32(add_ptr), _ip32(add_src), _ip32(add_mult),
+                                           cap), "pes_jobc_add_terms_system")
+    nt = int(add_ptr[-1])
+    return const0.value, add_ptr, add_src[:nt], add_mult[:nt]
 
 
 def selftest_timeout(timeout_ms=500):

@@ -193,3 +193,43 @@ def test_invalid_exponents():
         assert e.value.code == 1
     with pytest.raises(pes.PesError):
         pes.jobc_stats([[0, 1]], 2, paper_layout=True, exponents=[[2, 1]])
+
+
+@pytest.mark.parametrize("powers", [False, True])
+@pytest.mark.parametrize("seed", range(3))
+def test_symbolic_system(seed, powers):
+    """Systems (one job table for P polynomials): output p is polynomial p's
+    constant plus its monomials' value terms, output P + p*n + i its partial
+    for x_i with the exponent as integer factor, and no term of one
+    polynomial lands in another's outputs."""
+    rng = np.random.default_rng(500 + seed)
+    n, P = 6, 4
+    polys = [synth.random_supports(rng, n, int(rng.integers(0, 6)), 1, 4) for _ in range(P)]
+    exps = [[[int(e) for e in rng.integers(1, 4, size=len(s_))] for s_ in p_] for p_ in polys] if powers else None
+    supp = [m for p_ in polys for m in p_]
+    flat_ex = [e for pe in exps for e in pe] if powers else None
+    N = len(supp)
+    content = symbolic(supp, n, exponents=flat_ex) if N else {}
+    const0, add_ptr, add_src, add_mult = pes.jobc_add_terms_system(polys, n, exponents=exps)
+    for p in range(P):
+        content[const0 + p] = Counter([f"c{p}"])
+
+    def terms(o):
+        return sorted((tuple(sorted(content[s_].elements())), int(mu))
+                      for s_, mu in zip(add_src[add_ptr[o]:add_ptr[o + 1]], add_mult[add_ptr[o]:add_ptr[o + 1]]))
+
+    m0 = 0
+    for p, p_ in enumerate(polys):
+        def mono(m, skip=None):
+            out = [f"a{m0 + m + 1}"]
+            for t, v in enumerate(p_[m]):
+                e = exps[p][m][t] if powers else 1
+                out += [f"z{v}"] * (e - (1 if v == skip else 0))
+            return tuple(sorted(out))
+
+        assert terms(p) == sorted([((f"c{p}",), 1)] + [(mono(m), 1) for m in range(len(p_))])
+        for i in range(n):
+            want = sorted((mono(m, i), exps[p][m][t] if powers else 1)
+                          for m in range(len(p_)) for t, v in enumerate(p_[m]) if v == i)
+            assert terms(P + p * n + i) == want
+        m0 += len(p_)
