@@ -852,7 +852,9 @@ def sweep_arm(args, world, rank):
     degree-0 random coefficients, inputs z_i = exp(a_i t): for every k x d cell,
     forward (64 value series) and autograd backward of L = sum_p sum_j v_pj^2
     with respect to the shared inputs and all coefficients; closed-form check of
-    the values of two polynomials per cell."""
+    the values of two polynomials per cell; and the 64 polynomials as one
+    system plan (values and the 64 x 64 Jacobian in one launch), timed and
+    compared bit for bit with the per-polynomial values."""
     import torch
     from paper_2101_10881_gb300 import pes, synth
     from paper_2101_10881_gb300.autograd import poly_eval
@@ -892,18 +894,35 @@ def sweep_arm(args, world, rank):
             for q in (0, 1):
                 supp, c = sysc.polys[q]
                 errs.append(closed_form_err(supp, c, sysc.avals, vs[q].detach().cpu().numpy(), 53 * k + 64))
+            # the same 64 polynomials as one system plan: values and the 64 x 64
+            # Jacobian in one launch, bit for bit the per-polynomial results
+            sysp = pes.System([supp for supp, _ in sysc.polys], sysc.n, d, k)
+            Csys = torch.cat(coeffs, dim=1)
+            st = []
+            for it in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sv, sj = sysp.eval_system(Csys, Zb)
+                e1.record(stream)
+                e1.synchronize()
+                st.append(e0.elapsed_time(e1))
+            sysp.check()
+            sys_same = all(torch.equal(sv[:, q], vs[q].detach()) for q in range(len(vs)))
+            del sysp, Csys, sv, sj
             ops = dp_equiv_ops(conv_jobs, add_jobs, d, k)
             row = {"cell": f"k={k} d={d}", "k": k, "d": d, "forward_ms": fwd, "backward_ms": bwd,
                    "backward_over_forward": bwd / fwd if fwd > 0 else None,
                    "forward_dp_equiv_tflops": ops / (fwd * 1e-3) / 1e12, "conv_jobs": conv_jobs,
                    "closed_form_err": max(errs), "tol": tol[k], "within_tol": max(errs) <= tol[k],
-                   "arith": info[0]["arith_name"]}
+                   "arith": info[0]["arith_name"], "system_values_and_jacobian_ms": min(st),
+                   "system_values_equal_plans_bitwise": bool(sys_same)}
             rows.append(row)
             print(json.dumps(row), flush=True)
             del plans, vs, Cs, Z
             torch.cuda.empty_cache()
     print(json.dumps({"metric": METRIC, "sweep": "64x64 system, k x d", "cells": len(rows),
                       "all_within_tol": all(r["within_tol"] for r in rows),
+                      "system_plan_bitwise_in_every_cell": all(r["system_values_equal_plans_bitwise"] for r in rows),
                       "max_backward_over_forward": max(r["backward_over_forward"] or 0 for r in rows)}), flush=True)
     return 0
 
