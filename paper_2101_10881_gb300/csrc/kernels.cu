@@ -235,11 +235,14 @@ struct DigitMac {
 
   // acc += the term x_ix * y_iy of an output coefficient whose grid lies delta
   // digits above the term's: the products of digits p of x and q of y with
-  // p + delta + q < L (digit positions below the grid's L digits are dropped)
+  // p + delta + q < L (digit positions below the grid's L digits are dropped).
+  // The reference grid is the largest of the coefficient's terms, so delta >= 0;
+  // the unsigned compare also skips a negative delta, which would address
+  // outside the X row.
   __device__ __forceinline__ static void term(const DigitT* xdig, const DigitT* ydig, int ix, int iy, int delta,
                                               AccT (&A)[L]) {
     if constexpr (INTV) {
-      if (delta < L) {
+      if (static_cast<unsigned>(delta) < static_cast<unsigned>(L)) {
         // zero prefix: digit p of the shifted term is xs[p], no select
         const int32_t* xs = xdig + ix * XS + XOFF - delta;
         const int4* y4 = reinterpret_cast<const int4*>(ydig + iy * YS);
@@ -260,7 +263,7 @@ struct DigitMac {
         }
       }
     } else {
-      if (delta < L) {
+      if (static_cast<unsigned>(delta) < static_cast<unsigned>(L)) {
         const DigitT* yr = ydig + iy * YS;
         const DigitT* xr = xdig + ix * XS;
         DigitT Y[L];
