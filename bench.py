@@ -484,6 +484,8 @@ def ours_arm(args, world, rank, local):
             "unit": UNIT,
             "rule": "the paper's count: (d+1)^2 k-double multiplications and d(d+1) additions per convolution"},
         "wall_s_timed_region": wall,
+        "step_ms_spread": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms),
+                           "steps": len(step_ms)},
         "plan": {"conv_jobs": info["conv_jobs"], "layers": info["layers"], "add_jobs": info["add_jobs"],
                  "grid": plan.info()["grid"], "threads_per_cta": plan.info()["threads"],
                  "staging_depth": plan.info()["staging"], "split": plan.info()["split"],
@@ -672,6 +674,24 @@ def system_measure(args, dev, flush, peak):
     sysp.check()
     info = sysp.info()
     v, J = res.pop("sys_out")
+    # autograd through the system plan: forward (values) and backward of
+    # L = sum_p sum_j v_pj^2 (one VJP, one upstream series per polynomial)
+    from paper_2101_10881_gb300.autograd import poly_eval
+    fb = []
+    for it in range(3):
+        Cg, Zg = C.clone().requires_grad_(True), Z.clone().requires_grad_(True)
+        flush.fill_(1)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        vv = poly_eval(Cg, Zg, sysp)
+        e1.record(stream)
+        vv.backward(2 * vv.detach())
+        e2.record(stream)
+        e2.synchronize()
+        if it >= 1:
+            fb.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    sysp.check()
+    del Cg, Zg, vv
     plans = [pes.Plan(s_, sysc.n, sysc.d, sysc.k, with_vjp=False) for s_ in polys]
     Cs = [torch.from_numpy(c).to(dev) for _, c in sysc.polys]
     outs = [None] * len(plans)
@@ -694,7 +714,11 @@ def system_measure(args, dev, flush, peak):
             "conv_jobs": info["conv_jobs"], "jacobian_layout": "matrix [k][d+1][P][n]",
             "roofline_frac": (macs / (conv_ms * 1e-3) / 1e12) / peak if peak else None,
             "kernel_ms": conv_ms, "workspace_bytes": info["workspace_bytes"],
-            "system_equals_plans_bitwise": bool(same), "launches_system": 4, "launches_plans": 4 * len(plans)}
+            "system_equals_plans_bitwise": bool(same), "launches_system": 4, "launches_plans": 4 * len(plans),
+            "autograd": {"forward_ms": statistics.mean(t[0] for t in fb),
+                         "backward_ms": statistics.mean(t[1] for t in fb),
+                         "backward_over_forward": statistics.mean(t[1] for t in fb) / statistics.mean(t[0] for t in fb),
+                         "loss": "sum_p sum_j v_pj^2, one VJP through the system plan"}}
 
 
 def large_degree_measure(args, dev, flush, peak):
@@ -854,7 +878,8 @@ def sweep_arm(args, world, rank):
     with respect to the shared inputs and all coefficients; closed-form check of
     the values of two polynomials per cell; and the 64 polynomials as one
     system plan (values and the 64 x 64 Jacobian in one launch), timed and
-    compared bit for bit with the per-polynomial values."""
+    compared bit for bit with the per-polynomial values, and the same forward
+    and backward through the system plan."""
     import torch
     from paper_2101_10881_gb300 import pes, synth
     from paper_2101_10881_gb300.autograd import poly_eval
@@ -898,7 +923,7 @@ def sweep_arm(args, world, rank):
             # Jacobian in one launch, bit for bit the per-polynomial results
             sysp = pes.System([supp for supp, _ in sysc.polys], sysc.n, d, k)
             Csys = torch.cat(coeffs, dim=1)
-            st = []
+            st, sfb = [], []
             for it in range(3):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -906,16 +931,32 @@ def sweep_arm(args, world, rank):
                 e1.record(stream)
                 e1.synchronize()
                 st.append(e0.elapsed_time(e1))
-            sysp.check()
             sys_same = all(torch.equal(sv[:, q], vs[q].detach()) for q in range(len(vs)))
-            del sysp, Csys, sv, sj
+            # forward and backward of the same loss through the system plan: one
+            # VJP with one upstream series per polynomial, the input gradient
+            # summed over the polynomials exactly (autograd through 64 plans
+            # adds the 64 input gradients limb by limb instead)
+            for it in range(3):
+                Zs = Zb.clone().requires_grad_(True)
+                Cq = Csys.clone().requires_grad_(True)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                v_sys = poly_eval(Cq, Zs, sysp)
+                e1.record(stream)
+                v_sys.backward(2 * v_sys.detach())
+                e2.record(stream)
+                e2.synchronize()
+                sfb.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+            sysp.check()
+            del sysp, Csys, sv, sj, v_sys, Zs, Cq
             ops = dp_equiv_ops(conv_jobs, add_jobs, d, k)
             row = {"cell": f"k={k} d={d}", "k": k, "d": d, "forward_ms": fwd, "backward_ms": bwd,
                    "backward_over_forward": bwd / fwd if fwd > 0 else None,
                    "forward_dp_equiv_tflops": ops / (fwd * 1e-3) / 1e12, "conv_jobs": conv_jobs,
                    "closed_form_err": max(errs), "tol": tol[k], "within_tol": max(errs) <= tol[k],
                    "arith": info[0]["arith_name"], "system_values_and_jacobian_ms": min(st),
-                   "system_values_equal_plans_bitwise": bool(sys_same)}
+                   "system_values_equal_plans_bitwise": bool(sys_same),
+                   "system_forward_ms": min(t[0] for t in sfb), "system_backward_ms": min(t[1] for t in sfb)}
             rows.append(row)
             print(json.dumps(row), flush=True)
             del plans, vs, Cs, Z

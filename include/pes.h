@@ -143,7 +143,8 @@ pes_status pes_plan_complex(const int32_t* supp_ptr, const int32_t* supp_idx, co
  * the input series and one job table; the products of every monomial are the
  * ones its own plan would compute, so every output is bit-identical to a plan
  * of that polynomial alone.  Evaluate with pes_eval_system (pes_eval_grad is
- * pes_eval_system with PES_LAYOUT_SERIES).  There are no VJP tables.
+ * pes_eval_system with PES_LAYOUT_SERIES); pes_vjp takes one upstream series
+ * per polynomial.
  *   P >= 1, poly_ptr: P+1 non-decreasing entries, poly_ptr[0] == 0.
  * Errors as pes_plan_ex, and PES_EINVAL for a bad poly_ptr. */
 pes_status pes_plan_system(int32_t P, const int32_t* poly_ptr, const int32_t* supp_ptr, const int32_t* supp_idx,
@@ -184,11 +185,19 @@ pes_status pes_eval_system(pes_plan_t plan, const double* coeff, const double* i
  *   grad_coeff[m]_j = sum_{l=j..d} u_l M_m[l-j],  M_m = prod_{i in S_m} z_i,
  *   grad_input[i]_j = sum_{l=j..d} u_l g_i[l-j],  g_i = d p / d x_i,
  * i.e. truncated correlations (transposed convolutions) of u with the monomial
- * products and with the gradient series; exact because every variable has
- * exponent 1, so v is affine in each input series and each coefficient series.
+ * products and with the gradient series (the derivative of a truncated series
+ * product with respect to one factor is multiplication by the other, whose
+ * transpose is the correlation); for monomials with powers M_m is the product
+ * of the variables with their exponents.
  *   upstream:   device, [k][d+1];
  *   grad_input: device, [k][n][d+1] (written);
  *   grad_coeff: device, [k][N+1][d+1] (written).
+ * On a system plan (pes_plan_system), L = sum_p sum_j u_{p,j} v_{p,j}:
+ *   upstream [k][P][d+1] (one series per polynomial), grad_coeff [k][N+P][d+1]
+ *   in the layout of the coefficient buffer (the constant of p receives u_p,
+ *   monomial m of p the correlation of u_p with M_m), and grad_input[i] the sum
+ *   over p of the correlations of u_p with the Jacobian series d p / d x_i,
+ *   summed exactly and rounded once.
  * reuse_forward = 1: the plan's workspace still holds the forward, backward and
  * cross products of the last pes_eval_grad call on this plan with the same
  * coeff and input (no other call in between); only the correlations and the

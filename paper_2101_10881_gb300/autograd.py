@@ -15,6 +15,11 @@ product by truncated correlations (transposed convolutions):
 with M_m the product of the variables of monomial m and g_i = dp/dx_i; exact
 because every variable has exponent 1, so v is affine in each series.
 
+PyTorch adds the gradients of a tensor that feeds several calls limb by limb,
+which is double-precision addition of the limbs, not k-double addition; for
+several polynomials in the same inputs use one pes.System, whose single VJP sums
+the input gradients over the polynomials exactly and rounds once.
+
 Forward products are reused when possible: if no other call ran on the plan
 since the forward, the plan's workspace still holds them; otherwise, if the
 workspace fit `memory_budget` bytes at forward time, a snapshot taken then is
@@ -62,7 +67,9 @@ class PolyEval(torch.autograd.Function):
 
 def poly_eval(coeff, inputs, plan, memory_budget=None):
     """Value series of the polynomial of `plan` at `inputs`, differentiable with
-    respect to `coeff` (k, N+1, d+1) and `inputs` (k, n, d+1)."""
+    respect to `coeff` (k, N+1, d+1) and `inputs` (k, n, d+1).  With a
+    pes.System the values are (k, P, d+1), one series per polynomial, and
+    `coeff` is (k, N+P, d+1)."""
     if not isinstance(plan, pes.Plan):
         raise TypeError("plan must be a paper_2101_10881_gb300.pes.Plan")
     return PolyEval.apply(coeff, inputs, plan, memory_budget)

@@ -295,12 +295,14 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   return P;
 }
 
-Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr, int32_t d) {
-  Program1 P = compile(s, d, false, false);
+Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr, int32_t d, bool with_vjp) {
+  Program1 P = compile(s, d, false, with_vjp);
   const int32_t np = static_cast<int32_t>(poly_ptr.size()) - 1, n = s.n;
   P.system_P = np;
-  P.const0 = P.n_slots;
-  P.n_slots += np;
+  // the constants after every slot of compile's layout (its VJP slots included)
+  P.const0 = with_vjp ? P.n_slots_vjp : P.n_slots;
+  if (with_vjp) P.n_slots_vjp += np;
+  else P.n_slots += np;
   std::vector<std::vector<std::pair<int32_t, int32_t>>> contrib(static_cast<size_t>(np) * (1 + n));
   for (int32_t p = 0; p < np; ++p) {
     contrib[static_cast<size_t>(p)].push_back({P.const0 + p, 1});
@@ -320,6 +322,30 @@ Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr,
     }
     P.add_ptr[o + 1] = static_cast<int32_t>(P.add_src.size());
   }
+  if (!with_vjp) return P;
+
+  // ---- VJP: one upstream series per polynomial; the correlations of u_p with
+  // the monomial products of p and with p's Jacobian series ----
+  int32_t nx = P.n_slots_vjp;
+  P.slot_up0 = nx;
+  nx += np;
+  P.slot_J0 = nx;
+  nx += np * n;
+  P.slot_rJ0 = nx;
+  nx += np * n;
+  P.n_slots_vjp = nx;
+  std::vector<ConvJob> V(P.vjp_jobs.begin(), P.vjp_jobs.begin() + P.vjp_fwd_jobs);  // forward and M_m
+  for (int32_t p = 0; p < np; ++p)
+    for (int32_t m = poly_ptr[static_cast<size_t>(p)]; m < poly_ptr[static_cast<size_t>(p) + 1]; ++m)
+      V.push_back(ConvJob{P.slot_up0 + p, P.mslot[static_cast<size_t>(m)], P.slot_r0 + m, -1, -1, 0, JOB_CORR, 1});
+  for (int32_t p = 0; p < np; ++p)
+    for (int32_t i = 0; i < n; ++i) {
+      const size_t o = static_cast<size_t>(np + p * n + i);
+      if (P.add_ptr[o + 1] > P.add_ptr[o])
+        V.push_back(ConvJob{P.slot_up0 + p, P.slot_J0 + p * n + i, P.slot_rJ0 + p * n + i, -1, -1, 0, JOB_CORR, 1});
+    }
+  P.vjp_jobs = V;
+  P.slot_u = -1;  // the single upstream slot of compile is not used
   return P;
 }
 

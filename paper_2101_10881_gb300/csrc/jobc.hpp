@@ -109,8 +109,11 @@ struct Program1 {
   // per monomial: its terms of the addition stage, (output, slot, factor) with
   // output 0 the value and 1 + i the partial for x_i
   std::vector<std::vector<std::array<int32_t, 3>>> mono_terms;
-  // systems (compile_system): P polynomials, constant term of polynomial p in slot const0 + p
+  // systems (compile_system): P polynomials, constant term of polynomial p in slot const0 + p;
+  // with VJP tables: upstream series u_p in slot_up0 + p, the Jacobian series in digit form
+  // in slot_J0 + p*n + i, their correlations with u_p in slot_rJ0 + p*n + i
   int32_t system_P = 0, const0 = -1;
+  int32_t slot_up0 = -1, slot_J0 = -1, slot_rJ0 = -1;
   // monomials with powers (Sec. 3): series powers z_v^q, common factors and the
   // coefficients a'_m = a_m * prod z_v^(e_v - 1) that the reverse mode uses
   bool has_powers = false;
@@ -136,8 +139,12 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout = false, bool w
 // polynomial p.  The products are those of compile(s, d); the addition stage
 // has P value outputs (the constant term of polynomial p in slot const0 + p,
 // then its monomials) followed by the P x n Jacobian entries, output
-// P + p * n + i = d p_p / d x_i.  No VJP tables.
-Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr, int32_t d);
+// P + p * n + i = d p_p / d x_i.  With VJP tables (for L = sum_p <u_p, v_p>):
+// the forward products and the monomial products M_m of compile(s, d, false,
+// true), then the correlations of u_p with M_m (slot_r0 + m, m in polynomial p)
+// and with every nonempty Jacobian series (slot_rJ0 + p*n + i); the gradient
+// for x_i is the sum over p of the latter.
+Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr, int32_t d, bool with_vjp = false);
 
 // The same polynomial over complex series: every slot s of the real program
 // becomes the pair (2s, 2s + 1) (real, imaginary part), every product

@@ -561,6 +561,7 @@ struct pes_plan_s {
   bool with_vjp = false;
   bool complex_series = false;
   AddTable add_mat;  // systems: values and Jacobian with one P x n matrix per power of t
+  AddTable add_gi;   // systems: grad_input[i] = sum over the polynomials of the correlations
   int64_t ws_bytes = 0;
 };
 
@@ -636,11 +637,11 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
 
   std::unique_ptr<pes_plan_s> P(new (std::nothrow) pes_plan_s());
   if (!P) return fail(PES_ENOMEM, "plan");
-  // complex plans and systems have no VJP tables
-  P->with_vjp = o.with_vjp != 0 && !complex_series && poly_ptr == nullptr;
+  // complex plans have no VJP tables
+  P->with_vjp = o.with_vjp != 0 && !complex_series;
   P->complex_series = complex_series;
   if (poly_ptr != nullptr) {
-    P->prog = pes::compile_system(sup, *poly_ptr, d);
+    P->prog = pes::compile_system(sup, *poly_ptr, d, P->with_vjp);
   } else {
     P->prog = pes::compile(sup, d, false, P->with_vjp);
     if (complex_series) P->prog = pes::complexify(P->prog);
@@ -747,21 +748,52 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_m, monly);
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_corr, corr);
     if (s != PES_OK) return s;
-    // gradient series into workspace slots (digit form)
     std::vector<pes::AddOut> gouts;
-    for (int32_t i = 0; i < n; ++i)
-      gouts.push_back({static_cast<int64_t>(G.slot_g0 + i), 0, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+    std::vector<pes::CopyRow> urow, un;
+    if (np == 0) {
+      // gradient series into workspace slots (digit form)
+      for (int32_t i = 0; i < n; ++i)
+        gouts.push_back({static_cast<int64_t>(G.slot_g0 + i), 0, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
+      urow.push_back({0, D1, 2, 0, G.slot_u, 0});
+      // unpack: grad_coeff (buffer 0) <- u, r_m ; grad_input (buffer 1) <- r_{N+i}
+      un.push_back({0, (N + 1) * D1, 0, 0, G.slot_u, 0});
+      for (int32_t m = 1; m <= N; ++m) un.push_back({m * D1, (N + 1) * D1, 0, 0, G.slot_r0 + m - 1, 0});
+      for (int32_t i = 0; i < n; ++i) un.push_back({i * D1, n * D1, 1, 0, G.slot_r0 + N + i, 0});
+    } else {
+      // system: the nonempty Jacobian series into workspace slots; upstream
+      // [k][P][d+1]; grad_coeff rows as the coefficient buffer (constant of p
+      // <- u_p, monomial m <- r_m); grad_input[i] = sum_p of the correlations
+      // of u_p with the Jacobian series (p, i), summed exactly and rounded once
+      const int64_t cl = static_cast<int64_t>(N + np) * D1;
+      std::vector<pes::AddOut> giouts;
+      std::vector<int32_t> gicontrib;
+      for (int32_t p = 0; p < np; ++p) {
+        urow.push_back({p * D1, np * D1, 2, 0, G.slot_up0 + p, 0});
+        const int32_t m0 = (*poly_ptr)[static_cast<size_t>(p)], m1 = (*poly_ptr)[static_cast<size_t>(p) + 1];
+        un.push_back({static_cast<int64_t>(m0 + p) * D1, cl, 0, 0, G.slot_up0 + p, 0});
+        for (int32_t m = m0; m < m1; ++m) un.push_back({static_cast<int64_t>(m + p + 1) * D1, cl, 0, 0, G.slot_r0 + m, 0});
+        for (int32_t i = 0; i < n; ++i) {
+          const size_t o = static_cast<size_t>(np + p * n + i);
+          if (G.add_ptr[o + 1] > G.add_ptr[o])
+            gouts.push_back({static_cast<int64_t>(G.slot_J0 + p * n + i), 0, 0, 0, G.add_ptr[o], G.add_ptr[o + 1]});
+        }
+      }
+      for (int32_t i = 0; i < n; ++i) {
+        const int32_t c0 = static_cast<int32_t>(gicontrib.size());
+        for (int32_t p = 0; p < np; ++p) {
+          const size_t o = static_cast<size_t>(np + p * n + i);
+          if (G.add_ptr[o + 1] > G.add_ptr[o]) gicontrib.push_back(G.slot_rJ0 + p * n + i);
+        }
+        giouts.push_back({i * D1, n * D1, 0, 0, c0, static_cast<int32_t>(gicontrib.size())});
+      }
+      s = P->ex.make_add(P->add_gi, giouts, gicontrib, insts);
+      if (s != PES_OK) return s;
+    }
     s = P->ex.make_add(P->add_g, gouts, G.add_src, insts, G.add_mult);
     if (s != PES_OK) return s;
-    std::vector<pes::CopyRow> urow{{0, D1, 2, 0, G.slot_u, 0}};
-    P->pack_u.n = 1;
+    P->pack_u.n = static_cast<int32_t>(urow.size());
     s = P->ex.put(&P->pack_u.rows, urow);
     if (s != PES_OK) return s;
-    // unpack: grad_coeff (buffer 0) <- u, r_m ; grad_input (buffer 1) <- r_{N+i}
-    std::vector<pes::CopyRow> un;
-    un.push_back({0, (N + 1) * D1, 0, 0, G.slot_u, 0});
-    for (int32_t m = 1; m <= N; ++m) un.push_back({m * D1, (N + 1) * D1, 0, 0, G.slot_r0 + m - 1, 0});
-    for (int32_t i = 0; i < n; ++i) un.push_back({i * D1, n * D1, 1, 0, G.slot_r0 + N + i, 0});
     P->unpack.n = static_cast<int32_t>(un.size());
     s = P->ex.put(&P->unpack.rows, un);
     if (s != PES_OK) return s;
@@ -848,7 +880,6 @@ extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double
                               double* grad_input, double* grad_coeff, int32_t reuse_forward, void* stream) {
   if (!plan) return fail(PES_EINVAL, "plan is NULL");
   if (plan->complex_series) return fail(PES_EINVAL, "no VJP for complex series");
-  if (plan->prog.system_P > 0) return fail(PES_EINVAL, "no VJP for systems");
   if (!plan->with_vjp) return fail(PES_EINVAL, "plan was built without with_vjp");
   if (!upstream || !grad_input || !grad_coeff || (!reuse_forward && (!coeff || !input)))
     return fail(PES_EINVAL, "NULL buffer");
@@ -871,6 +902,10 @@ extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double
   PES_CUDA(E.run_add(plan->add_g, nullptr, nullptr, st));
   PES_CUDA(E.run_dag(plan->vjp_corr, 1, st));
   PES_CUDA(E.mark(2, st));
+  if (plan->prog.system_P > 0) {
+    PES_CUDA(E.run_add(plan->add_gi, grad_input, nullptr, st));  // sum over the polynomials
+    ++E.last_launches;
+  }
   PES_CUDA(E.mark(3, st));
   PES_CUDA(E.run_unpack(plan->unpack, grad_coeff, grad_input, st));
   PES_CUDA(E.mark(4, st));

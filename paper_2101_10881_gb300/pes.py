@@ -308,7 +308,9 @@ class System(Plan):
     polys: list of P polynomials, each a list of supports (variable-index
     lists); exponents: None or, per polynomial, per monomial, one positive
     exponent per variable.  The coefficient buffer is [k][N+P][d+1]: each
-    polynomial's constant series, then its monomials' coefficient series."""
+    polynomial's constant series, then its monomials' coefficient series.
+    Differentiable through autograd.poly_eval (one upstream series per
+    polynomial)."""
 
     def __init__(self, polys, n, d, k, exponents=None, **opts):
         self.polys = [[list(m) for m in p_] for p_ in polys]
@@ -362,8 +364,8 @@ class System(Plan):
     def eval_grad(self, coeff, inputs, value=None, grad=None, stream=None):
         return self.eval_system(coeff, inputs, "series", value, grad, stream)
 
-    def vjp(self, *a, **kw):
-        raise PesError(1, "System.vjp", "no VJP for systems")
+    # vjp (Plan.vjp): upstream (k, P, d+1), one series per polynomial; returns
+    # grad_input (k, n, d+1) and grad_coeff (k, N+P, d+1)
 
 
 class Batch:

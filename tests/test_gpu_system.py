@@ -1,7 +1,8 @@
 """Systems of polynomials and their Jacobian matrix (the value and Jacobian
 series a Newton step on power series needs) on the GPU, through the C-ABI
 (pes_plan_system / pes_eval_system), against the oracle polynomial by
-polynomial; bit-identity with one plan per polynomial; the two output layouts."""
+polynomial; bit-identity with one plan per polynomial; the two output layouts;
+the VJP with one upstream series per polynomial (pes_vjp, autograd)."""
 import numpy as np
 import pytest
 
@@ -170,8 +171,87 @@ def test_system_full_size_sampled(torch):
         assert truncated_value_err(v[:, :, p], ref) <= TOL[k]
 
 
-def test_system_rejects_vjp(torch):
-    sysp = pes.System([[[0, 1]], [[1]]], 2, 3, 2)
-    with pytest.raises(pes.PesError) as e:
-        pes._check(pes.lib().pes_vjp(sysp.handle, None, None, None, None, None, 1, None), "pes_vjp")
-    assert e.value.code == 1
+def system_vjp(torch, polys, exps, n, coeffs, inputs, u, k, d, **opts):
+    sysp = pes.System(polys, n, d, k, exponents=exps, **opts)
+    C, Z, U = dev(torch, np.concatenate(coeffs, axis=1)), dev(torch, inputs), dev(torch, u)
+    sysp.eval_grad(C, Z)
+    gi, gc = sysp.vjp(C, Z, U, reuse_forward=True)
+    gi2, gc2 = sysp.vjp(C, Z, U, reuse_forward=False)
+    sysp.check()
+    assert torch.equal(gi, gi2) and torch.equal(gc, gc2)
+    return sysp, gi.cpu().numpy(), gc.cpu().numpy()
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_system_vjp_exact_tiny(torch, k):
+    """L = sum_p <u_p, v_p> on a tiny system: grad_input (summed over the
+    polynomials) and grad_coeff against exact rational arithmetic."""
+    from tests.exact import normwise_err_fr, series_fractions, vjp_fr
+    d, n = 5, 4
+    rng = np.random.default_rng(1600 + k)
+    polys = [[[0, 1], [1, 2, 3]], [[2], [0, 3]], [[0, 1, 2, 3]]]
+    coeffs = [random_md(rng, k, (len(p_) + 1, d + 1)) for p_ in polys]
+    inputs = random_md(rng, k, (n, d + 1))
+    u = random_md(rng, k, (len(polys), d + 1))
+    _, gi, gc = system_vjp(torch, polys, None, n, coeffs, inputs, u, k, d)
+    zf = series_fractions(inputs)
+    gin_ref = np.zeros((n, d + 1), dtype=object)
+    row = 0
+    for p, p_ in enumerate(polys):
+        gin, gco = vjp_fr(p_, n, series_fractions(coeffs[p]), zf, series_fractions(u[:, p]))
+        gin_ref = gin_ref + np.array(gin, dtype=object)
+        assert normwise_err_fr(gc[:, row:row + len(p_) + 1], gco) <= TOL[k]
+        row += len(p_) + 1
+    assert normwise_err_fr(gi, gin_ref) <= TOL[k]
+
+
+@pytest.mark.parametrize("powers", [False, True])
+@pytest.mark.parametrize("k", [2, 10])
+def test_system_vjp_matches_oracle(torch, k, powers):
+    """Against the oracle's VJP polynomial by polynomial: grad_coeff rows
+    exactly as each polynomial's own; grad_input the sum over the polynomials
+    (the oracle's per-polynomial results are each rounded, so their exact sum
+    is within P times the tolerance)."""
+    from tests.exact import normwise_err_fr, series_fractions
+    d = 30
+    polys, exps, n, coeffs, inputs = case(k, d, 1700 + k, powers=powers)
+    u = random_md(np.random.default_rng(1701 + k), k, (len(polys), d + 1))
+    _, gi, gc = system_vjp(torch, polys, exps, n, coeffs, inputs, u, k, d)
+    gin_ref = np.zeros((n, d + 1), dtype=object)
+    row = 0
+    for p, p_ in enumerate(polys):
+        ri, rc = O.vjp(p_, n, coeffs[p], inputs, np.ascontiguousarray(u[:, p]), exponents=exps[p] if exps else None)
+        gin_ref = gin_ref + series_fractions(ri)
+        assert normwise_err(gc[:, row:row + len(p_) + 1], rc) <= TOL[k]
+        row += len(p_) + 1
+    assert normwise_err_fr(gi, gin_ref) <= len(polys) * TOL[k]
+
+
+def test_system_autograd_matches_separate_plans(torch):
+    """torch.autograd through a system plan (poly_eval with one upstream
+    series per polynomial) against the same loss through one plan per
+    polynomial: L = sum_p sum_j v_pj^2."""
+    from paper_2101_10881_gb300.autograd import poly_eval
+    from tests.exact import normwise_err_fr, series_fractions
+    k, d = 3, 25
+    polys, _, n, coeffs, inputs = case(k, d, 1800)
+    sysp = pes.System(polys, n, d, k)
+    C = dev(torch, np.concatenate(coeffs, axis=1)).requires_grad_(True)
+    Z = dev(torch, inputs).requires_grad_(True)
+    v = poly_eval(C, Z, sysp)
+    assert v.shape == (k, len(polys), d + 1)
+    v.backward(2 * v.detach())
+    sysp.check()
+    gz_ref = np.zeros((n, d + 1), dtype=object)
+    row = 0
+    for p, p_ in enumerate(polys):
+        plan = pes.Plan(p_, n, d, k)
+        Cp = dev(torch, coeffs[p]).requires_grad_(True)
+        Zp = dev(torch, inputs).requires_grad_(True)
+        vp = poly_eval(Cp, Zp, plan)
+        assert torch.equal(vp.detach(), v.detach()[:, p])
+        vp.backward(2 * vp.detach())
+        assert torch.equal(Cp.grad, C.grad[:, row:row + len(p_) + 1])
+        gz_ref = gz_ref + series_fractions(Zp.grad.cpu().numpy())
+        row += len(p_) + 1
+    assert normwise_err_fr(Z.grad.cpu().numpy(), gz_ref) <= len(polys) * TOL[k]
