@@ -612,6 +612,8 @@ extern "C" pes_status pes_plan_system(int32_t P, const int32_t* poly_ptr, const 
                                       const int32_t* supp_idx, const int32_t* supp_exp, int32_t n, int32_t d,
                                       int32_t k, const pes_options* opt, pes_plan_t* out) {
   if (P < 1 || !poly_ptr) return fail(PES_EINVAL, "a system needs P >= 1 polynomials and poly_ptr");
+  if (n < 1 || static_cast<int64_t>(P) * (n + 1) >= (1LL << 30))
+    return fail(PES_EINVAL, "P x (n + 1) outputs must stay below 2^30");
   if (poly_ptr[0] != 0) return fail(PES_EINVAL, "poly_ptr[0] must be 0");
   for (int32_t p = 0; p < P; ++p)
     if (poly_ptr[p + 1] < poly_ptr[p]) return fail(PES_EINVAL, "poly_ptr must not decrease");
@@ -1491,6 +1493,8 @@ extern "C" pes_status pes_jobc_add_terms_system(int32_t P, const int32_t* poly_p
                                                 int32_t* const0, int32_t* add_ptr, int32_t* add_src,
                                                 int32_t* add_mult, int64_t cap) {
   if (P < 1 || !poly_ptr || poly_ptr[0] != 0) return fail(PES_EINVAL, "bad poly_ptr");
+  if (n < 1 || static_cast<int64_t>(P) * (n + 1) >= (1LL << 30))
+    return fail(PES_EINVAL, "P x (n + 1) outputs must stay below 2^30");
   for (int32_t p = 0; p < P; ++p)
     if (poly_ptr[p + 1] < poly_ptr[p]) return fail(PES_EINVAL, "poly_ptr must not decrease");
   pes::Supports sup;

@@ -255,3 +255,20 @@ def test_system_autograd_matches_separate_plans(torch):
         gz_ref = gz_ref + series_fractions(Zp.grad.cpu().numpy())
         row += len(p_) + 1
     assert normwise_err_fr(Z.grad.cpu().numpy(), gz_ref) <= len(polys) * TOL[k]
+
+
+def test_system_of_constants(torch):
+    """Every polynomial a constant (no monomial at all): values are the
+    constants, the Jacobian is zero, the VJP gives u_p for every constant and
+    a zero input gradient."""
+    k, d, n = 2, 9, 3
+    rng = np.random.default_rng(1900)
+    coeffs = [random_md(rng, k, (1, d + 1)) for _ in range(3)]
+    inputs = random_md(rng, k, (n, d + 1))
+    u = random_md(rng, k, (3, d + 1))
+    sysp, gi, gc = system_vjp(torch, [[], [], []], None, n, coeffs, inputs, u, k, d)
+    v, J = sysp.eval_system(dev(torch, np.concatenate(coeffs, axis=1)), dev(torch, inputs))
+    sysp.check()
+    assert np.array_equal(v.cpu().numpy(), np.concatenate(coeffs, axis=1))
+    assert not J.any() and not gi.any()
+    assert np.array_equal(gc, u)
