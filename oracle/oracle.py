@@ -61,6 +61,7 @@ def _load():
                 "orc_eval_grad_pow": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, c_int],
                 "orc_vjp_pow": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, dp, c_int],
                 "orc_eval_grad_complex": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp],
+                "orc_vjp_complex": [c_int, c_int, c_int, c_int, ip, ip, ip, dp, dp, dp, dp, dp],
                 "orc_threads": [c_int],
                 "orc_conv_many": [c_int, c_int, c_int, dp, dp, dp, c_int],
             }.items():
@@ -203,6 +204,25 @@ def eval_grad_complex(supports, n, coeff, inputs, exponents=None, grad: bool = T
     _check(_load().orc_eval_grad_complex(k, s - 1, N, n, _ip(ptr), _ip(idx), exp_p, _dp(coeff), _dp(inputs),
                                          _dp(value), gp), "eval_grad_complex")
     return (value, g) if grad else value
+
+
+def vjp_complex(supports, n, coeff, inputs, upstream, exponents=None):
+    """(grad_input (2, k, n, d+1), grad_coeff (2, k, N+1, d+1)) of the real loss
+    L = sum_j (Re u_j Re v_j + Im u_j Im v_j), upstream u (2, k, d+1): the
+    derivatives with respect to the real parts (index 0) and the imaginary
+    parts (index 1) of every input and coefficient series."""
+    coeff, inputs, upstream = _f64(coeff), _f64(inputs), _f64(upstream)
+    two, k, n1, s = coeff.shape
+    N = len(supports)
+    assert two == 2 and n1 == N + 1 and inputs.shape == (2, k, n, s) and upstream.shape == (2, k, s)
+    ptr, idx = _supports(supports)
+    ex = _exponents(exponents, supports)
+    exp_p = _ip(ex) if ex is not None else ctypes.POINTER(ctypes.c_int32)()
+    gi = np.empty((2, k, n, s))
+    gc = np.empty((2, k, N + 1, s))
+    _check(_load().orc_vjp_complex(k, s - 1, N, n, _ip(ptr), _ip(idx), exp_p, _dp(coeff), _dp(inputs),
+                                   _dp(upstream), _dp(gi), _dp(gc)), "vjp_complex")
+    return gi, gc
 
 
 def vjp(supports, n, coeff, inputs, upstream, nthreads: int = 0, exponents=None):

@@ -829,6 +829,97 @@ int orc_eval_grad_complex(int k, int d, int N, int n, const int32_t *supp_ptr, c
     return fail ? 3 : 0;
 }
 
+/* r = correlation of u with the conjugate of s, truncated at degree d: for L =
+ * sum_l (Re u_l Re v_l + Im u_l Im v_l) and v_l = sum_{j<=l} s_{l-j} w_j, the
+ * derivatives of L with respect to Re w_j and Im w_j are the real and
+ * imaginary parts of sum_{l>=j} u_l conj(s_{l-j}):
+ *   Re r_j = sum_{l>=j} Re u_l Re s_{l-j} + Im u_l Im s_{l-j},
+ *   Im r_j = sum_{l>=j} Im u_l Re s_{l-j} - Re u_l Im s_{l-j},
+ * each an exact sum rounded once to k limbs. */
+static void ccorr_conj(int k, int d, ccser u, ccser s, cpser r, expn *e)
+{
+    for (int j = 0; j <= d; ++j) {
+        e->m = 0;
+        for (int l = j; l <= d; ++l) {
+            add_product(e, k, u.re + l, u.ls, s.re + (l - j), s.ls);
+            add_product(e, k, u.im + l, u.ls, s.im + (l - j), s.ls);
+        }
+        round_k(e, k, r.re + j, r.ls);
+        e->m = 0;
+        for (int l = j; l <= d; ++l) {
+            add_product(e, k, u.im + l, u.ls, s.re + (l - j), s.ls);
+            sub_product(e, k, u.re + l, u.ls, s.im + (l - j), s.ls);
+        }
+        round_k(e, k, r.im + j, r.ls);
+    }
+}
+
+/*
+ * Vector-Jacobian product over complex series, with the real and imaginary
+ * parts of every series as separate real variables: for the real loss
+ * L = sum_j (Re u_j Re v_j + Im u_j Im v_j) (v the value series of
+ * orc_eval_grad_complex), grad_coeff and grad_input hold dL/dRe and dL/dIm of
+ * every coefficient series and input series as the real and imaginary block:
+ *   grad_coeff[0] = u,  grad_coeff[m] = corr(u, conj(M_m)),  grad_input[i] = corr(u, conj(g_i)),
+ * M_m the product of the variables of monomial m (with their exponents) and
+ * g_i = d p / d x_i (the polynomial is holomorphic in every series, so the
+ * derivative of v with respect to one series is multiplication by g_i or
+ * M_m, and the transpose of multiplication by s is correlation with conj(s)
+ * under this inner product).  upstream [2][k][d+1], grad_input [2][k][n][d+1],
+ * grad_coeff [2][k][N+1][d+1].
+ */
+int orc_vjp_complex(int k, int d, int N, int n, const int32_t *supp_ptr, const int32_t *supp_idx,
+                    const int32_t *supp_exp, const double *coeff, const double *input, const double *upstream,
+                    double *grad_input, double *grad_coeff)
+{
+    if (!valid_k(k) || d < 0 || check_supports(N, n, supp_ptr, supp_idx) ||
+        check_exponents(N, supp_ptr, supp_exp))
+        return 1;
+    const size_t S = (size_t)d + 1;
+    const size_t cstride = (size_t)(N + 1) * S, cimag = (size_t)k * cstride;
+    const size_t istride = (size_t)n * S, iimag = (size_t)k * istride;
+    const size_t blk = (size_t)k * S;
+    double *value = (double *)malloc(sizeof(double) * 2 * blk);
+    double *g = (double *)malloc(sizeof(double) * 2 * (size_t)k * istride);
+    double *prod = (double *)malloc(sizeof(double) * 6 * blk);
+    expn e;
+    if (!value || !g || !prod || !expn_init(&e, 8 * k * k + 64)) {
+        free(value);
+        free(g);
+        free(prod);
+        return 3;
+    }
+    int rc = orc_eval_grad_complex(k, d, N, n, supp_ptr, supp_idx, supp_exp, coeff, input, value, g);
+    if (rc == 0) {
+        ccser cu = {upstream, upstream + blk, S};
+        for (int l = 0; l < k; ++l) { /* dL/da_0 = u */
+            memcpy(grad_coeff + (size_t)l * cstride, upstream + (size_t)l * S, sizeof(double) * S);
+            memcpy(grad_coeff + cimag + (size_t)l * cstride, upstream + blk + (size_t)l * S, sizeof(double) * S);
+        }
+        for (int m = 0; m < N; ++m) {
+            const int32_t *vars = supp_idx + supp_ptr[m];
+            const int32_t *ex = supp_exp ? supp_exp + supp_ptr[m] : NULL;
+            int nv = supp_ptr[m + 1] - supp_ptr[m];
+            /* M_m: the monomial without its coefficient, from 1 */
+            cmonomial_product(k, d, S, coeff, cstride, cimag, input, istride, iimag, vars, ex, nv, 0, -1, prod,
+                              prod + 2 * blk, prod + 4 * blk, &e);
+            ccser cm = {prod, prod + blk, S};
+            cpser r = {grad_coeff + (size_t)(m + 1) * S, grad_coeff + cimag + (size_t)(m + 1) * S, cstride};
+            ccorr_conj(k, d, cu, cm, r, &e);
+        }
+        for (int i = 0; i < n; ++i) {
+            ccser cg = {g + (size_t)i * S, g + iimag + (size_t)i * S, istride};
+            cpser r = {grad_input + (size_t)i * S, grad_input + iimag + (size_t)i * S, istride};
+            ccorr_conj(k, d, cu, cg, r, &e);
+        }
+    }
+    free(value);
+    free(g);
+    free(prod);
+    expn_free(&e);
+    return rc;
+}
+
 /* number of threads the oracle would use for nthreads (for reporting) */
 int orc_threads(int nthreads) { return used_threads(nthreads); }
 

@@ -5,7 +5,10 @@ a complex product as four real ones).
 Checked against exact complex rationals on tiny inputs, the closed forms of
 exp-series inputs with complex rates, the real oracle when every imaginary
 part is zero (bit for bit), and conjugation (conjugate coefficients and inputs
-give the conjugate results, bit for bit)."""
+give the conjugate results, bit for bit).  The VJP over complex series (real
+and imaginary parts as real variables) against exact central differences of
+the real loss, the real VJP at zero imaginary parts, conjugation and rotation
+of the upstream series by i."""
 from fractions import Fraction
 
 import numpy as np
@@ -113,3 +116,76 @@ def test_complex_closed_form_exp_inputs(k):
     # rounding the inputs to k limbs perturbs the value far below the tolerance
     assert normwise_err_fr(v[0], [want_re]) <= TOL[k]
     assert normwise_err_fr(v[1], [want_im]) <= TOL[k]
+
+
+# ---------------------------------------------------------------------------
+# VJP over complex series (real and imaginary parts as real variables)
+# ---------------------------------------------------------------------------
+
+def loss_fr(supp, n, cp, ip, up):
+    """L = sum_j Re u_j Re v_j + Im u_j Im v_j, exactly (exponents one)."""
+    vf, _, _ = eval_grad_complex_fr(supp, None, n, cp, ip)
+    return sum(a * b for a, b in zip(up[0], vf[0])) + sum(a * b for a, b in zip(up[1], vf[1]))
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 10])
+def test_complex_vjp_central_differences_exact(k):
+    """With exponents one the value is affine in every real and imaginary part
+    of every input coefficient and coefficient-series coefficient, so the
+    central difference (L(x + h) - L(x - h)) / 2h of the exact loss is the exact
+    derivative: every component of the oracle's gradients (dL/dRe in block 0,
+    dL/dIm in block 1) against it.  Independent of how the oracle forms the
+    gradient (no conjugate correlation here)."""
+    rng = np.random.default_rng(1200 + k)
+    n, N, d = 3, 3, 3
+    supp, coeff, inputs = complex_case(rng, k, n, N, d)
+    u = np.stack([random_md(rng, k, (d + 1,)), random_md(rng, k, (d + 1,))])
+    gi, gc = O.vjp_complex(supp, n, coeff, inputs, u)
+    cp, ip = pairs(coeff), pairs(inputs)
+    up = (list(series_fractions(u[0])), list(series_fractions(u[1])))
+    h = Fraction(1, 1 << 20)
+    for which, base, grad in (("input", ip, gi), ("coeff", cp, gc)):
+        for s_ in range(len(base)):
+            for part in (0, 1):
+                exact = []
+                for j in range(d + 1):
+                    lo = [(list(a), list(b)) for a, b in base]
+                    hi = [(list(a), list(b)) for a, b in base]
+                    lo[s_][part][j] -= h
+                    hi[s_][part][j] += h
+                    if which == "input":
+                        fd = (loss_fr(supp, n, cp, hi, up) - loss_fr(supp, n, cp, lo, up)) / (2 * h)
+                    else:
+                        fd = (loss_fr(supp, n, hi, ip, up) - loss_fr(supp, n, lo, ip, up)) / (2 * h)
+                    exact.append(fd)
+                assert normwise_err_fr(grad[part][:, s_], [exact]) <= TOL[k], (which, s_, part)
+
+
+def test_complex_vjp_with_zero_imaginary_parts_is_the_real_vjp():
+    k, d, n = 3, 9, 4
+    rng = np.random.default_rng(1210)
+    supp = synth.random_supports(rng, n, 6, 1, 4)
+    coeff = random_md(rng, k, (len(supp) + 1, d + 1))
+    inputs = random_md(rng, k, (n, d + 1))
+    u = random_md(rng, k, (d + 1,))
+    ri, rc = O.vjp(supp, n, coeff, inputs, u)
+    gi, gc = O.vjp_complex(supp, n, np.stack([coeff, 0 * coeff]), np.stack([inputs, 0 * inputs]),
+                           np.stack([u, 0 * u]))
+    assert np.array_equal(gi[0], ri) and np.array_equal(gc[0], rc)
+    assert not gi[1].any() and not gc[1].any()
+
+
+def test_complex_vjp_conjugation_and_rotation():
+    """Conjugating coefficients, inputs and upstream conjugates both gradients;
+    multiplying the upstream by i multiplies them by i (bit for bit)."""
+    k, d, n = 2, 7, 3
+    rng = np.random.default_rng(1220)
+    supp, coeff, inputs = complex_case(rng, k, n, 5, d)
+    u = np.stack([random_md(rng, k, (d + 1,)), random_md(rng, k, (d + 1,))])
+    gi, gc = O.vjp_complex(supp, n, coeff, inputs, u)
+    conj = lambda a: np.stack([a[0], -a[1]])  # noqa: E731
+    hi, hc = O.vjp_complex(supp, n, conj(coeff), conj(inputs), conj(u))
+    assert np.array_equal(hi, conj(gi)) and np.array_equal(hc, conj(gc))
+    iu = np.stack([-u[1], u[0]])
+    ji, jc = O.vjp_complex(supp, n, coeff, inputs, iu)
+    assert np.array_equal(ji, np.stack([-gi[1], gi[0]])) and np.array_equal(jc, np.stack([-gc[1], gc[0]]))
