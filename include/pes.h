@@ -130,7 +130,12 @@ pes_status pes_plan_powers(const int32_t* supp_ptr, const int32_t* supp_idx, con
  * four real ones combined exactly (the real part xr yr - xi yi, the imaginary
  * part xr yi + xi yr); the value and every partial are rounded once per
  * component.  supp_exp may be NULL (exponents 1) or as in pes_plan_powers.
- * There are no VJP tables: pes_vjp returns PES_EINVAL on a complex plan. */
+ * pes_vjp on a complex plan takes upstream [2][k][d+1] and writes
+ * grad_input [2][k][n][d+1] and grad_coeff [2][k][N+1][d+1]: the derivatives of
+ * the real loss L = sum_j (Re u_j Re v_j + Im u_j Im v_j) with respect to the
+ * real parts (first block) and the imaginary parts (second block) of every
+ * series, i.e. the correlations of u with the conjugates of the gradient
+ * series and of the monomial products. */
 pes_status pes_plan_complex(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
                             int32_t n, int32_t d, int32_t k, const pes_options* opt, pes_plan_t* out);
 

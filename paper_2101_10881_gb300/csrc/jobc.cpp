@@ -287,6 +287,8 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   P.n_slots_vjp = nx;
   finalize(V.jobs, nx);
   P.vjp_fwd_jobs = static_cast<int32_t>(V.jobs.size());
+  for (const ConvJob& j : V.jobs)  // the monomial products alone (their list resolves its own deps)
+    if (j.out >= P.slot_M0 && j.out < P.slot_g0) P.vjp_mjobs.push_back(ConvJob{j.in1, j.in2, j.out, -1, -1, 0, j.kind, j.layer});
   for (int32_t m = 0; m < N; ++m)
     V.jobs.push_back(ConvJob{P.slot_u, P.mslot[static_cast<size_t>(m)], P.slot_r0 + m, -1, -1, 0, JOB_CORR, 1});
   for (int32_t i = 0; i < n; ++i)
@@ -358,31 +360,54 @@ Program1 complexify(const Program1& R) {
   C.n_input_slots = 2 * R.n_input_slots;
   auto re = [](int32_t s) { return 2 * s; };
   auto im = [](int32_t s) { return 2 * s + 1; };
-  int32_t next = 2 * R.n_slots;
-  std::vector<int32_t> ready(static_cast<size_t>(next) + 4 * R.jobs.size(), 0);
-  Builder B;
-  int32_t max_layer = 0;
-  auto job = [&](int32_t in1, int32_t in2, int32_t out, int32_t kind) {
-    const int32_t layer = 1 + std::max(ready[static_cast<size_t>(in1)], ready[static_cast<size_t>(in2)]);
-    B.add(in1, in2, out, layer, kind);
-    ready[static_cast<size_t>(out)] = layer;
-    max_layer = std::max(max_layer, layer);
+  const bool vjp = !R.vjp_jobs.empty();
+  // scratch slots after the doubled layout (its VJP slots included)
+  int32_t next = 2 * (vjp ? R.n_slots_vjp : R.n_slots);
+  const size_t bound = static_cast<size_t>(next) + 4 * (R.jobs.size() + R.vjp_jobs.size() + R.vjp_mjobs.size());
+  // Complex form of a list of real jobs, every job in the earliest layer its
+  // operands (within the list) allow: a product x * y becomes xr yr, xi yi,
+  // xr yi, xi yr in four scratch slots and re = xr yr - xi yi, im = xr yi + xi yr;
+  // a correlation of u with s (the VJP) becomes the correlation with conj(s):
+  // re = ur . sr + ui . si, im = ui . sr - ur . si.
+  auto cx = [&](std::vector<ConvJob>::const_iterator b, std::vector<ConvJob>::const_iterator e, int32_t* layers,
+                int32_t* power) {
+    std::vector<int32_t> ready(bound, 0);
+    Builder B;
+    int32_t max_layer = 0;
+    auto job = [&](int32_t in1, int32_t in2, int32_t out, int32_t kind) {
+      const int32_t layer = 1 + std::max(ready[static_cast<size_t>(in1)], ready[static_cast<size_t>(in2)]);
+      B.add(in1, in2, out, layer, kind);
+      ready[static_cast<size_t>(out)] = layer;
+      max_layer = std::max(max_layer, layer);
+    };
+    for (auto it = b; it != e; ++it) {  // producers before consumers
+      const ConvJob& r = *it;
+      const int32_t t = next;
+      next += 4;
+      if (r.kind == JOB_CORR) {
+        job(re(r.in1), re(r.in2), t, JOB_CORR);
+        job(im(r.in1), im(r.in2), t + 1, JOB_CORR);
+        job(im(r.in1), re(r.in2), t + 2, JOB_CORR);
+        job(re(r.in1), im(r.in2), t + 3, JOB_CORR);
+        job(t, t + 1, re(r.out), JOB_ADD);
+        job(t + 2, t + 3, im(r.out), JOB_SUB);
+      } else {
+        job(re(r.in1), re(r.in2), t, JOB_CONV);
+        job(im(r.in1), im(r.in2), t + 1, JOB_CONV);
+        job(re(r.in1), im(r.in2), t + 2, JOB_CONV);
+        job(im(r.in1), re(r.in2), t + 3, JOB_CONV);
+        job(t, t + 1, re(r.out), JOB_SUB);
+        job(t + 2, t + 3, im(r.out), JOB_ADD);
+      }
+      if (power && it - b < R.power_jobs) *power += 6;
+    }
+    finalize(B.jobs, static_cast<int32_t>(bound));
+    if (layers) *layers = max_layer;
+    return B.jobs;
   };
-  for (size_t j = 0; j < R.jobs.size(); ++j) {  // R.jobs: producers before consumers
-    const ConvJob& r = R.jobs[j];
-    const int32_t t = next;
-    next += 4;
-    job(re(r.in1), re(r.in2), t, JOB_CONV);
-    job(im(r.in1), im(r.in2), t + 1, JOB_CONV);
-    job(re(r.in1), im(r.in2), t + 2, JOB_CONV);
-    job(im(r.in1), re(r.in2), t + 3, JOB_CONV);
-    job(t, t + 1, re(r.out), JOB_SUB);
-    job(t + 2, t + 3, im(r.out), JOB_ADD);
-    if (j < static_cast<size_t>(R.power_jobs)) C.power_jobs += 6;
-  }
+  int32_t max_layer = 0;
+  C.jobs = cx(R.jobs.begin(), R.jobs.end(), &max_layer, &C.power_jobs);
   C.n_slots = next;
-  C.jobs = B.jobs;
-  finalize(C.jobs, C.n_slots);
   C.n_layers = max_layer;
   C.layer_ptr.assign(static_cast<size_t>(max_layer) + 1, 0);
   for (const ConvJob& j : C.jobs) C.layer_ptr[static_cast<size_t>(j.layer)]++;
@@ -399,6 +424,22 @@ Program1 complexify(const Program1& R) {
       C.add_ptr[2 * o + part + 1] = static_cast<int32_t>(C.add_src.size());
     }
   }
+  if (!vjp) return C;
+  // VJP: the forward and monomial products, the monomial products alone, and
+  // the correlations, each list layered on its own; the VJP slots keep their
+  // real-layout numbers s (the parts live in 2s and 2s + 1)
+  std::vector<ConvJob> fwdm = cx(R.vjp_jobs.begin(), R.vjp_jobs.begin() + R.vjp_fwd_jobs, nullptr, nullptr);
+  std::vector<ConvJob> corr = cx(R.vjp_jobs.begin() + R.vjp_fwd_jobs, R.vjp_jobs.end(), nullptr, nullptr);
+  C.vjp_mjobs = cx(R.vjp_mjobs.begin(), R.vjp_mjobs.end(), nullptr, nullptr);
+  C.vjp_fwd_jobs = static_cast<int32_t>(fwdm.size());
+  C.vjp_jobs = fwdm;
+  C.vjp_jobs.insert(C.vjp_jobs.end(), corr.begin(), corr.end());
+  C.slot_u = R.slot_u;
+  C.slot_M0 = R.slot_M0;
+  C.mslot = R.mslot;
+  C.slot_g0 = R.slot_g0;
+  C.slot_r0 = R.slot_r0;
+  C.n_slots_vjp = next;
   return C;
 }
 

@@ -127,6 +127,7 @@ struct Program1 {
   int32_t n_slots_vjp = 0;
   std::vector<ConvJob> vjp_jobs;       // forward jobs + M jobs (topological), then correlation jobs
   int32_t vjp_fwd_jobs = 0;            // number of conv jobs before the correlations
+  std::vector<ConvJob> vjp_mjobs;      // the M jobs alone (for a VJP that reuses the forward products)
 };
 
 // Build the eval+grad layout and jobs.  paper_layout=true reproduces the data
@@ -151,8 +152,11 @@ Program1 compile_system(const Supports& s, const std::vector<int32_t>& poly_ptr,
 // x * y becomes four real products xr yr, xi yi, xr yi, xi yr (four scratch
 // slots) and the ADD / SUB jobs re = xr yr - xi yi, im = xr yi + xi yr; the
 // addition stage sums real and imaginary parts separately, output 2o the real
-// and 2o + 1 the imaginary part of output o of the real program.  No VJP
-// tables.  Every job sits in the earliest layer its operands allow.
+// and 2o + 1 the imaginary part of output o of the real program.  With VJP
+// tables in `real`, its correlations of u with s become correlations with
+// conj(s) (the gradient of the real loss sum Re u Re v + Im u Im v with
+// respect to real and imaginary parts); the VJP slot fields keep their
+// real-layout numbers.  Every job sits in the earliest layer its operands allow.
 Program1 complexify(const Program1& real);
 
 // Addition-tree level sizes of the paper's pairwise summation (Sec. 5, read with

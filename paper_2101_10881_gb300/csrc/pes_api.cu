@@ -639,8 +639,7 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
 
   std::unique_ptr<pes_plan_s> P(new (std::nothrow) pes_plan_s());
   if (!P) return fail(PES_ENOMEM, "plan");
-  // complex plans have no VJP tables
-  P->with_vjp = o.with_vjp != 0 && !complex_series;
+  P->with_vjp = o.with_vjp != 0;
   P->complex_series = complex_series;
   if (poly_ptr != nullptr) {
     P->prog = pes::compile_system(sup, *poly_ptr, d, P->with_vjp);
@@ -742,9 +741,7 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
   if (P->with_vjp) {
     std::vector<pes::ConvJob> fwdm(G.vjp_jobs.begin(), G.vjp_jobs.begin() + G.vjp_fwd_jobs);
     std::vector<pes::ConvJob> corr(G.vjp_jobs.begin() + G.vjp_fwd_jobs, G.vjp_jobs.end());
-    std::vector<pes::ConvJob> monly;
-    for (const auto& j : fwdm)
-      if (j.out >= G.slot_M0 && j.out < G.slot_g0) monly.push_back(pes::ConvJob{j.in1, j.in2, j.out, -1, -1, 0, j.kind, j.layer});
+    std::vector<pes::ConvJob> monly = G.vjp_mjobs;
     resolve_local_deps(monly);  // M_m * F_m (monomials with powers) waits for M_m
     s = P->ex.make_joblist(P->vjp_fwd, fwdm);
     if (s == PES_OK) s = P->ex.make_joblist(P->vjp_m, monly);
@@ -752,7 +749,25 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
     if (s != PES_OK) return s;
     std::vector<pes::AddOut> gouts;
     std::vector<pes::CopyRow> urow, un;
-    if (np == 0) {
+    if (complex_series) {
+      // VJP slot s of the real layout holds its parts in 2s and 2s + 1;
+      // upstream, grad_coeff and grad_input are real block then imaginary block
+      for (int32_t i = 0; i < n; ++i)
+        for (int part = 0; part < 2; ++part) {
+          const size_t o = static_cast<size_t>(2 * (1 + i) + part);
+          gouts.push_back({static_cast<int64_t>(2 * (G.slot_g0 + i) + part), 0, 0, 0, G.add_ptr[o], G.add_ptr[o + 1]});
+        }
+      const int64_t uim = static_cast<int64_t>(k) * D1;
+      urow.push_back({0, D1, 2, 0, 2 * G.slot_u, 0});
+      urow.push_back({uim, D1, 2, 0, 2 * G.slot_u + 1, 0});
+      for (int part = 0; part < 2; ++part) {
+        const int64_t co = part ? cim : 0, io = part ? iim : 0;
+        un.push_back({co, (N + 1) * D1, 0, 0, 2 * G.slot_u + part, 0});
+        for (int32_t m = 1; m <= N; ++m)
+          un.push_back({co + m * D1, (N + 1) * D1, 0, 0, 2 * (G.slot_r0 + m - 1) + part, 0});
+        for (int32_t i = 0; i < n; ++i) un.push_back({io + i * D1, n * D1, 1, 0, 2 * (G.slot_r0 + N + i) + part, 0});
+      }
+    } else if (np == 0) {
       // gradient series into workspace slots (digit form)
       for (int32_t i = 0; i < n; ++i)
         gouts.push_back({static_cast<int64_t>(G.slot_g0 + i), 0, 0, 0, G.add_ptr[1 + i], G.add_ptr[2 + i]});
@@ -881,7 +896,6 @@ extern "C" pes_status pes_eval_system(pes_plan_t plan, const double* coeff, cons
 extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double* input, const double* upstream,
                               double* grad_input, double* grad_coeff, int32_t reuse_forward, void* stream) {
   if (!plan) return fail(PES_EINVAL, "plan is NULL");
-  if (plan->complex_series) return fail(PES_EINVAL, "no VJP for complex series");
   if (!plan->with_vjp) return fail(PES_EINVAL, "plan was built without with_vjp");
   if (!upstream || !grad_input || !grad_coeff || (!reuse_forward && (!coeff || !input)))
     return fail(PES_EINVAL, "NULL buffer");

@@ -1,6 +1,8 @@
 """Complex coefficient and input series on the GPU (pes_plan_complex) against
 the oracle: every complex product four real ones combined exactly by add and
-subtract jobs, real and imaginary parts summed separately."""
+subtract jobs, real and imaginary parts summed separately; the VJP (gradients
+with respect to real and imaginary parts, correlations with conjugate series)
+and autograd."""
 import numpy as np
 import pytest
 
@@ -88,10 +90,78 @@ def test_complex_conjugation(torch):
     assert torch.equal(h[0], g[0]) and torch.equal(h[1], -g[1])
 
 
-def test_complex_plan_has_no_vjp(torch):
-    k, d = 2, 5
-    supp, _, n, coeff, inputs = case(k, d, 1280)
+def complex_vjp(torch, plan, coeff, inputs, u):
+    C, Z, U = dev(torch, coeff), dev(torch, inputs), dev(torch, u)
+    plan.eval_grad(C, Z)
+    gi, gc = plan.vjp(C, Z, U, reuse_forward=True)
+    gi2, gc2 = plan.vjp(C, Z, U, reuse_forward=False)
+    plan.check()
+    assert torch.equal(gi, gi2) and torch.equal(gc, gc2)
+    return gi.cpu().numpy(), gc.cpu().numpy()
+
+
+@pytest.mark.parametrize("powers", [False, True])
+@pytest.mark.parametrize("arith", ["int", "fp64"])
+@pytest.mark.parametrize("k", [1, 2, 5, 10])
+def test_complex_vjp_matches_oracle(torch, k, arith, powers):
+    """The derivatives of L = sum_j Re u_j Re v_j + Im u_j Im v_j with respect to
+    the real and imaginary parts of every input and coefficient series
+    (correlations with the conjugate series), with and without reuse of the
+    forward products, against the oracle."""
+    d = 24
+    supp, ex, n, coeff, inputs = case(k, d, 1300 + k, powers=powers)
+    u = np.stack([random_md(np.random.default_rng(1301 + k), k, (d + 1,)),
+                  random_md(np.random.default_rng(1302 + k), k, (d + 1,))])
+    plan = pes.Plan(supp, n, d, k, exponents=ex, complex_series=True, arith=arith)
+    gi, gc = complex_vjp(torch, plan, coeff, inputs, u)
+    ri, rc = O.vjp_complex(supp, n, coeff, inputs, u, exponents=ex)
+    for part in (0, 1):
+        assert normwise_err(gi[part], ri[part]) <= TOL[k]
+        assert normwise_err(gc[part], rc[part]) <= TOL[k]
+
+
+def test_complex_vjp_with_zero_imaginary_parts_is_the_real_vjp(torch):
+    """Zero imaginary parts everywhere: the real parts of the gradients are the
+    real plan's VJP bit for bit, the imaginary parts zero."""
+    k, d = 4, 30
+    supp, _, n, coeff, inputs = case(k, d, 1310)
+    u = random_md(np.random.default_rng(1311), k, (d + 1,))
+    real = pes.Plan(supp, n, d, k)
+    ri, rc = complex_vjp(torch, real, coeff[0], inputs[0], u)
+    cplx = pes.Plan(supp, n, d, k, complex_series=True)
+    gi, gc = complex_vjp(torch, cplx, np.stack([coeff[0], 0 * coeff[0]]), np.stack([inputs[0], 0 * inputs[0]]),
+                         np.stack([u, 0 * u]))
+    assert np.array_equal(gi[0], ri) and np.array_equal(gc[0], rc)
+    assert not gi[1].any() and not gc[1].any()
+
+
+def test_complex_autograd(torch):
+    """torch.autograd through a complex plan (pairs of real tensors): the
+    backward of L = sum of the squares of every real and imaginary part of the
+    value series against the oracle's VJP with u = 2 v."""
+    from paper_2101_10881_gb300.autograd import poly_eval
+    k, d = 3, 20
+    supp, _, n, coeff, inputs = case(k, d, 1320)
     plan = pes.Plan(supp, n, d, k, complex_series=True)
-    with pytest.raises(pes.PesError) as e:
-        plan.vjp(dev(torch, coeff), dev(torch, inputs), dev(torch, np.zeros((2, k, d + 1))))
-    assert e.value.code == 1
+    C = dev(torch, coeff).requires_grad_(True)
+    Z = dev(torch, inputs).requires_grad_(True)
+    v = poly_eval(C, Z, plan)
+    assert v.shape == (2, k, d + 1)
+    v.backward(2 * v.detach())
+    plan.check()
+    ri, rc = O.vjp_complex(supp, n, coeff, inputs, 2 * v.detach().cpu().numpy())
+    for part in (0, 1):
+        assert normwise_err(Z.grad.cpu().numpy()[part], ri[part]) <= TOL[k]
+        assert normwise_err(C.grad.cpu().numpy()[part], rc[part]) <= TOL[k]
+
+
+def test_complex_vjp_tiled_bit_identical(torch):
+    """The tiled kernel (correlation and add / subtract jobs per output tile)
+    gives the whole-series kernel's bits for the complex VJP."""
+    k, d = 2, 61
+    supp, ex, n, coeff, inputs = case(k, d, 1330, powers=True)
+    u = np.stack([random_md(np.random.default_rng(1331), k, (d + 1,)),
+                  random_md(np.random.default_rng(1332), k, (d + 1,))])
+    out = [complex_vjp(torch, pes.Plan(supp, n, d, k, exponents=ex, complex_series=True, tile=t), coeff, inputs, u)
+           for t in (0, 16)]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
