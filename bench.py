@@ -598,7 +598,8 @@ def complex_measure(args, dev, flush, peak):
     monomials of 64 variables, d=152, k=10) with random complex series.  Every
     complex product is 4 real convolutions and 2 series additions (the paper's
     count for a complex multiplication: 4 multiplications and 2 additions);
-    ms per eval+grad step with CUDA events and an L2 flush between steps."""
+    ms per eval+grad step with CUDA events and an L2 flush between steps; and
+    the VJP (gradients with respect to real and imaginary parts) after it."""
     import numpy as np
     import torch
     from paper_2101_10881_gb300 import pes, synth
@@ -606,7 +607,7 @@ def complex_measure(args, dev, flush, peak):
     rng = np.random.default_rng(args.seed + 41)
     coeff = np.stack([prob.coeff, synth.random_md(rng, prob.k, prob.coeff.shape[1:])])
     inputs = np.stack([prob.inputs, synth.random_md(rng, prob.k, prob.inputs.shape[1:])])
-    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, complex_series=True, with_vjp=False, profile=True,
+    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, complex_series=True, profile=True,
                     autotune=not args.no_autotune)
     C = torch.from_numpy(coeff).to(dev)
     Z = torch.from_numpy(inputs).to(dev)
@@ -622,6 +623,19 @@ def complex_measure(args, dev, flush, peak):
         if it >= max(args.warmup, 3):
             times.append(e0.elapsed_time(e1))
             conv.append(plan.last_timing()["conv_ms"])
+    # the VJP of the real loss sum Re u Re v + Im u Im v, reusing the forward
+    # products (the backward of the autograd Function)
+    U = torch.from_numpy(np.stack([synth.random_md(rng, prob.k, (prob.d + 1,)) for _ in range(2)])).to(dev)
+    vjp_ms = []
+    for it in range(3):
+        plan.eval_grad(C, Z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.vjp(C, Z, U, reuse_forward=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= 1:
+            vjp_ms.append(e0.elapsed_time(e1))
     plan.check()
     info = plan.info()
     ms, cms = statistics.mean(times), statistics.mean(conv)
@@ -635,7 +649,8 @@ def complex_measure(args, dev, flush, peak):
             "real_convolutions": products, "series_additions": series_adds,
             "roofline_frac": (macs / (cms * 1e-3) / 1e12) / peak if peak else None,
             "kernel_ms": cms, "threads_per_cta": info["threads"], "arith": info["arith_name"],
-            "workspace_bytes": info["workspace_bytes"]}
+            "workspace_bytes": info["workspace_bytes"],
+            "vjp_ms": statistics.mean(vjp_ms), "vjp_over_forward": statistics.mean(vjp_ms) / ms}
 
 
 def system_measure(args, dev, flush, peak):
