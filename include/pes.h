@@ -265,6 +265,11 @@ pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);
 pes_status pes_plan_batch(int32_t count, const int32_t* n, const int32_t* N, const int32_t* d,
                           const int32_t* supp_ptr, const int32_t* supp_idx, int32_t k, const pes_options* opt,
                           pes_batch_t* out);
+/* The same for monomials with powers (as pes_plan_powers): supp_exp holds one
+ * exponent in [1, 64] per entry of supp_idx (or is NULL: exponents 1). */
+pes_status pes_plan_batch_powers(int32_t count, const int32_t* n, const int32_t* N, const int32_t* d,
+                                 const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                 int32_t k, const pes_options* opt, pes_batch_t* out);
 void pes_batch_destroy(pes_batch_t batch);
 
 /* Offsets (in doubles) of instance b in the concatenated buffers, arrays of

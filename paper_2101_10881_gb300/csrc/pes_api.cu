@@ -1031,6 +1031,13 @@ struct pes_batch_s {
 extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int32_t* N, const int32_t* d,
                                      const int32_t* supp_ptr, const int32_t* supp_idx, int32_t k,
                                      const pes_options* opt, pes_batch_t* out) {
+  return pes_plan_batch_powers(count, n, N, d, supp_ptr, supp_idx, nullptr, k, opt, out);
+}
+
+extern "C" pes_status pes_plan_batch_powers(int32_t count, const int32_t* n, const int32_t* N, const int32_t* d,
+                                            const int32_t* supp_ptr, const int32_t* supp_idx,
+                                            const int32_t* supp_exp, int32_t k, const pes_options* opt,
+                                            pes_batch_t* out) {
   if (!out) return fail(PES_EINVAL, "out is NULL");
   *out = nullptr;
   if (count < 1 || !n || !N || !d || !supp_ptr) return fail(PES_EINVAL, "bad batch arguments");
@@ -1060,7 +1067,8 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     pes::Supports sup;
     const int32_t* bp = supp_ptr + prow;
     const int32_t* bi = supp_idx ? supp_idx + qidx : nullptr;
-    s = build_supports(bp, bi, N[b], n[b], sup);
+    const int32_t* be = supp_exp ? supp_exp + qidx : nullptr;
+    s = build_supports(bp, bi, N[b], n[b], sup, be);
     if (s != PES_OK) return fail(s, "instance " + std::to_string(b) + ": " + g_last_error);
     progs[static_cast<size_t>(b)] = pes::compile(sup, d[b], false, false);
     const int64_t D1 = d[b] + 1;
@@ -1138,7 +1146,7 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
 
     std::vector<pes::CopyRow> rows;
     std::vector<pes::AddOut> outs;
-    std::vector<int32_t> contrib;
+    std::vector<int32_t> contrib, mult;
     for (size_t u = 0; u < ng; ++u) {
       const int32_t b = G->members[u];
       const int32_t iu = static_cast<int32_t>(u);
@@ -1149,6 +1157,7 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
       for (int32_t i = 0; i < n[b]; ++i) rows.push_back({io + i * D1, n[b] * D1, 1, iu, 1 + N[b] + i, 0});
       const int32_t c0 = static_cast<int32_t>(contrib.size());
       contrib.insert(contrib.end(), P.add_src.begin(), P.add_src.end());
+      mult.insert(mult.end(), P.add_mult.begin(), P.add_mult.end());
       outs.push_back({B->value_off[static_cast<size_t>(b)], D1, 0, iu, c0 + P.add_ptr[0], c0 + P.add_ptr[1]});
       for (int32_t i = 0; i < n[b]; ++i)
         outs.push_back({B->grad_off[static_cast<size_t>(b)] + i * D1, n[b] * D1, 1, iu, c0 + P.add_ptr[1 + i],
@@ -1159,7 +1168,7 @@ extern "C" pes_status pes_plan_batch(int32_t count, const int32_t* n, const int3
     }
     G->pack.n = static_cast<int32_t>(rows.size());
     s = G->ex.put(&G->pack.rows, rows);
-    if (s == PES_OK) s = G->ex.make_add(G->add, outs, contrib, insts);
+    if (s == PES_OK) s = G->ex.make_add(G->add, outs, contrib, insts, mult);
     if (s != PES_OK) return s;
     PES_CUDA(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
     PES_CUDA(cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming));

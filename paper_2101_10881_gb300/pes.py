@@ -28,7 +28,8 @@ ARITH = {"auto": -1, "fp64": 0, "int": 1}
 EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", "pes_plan_complex", "pes_plan_destroy",
            "pes_eval_grad", "pes_plan_system", "pes_eval_system", "pes_jobc_add_terms_system",
            "pes_vjp", "pes_jobc_stats_powers", "pes_jobc_jobs_powers", "pes_jobc_add_terms_powers",
-           "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch", "pes_batch_destroy",
+           "pes_workspace_io", "pes_last_timing", "pes_batch_last_timing", "pes_check", "pes_get_plan_info", "pes_plan_batch",
+           "pes_plan_batch_powers", "pes_batch_destroy",
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
            "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_int_peak", "pes_jobc_stats", "pes_jobc_jobs",
            "pes_jobc_add_levels", "pes_jobc_add_terms", "pes_selftest_timeout", "pes_eval_grad_static", "pes_status_string",
@@ -104,6 +105,8 @@ def lib():
                 "pes_get_plan_info": (i32, [vp, ctypes.POINTER(PlanInfo)]),
                 "pes_plan_batch": (i32, [i32, ip32, ip32, ip32, ip32, ip32, i32, ctypes.POINTER(Options),
                                          ctypes.POINTER(vp)]),
+                "pes_plan_batch_powers": (i32, [i32, ip32, ip32, ip32, ip32, ip32, ip32, i32,
+                                                ctypes.POINTER(Options), ctypes.POINTER(vp)]),
                 "pes_batch_destroy": (None, [vp]),
                 "pes_batch_offsets": (i32, [vp, ip64, ip64, ip64, ip64]),
                 "pes_eval_grad_batch": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -371,24 +374,31 @@ class System(Plan):
 class Batch:
     """pes_plan_batch: many polynomials evaluated by one graph-captured launch."""
 
-    def __init__(self, instances, k, **opts):
-        """instances: list of (supports, n, d)."""
+    def __init__(self, instances, k, exponents=None, **opts):
+        """instances: list of (supports, n, d); exponents: None or, per
+        instance, per monomial, one positive exponent per variable."""
         self.k = int(k)
         self.count = len(instances)
         n = np.array([int(t[1]) for t in instances], dtype=np.int32)
         d = np.array([int(t[2]) for t in instances], dtype=np.int32)
         N = np.array([len(t[0]) for t in instances], dtype=np.int32)
-        ptrs, idxs = [], []
-        for supp, _, _ in instances:
+        ptrs, idxs, exs = [], [], []
+        for b, (supp, _, _) in enumerate(instances):
             p, i = csr(supp)
             ptrs.append(p)
             idxs.append(i[: p[-1]])
+            if exponents is not None:
+                exs.append(exponent_array(exponents[b], supp))
         ptr = np.concatenate(ptrs).astype(np.int32)
         idx = np.concatenate(idxs).astype(np.int32) if sum(len(x) for x in idxs) else np.zeros(1, np.int32)
+        ex = None
+        if exponents is not None:
+            ex = np.concatenate(exs).astype(np.int32) if sum(len(x) for x in exs) else np.ones(1, np.int32)
         o = make_options(**opts)
         h = ctypes.c_void_p()
-        _check(lib().pes_plan_batch(self.count, _ip32(n), _ip32(N), _ip32(d), _ip32(ptr), _ip32(idx), self.k,
-                                    ctypes.byref(o), ctypes.byref(h)), "pes_plan_batch")
+        _check(lib().pes_plan_batch_powers(self.count, _ip32(n), _ip32(N), _ip32(d), _ip32(ptr), _ip32(idx),
+                                           _ip32(ex) if ex is not None else None, self.k, ctypes.byref(o),
+                                           ctypes.byref(h)), "pes_plan_batch_powers")
         self._h = h
         self.n, self.N, self.d = n, N, d
         offs = [np.zeros(self.count + 1, dtype=np.int64) for _ in range(4)]

@@ -109,3 +109,39 @@ def test_invalid_exponents_rejected(torch):
         with pytest.raises(pes.PesError) as e:
             pes.Plan([[0, 1]], 2, 4, 2, exponents=bad)
         assert e.value.code == 1
+
+
+def test_batch_with_powers_matches_single_plans(torch):
+    """Batched instances with powers (pes_plan_batch_powers), mixed degrees:
+    every instance equals its own plan bit for bit and the oracle within
+    tolerance."""
+    k = 3
+    rng = np.random.default_rng(970)
+    insts, probs, exps = [], [], []
+    for b, d in enumerate([0, 7, 31, 152, 60]):
+        n = int(rng.integers(3, 7))
+        N = int(rng.integers(1, 7))
+        supp = synth.random_supports(rng, n, N, 1, min(n, 4))
+        ex = [[int(e) for e in rng.integers(1, 4, size=len(s))] for s in supp]
+        probs.append(synth.Problem(f"b{b}", n, d, k, supp, random_md(rng, k, (N + 1, d + 1)),
+                                   random_md(rng, k, (n, d + 1))))
+        insts.append((supp, n, d))
+        exps.append(ex)
+    B = pes.Batch(insts, k, exponents=exps)
+    C = dev(torch, np.concatenate([p.coeff.ravel() for p in probs]))
+    Z = dev(torch, np.concatenate([p.inputs.ravel() for p in probs]))
+    ln = B.lengths()
+    V = torch.empty(ln["value"], dtype=torch.float64, device="cuda")
+    G = torch.empty(ln["grad"], dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        B.eval_grad(C, Z, V, G)
+    B.check()
+    V, G = V.cpu().numpy(), G.cpu().numpy()
+    for b, p in enumerate(probs):
+        plan = pes.Plan(p.supports, p.n, p.d, k, exponents=exps[b], with_vjp=False)
+        sv, sg = plan.eval_grad(dev(torch, p.coeff), dev(torch, p.inputs))
+        v = V[B.value_off[b]:B.value_off[b + 1]].reshape(k, p.d + 1)
+        g = G[B.grad_off[b]:B.grad_off[b + 1]].reshape(k, p.n, p.d + 1)
+        assert np.array_equal(v, sv.cpu().numpy()) and np.array_equal(g, sg.cpu().numpy())
+        rv, rg = O.eval_grad(p.supports, p.n, p.coeff, p.inputs, exponents=exps[b])
+        assert normwise_err(v, rv) <= TOL[k] and normwise_err(g, rg) <= TOL[k]
