@@ -1128,39 +1128,61 @@ __global__ void prologue_kernel(Ctrl* ctrl) {
 // addition stage: warp per output coefficient, exact digit sums, warp shuffles
 // ---------------------------------------------------------------------------
 
-template <int K, bool INTV>
-__global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
+// GROUPED: group_warps warps per output coefficient (block barriers combine
+// them); else one warp per output coefficient and no barrier.
+template <int K, bool INTV, bool GROUPED>
+__device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
   constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
   constexpr int L = digits_for_k(K, B);
   constexpr int RW = row_words(L, INTV);
-  const long long w = static_cast<long long>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (w >= items) return;
-  int lo = 0, hi = a.nouts - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.item_ptr[mid] <= w) lo = mid; else hi = mid - 1;
+  // a group of group_warps warps per output coefficient (outputs with many
+  // contributions spread them over more lanes); every thread reaches the
+  // block barriers, so lanes past the last item only skip the work
+  __shared__ int32_t gm_s[8];
+  __shared__ long long acc_s[8][L];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = GROUPED ? a.group_warps : 1;
+  const int G = gw * 32;
+  const int sw = warp % gw;                  // warp within the group
+  const int gl = sw * 32 + lane;             // lane within the group
+  const long long w = static_cast<long long>(blockIdx.x) * (8 / gw) + warp / gw;
+  const bool valid = w < items;
+  AddOut ao{};
+  int j = 0;
+  InstInfo in{};
+  if (valid) {
+    int lo = 0, hi = a.nouts - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.item_ptr[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    ao = a.outs[lo];
+    j = static_cast<int>(w - a.item_ptr[lo]);
+    in = a.inst[ao.inst];
   }
-  const AddOut ao = a.outs[lo];
-  const int j = static_cast<int>(w - a.item_ptr[lo]);
-  const InstInfo in = a.inst[ao.inst];
   const int32_t* base = a.ws + in.ws_base;
   const long long gofs = static_cast<long long>(in.S) * RW + j;  // grid of coefficient j within a slot
   const long long rofs = static_cast<long long>(j) * RW;         // row of coefficient j within a slot
 
   // common grid: the largest grid of the contributions
   int32_t gmax = 2 * GRID_ZERO;
-  for (int c = ao.cbeg + lane; c < ao.cend; c += 32)
-    gmax = max(gmax, base[static_cast<long long>(a.contrib[c]) * in.ws_sstride + gofs]);
+  if (valid)
+    for (int c = ao.cbeg + gl; c < ao.cend; c += G)
+      gmax = max(gmax, base[static_cast<long long>(a.contrib[c]) * in.ws_sstride + gofs]);
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if constexpr (GROUPED) {
+    if (lane == 0) gm_s[warp] = gmax;
+    __syncthreads();
+    for (int t = 0; t < gw; ++t) gmax = max(gmax, gm_s[warp - sw + t]);
+  }
 
   // every lane sums its contributions' digits, shifted to the common grid
   int64_t acc[L];
 #pragma unroll
   for (int p = 0; p < L; ++p) acc[p] = 0;
-  if (gmax >= -100000) {
-    for (int c = ao.cbeg + lane; c < ao.cend; c += 32) {
+  if (valid && gmax >= -100000) {
+    for (int c = ao.cbeg + gl; c < ao.cend; c += G) {
       const int32_t* slot = base + static_cast<long long>(a.contrib[c]) * in.ws_sstride;
       const int sh = gmax - slot[gofs];  // digits below the common grid's top
       if (sh >= L) continue;               // below the last digit
@@ -1178,7 +1200,17 @@ __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     acc[p] = v;
   }
-  if (lane != 0) return;
+  if constexpr (GROUPED) {
+    if (lane == 0)
+#pragma unroll
+      for (int p = 0; p < L; ++p) acc_s[warp][p] = acc[p];
+    __syncthreads();
+    if (sw == 0 && lane == 0)
+      for (int t = 1; t < gw; ++t)
+#pragma unroll
+        for (int p = 0; p < L; ++p) acc[p] += acc_s[warp + t][p];
+  }
+  if (!valid || gl != 0) return;
   // acc[p] weighs 2^(B (gmax - 1 - p)): word p + 1 of a sum on grid gmax + 1
   int64_t E[L + 1];
   E[0] = 0;
@@ -1207,6 +1239,16 @@ __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
     return;
   }
   from_digits<K, L, B>(E, gmax + 1, dst, ao.dst_lstride);
+}
+
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
+  add_body<K, INTV, false>(a, items);
+}
+
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256) add_kernel_grouped(AddArgs a, long long items) {
+  add_body<K, INTV, true>(a, items);
 }
 
 // ---------------------------------------------------------------------------
@@ -1390,9 +1432,15 @@ cudaError_t launch_unpack(const CopyArgs& a, int k, int arith, cudaStream_t st) 
 
 cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaStream_t st) {
   if (items == 0) return cudaSuccess;
+  if (!(a.group_warps == 1 || a.group_warps == 2 || a.group_warps == 4 || a.group_warps == 8))
+    return cudaErrorInvalidValue;
   const int warps = 8;
-  const unsigned grid = static_cast<unsigned>((items + warps - 1) / warps);
-  PES_DISPATCH_K_ARITH(add_kernel, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
+  const int per_block = warps / a.group_warps;  // output coefficients per block
+  const unsigned grid = static_cast<unsigned>((items + per_block - 1) / per_block);
+  if (a.group_warps > 1)
+    PES_DISPATCH_K_ARITH(add_kernel_grouped, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
+  else
+    PES_DISPATCH_K_ARITH(add_kernel, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
   return cudaGetLastError();
 }
 

@@ -54,6 +54,7 @@ struct AddArgs {
   const InstInfo* inst;
   int32_t* ws;
   double* dst[2];           // k-limb results: caller buffers by selector
+  int32_t group_warps;      // warps that share one output coefficient (1, 2, 4 or 8)
 };
 
 struct CopyArgs {
@@ -88,6 +89,15 @@ int digits_of_k(int k, int arith);
 int ws_row_words(int k, int arith);
 inline int64_t ws_slot_words(int k, int arith, int32_t S) {
   return static_cast<int64_t>(S) * (ws_row_words(k, arith) + 1);
+}
+
+// Warps of the addition kernel that share one output coefficient, from the
+// largest number of contributions of an output: one warp up to 1024 (the
+// block barriers of a group cost more than they save below that), then up to
+// 8 warps for the long sums (the value of a polynomial of thousands of
+// monomials would otherwise be a serial tail of one warp per coefficient).
+inline int32_t add_group_warps(int64_t max_contrib) {
+  return max_contrib > 4096 ? 8 : max_contrib > 2048 ? 4 : max_contrib > 1024 ? 2 : 1;
 }
 
 // Launchers (return cudaError_t of the launch).

@@ -226,6 +226,9 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   aa.ws = ws;
   aa.dst[0] = value;
   aa.dst[1] = grad;
+  int64_t maxc = 0;
+  for (const auto& o : outs) maxc = std::max<int64_t>(maxc, o.cend - o.cbeg);
+  aa.group_warps = pes::add_group_warps(maxc);
 
   const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(static_cast<long long>(per_sm) * nsm,
                                                                                static_cast<long long>(da.njobs))));

@@ -66,6 +66,7 @@ struct AddTable {
   int32_t* mult = nullptr;  // integer factor per contribution (nullptr: all 1)
   int32_t nouts = 0;
   int64_t items = 0;
+  int32_t group_warps = 1;  // warps per output coefficient of the addition kernel
 };
 
 struct CopyTable {
@@ -173,6 +174,9 @@ struct Exec {
   pes_status make_add(AddTable& A, const std::vector<pes::AddOut>& outs, const std::vector<int32_t>& contrib,
                       const std::vector<pes::InstInfo>& insts, const std::vector<int32_t>& mult = {}) {
     A.nouts = static_cast<int32_t>(outs.size());
+    int64_t maxc = 0;
+    for (const auto& o : outs) maxc = std::max<int64_t>(maxc, o.cend - o.cbeg);
+    A.group_warps = pes::add_group_warps(maxc);
     std::vector<int64_t> ip(outs.size() + 1, 0);
     for (size_t o = 0; o < outs.size(); ++o) ip[o + 1] = ip[o] + insts[static_cast<size_t>(outs[o].inst)].d + 1;
     A.items = ip.back();
@@ -314,6 +318,7 @@ struct Exec {
     a.ws = ws;
     a.dst[0] = dst0;
     a.dst[1] = dst1;
+    a.group_warps = A.group_warps;
     return pes::launch_add(a, k, arith, A.items, st);
   }
 
