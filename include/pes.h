@@ -358,8 +358,9 @@ pes_status pes_jobc_add_terms_system(int32_t P, const int32_t* poly_ptr, const i
                                      const int32_t* supp_idx, const int32_t* supp_exp, int32_t n, int32_t* const0,
                                      int32_t* add_ptr, int32_t* add_src, int32_t* add_mult, int64_t cap);
 
-/* Self-test of the failure path: runs the convolution kernel on one job that
- * waits for a completion flag nobody sets, with the given bound (ms).  Returns
+/* Self-test of the failure path: runs the convolution kernel (the whole-series
+ * kernel, then the tiled kernel) on one job that waits for a completion flag
+ * nobody sets, with the given bound (ms).  Returns
  * PES_OK when the kernel gave up on its own and reported PES_ETIMEOUT through
  * the status word (written to *device_status), leaving the context usable. */
 pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status);

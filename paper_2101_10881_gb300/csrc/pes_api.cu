@@ -59,14 +59,19 @@ struct JobList {
   int32_t grid = 0;
 };
 
+// The outputs of an addition stage in two parts: those with at most 1,024
+// contributions (one warp per output coefficient) and the longer sums (several
+// warps per output coefficient, pes::add_group_warps); one launch per
+// nonempty part, both reading the same contribution list.
 struct AddTable {
-  pes::AddOut* outs = nullptr;
-  int64_t* item_ptr = nullptr;
+  pes::AddOut* outs[2] = {nullptr, nullptr};
+  int64_t* item_ptr[2] = {nullptr, nullptr};
+  int32_t nouts[2] = {0, 0};
+  int64_t items[2] = {0, 0};
+  int32_t group_warps[2] = {1, 1};
   int32_t* contrib = nullptr;
   int32_t* mult = nullptr;  // integer factor per contribution (nullptr: all 1)
-  int32_t nouts = 0;
-  int64_t items = 0;
-  int32_t group_warps = 1;  // warps per output coefficient of the addition kernel
+  int64_t total_items() const { return items[0] + items[1]; }
 };
 
 struct CopyTable {
@@ -173,15 +178,27 @@ struct Exec {
   // mult: integer factor of every contribution, or empty when all are 1
   pes_status make_add(AddTable& A, const std::vector<pes::AddOut>& outs, const std::vector<int32_t>& contrib,
                       const std::vector<pes::InstInfo>& insts, const std::vector<int32_t>& mult = {}) {
-    A.nouts = static_cast<int32_t>(outs.size());
-    int64_t maxc = 0;
-    for (const auto& o : outs) maxc = std::max<int64_t>(maxc, o.cend - o.cbeg);
-    A.group_warps = pes::add_group_warps(maxc);
-    std::vector<int64_t> ip(outs.size() + 1, 0);
-    for (size_t o = 0; o < outs.size(); ++o) ip[o + 1] = ip[o] + insts[static_cast<size_t>(outs[o].inst)].d + 1;
-    A.items = ip.back();
-    pes_status s = put(&A.outs, outs);
-    if (s == PES_OK) s = put(&A.item_ptr, ip);
+    std::vector<pes::AddOut> part[2];
+    int64_t maxc[2] = {0, 0};
+    for (const auto& o : outs) {
+      const int64_t c = o.cend - o.cbeg;
+      const int b = pes::add_group_warps(c) > 1 ? 1 : 0;
+      part[b].push_back(o);
+      maxc[b] = std::max(maxc[b], c);
+    }
+    pes_status s = PES_OK;
+    for (int b = 0; b < 2 && s == PES_OK; ++b) {
+      A.nouts[b] = static_cast<int32_t>(part[b].size());
+      A.group_warps[b] = pes::add_group_warps(maxc[b]);
+      std::vector<int64_t> ip(part[b].size() + 1, 0);
+      for (size_t o = 0; o < part[b].size(); ++o)
+        ip[o + 1] = ip[o] + insts[static_cast<size_t>(part[b][o].inst)].d + 1;
+      A.items[b] = ip.back();
+      if (!part[b].empty()) {
+        s = put(&A.outs[b], part[b]);
+        if (s == PES_OK) s = put(&A.item_ptr[b], ip);
+      }
+    }
     if (s == PES_OK) s = put(&A.contrib, contrib);
     const bool ones = std::all_of(mult.begin(), mult.end(), [](int32_t v) { return v == 1; });
     if (s == PES_OK && !ones) s = put(&A.mult, mult);
@@ -307,20 +324,30 @@ struct Exec {
   // sums into caller buffers (rounded to k limbs), or, with dst0 == dst1 ==
   // nullptr, into workspace slots in digit form
   cudaError_t run_add(const AddTable& A, double* dst0, double* dst1, cudaStream_t st) const {
-    pes::AddArgs a{};
-    a.outs = A.outs;
-    a.nouts = A.nouts;
-    a.to_ws = (dst0 == nullptr && dst1 == nullptr) ? 1 : 0;
-    a.item_ptr = A.item_ptr;
-    a.contrib = A.contrib;
-    a.mult = A.mult;
-    a.inst = inst;
-    a.ws = ws;
-    a.dst[0] = dst0;
-    a.dst[1] = dst1;
-    a.group_warps = A.group_warps;
-    return pes::launch_add(a, k, arith, A.items, st);
+    for (int b = 0; b < 2; ++b) {
+      if (A.items[b] == 0) continue;
+      pes::AddArgs a{};
+      a.outs = A.outs[b];
+      a.nouts = A.nouts[b];
+      a.to_ws = (dst0 == nullptr && dst1 == nullptr) ? 1 : 0;
+      a.item_ptr = A.item_ptr[b];
+      a.contrib = A.contrib;
+      a.mult = A.mult;
+      a.inst = inst;
+      a.ws = ws;
+      a.dst[0] = dst0;
+      a.dst[1] = dst1;
+      a.group_warps = A.group_warps[b];
+      cudaError_t e = pes::launch_add(a, k, arith, A.items[b], st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
+
+  // kernels a run_add / run_dag / run_pack / run_unpack call launches
+  static int32_t launches(const AddTable& A) { return (A.items[0] > 0) + (A.items[1] > 0); }
+  static int32_t launches(const JobList& L) { return L.n > 0 ? 1 : 0; }
+  static int32_t launches(const CopyTable& C) { return C.n > 0 ? 1 : 0; }
 
   cudaError_t run_pack(const CopyTable& C, const double* s0, const double* s1, const double* s2,
                        cudaStream_t st) const {
@@ -859,7 +886,7 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
   PES_CUDA(E.run_add(plan->add, value, grad, st));
   PES_CUDA(E.mark(3, st));
   PES_CUDA(E.mark(4, st));
-  E.last_launches = 4;
+  E.last_launches = 1 + Exec::launches(plan->pack) + Exec::launches(plan->fwd) + Exec::launches(plan->add);
   return PES_OK;
 }
 
@@ -894,7 +921,7 @@ extern "C" pes_status pes_eval_system(pes_plan_t plan, const double* coeff, cons
   PES_CUDA(E.run_add(plan->add_mat, value, jac, st));
   PES_CUDA(E.mark(3, st));
   PES_CUDA(E.mark(4, st));
-  E.last_launches = 4;
+  E.last_launches = 1 + Exec::launches(plan->pack) + Exec::launches(plan->fwd) + Exec::launches(plan->add_mat);
   return PES_OK;
 }
 
@@ -912,20 +939,21 @@ extern "C" pes_status pes_vjp(pes_plan_t plan, const double* coeff, const double
     PES_CUDA(E.run_pack(plan->pack_u, nullptr, nullptr, upstream, st));
     PES_CUDA(E.mark(1, st));
     PES_CUDA(E.run_dag(plan->vjp_m, 0, st));
-    E.last_launches = 5 + (plan->vjp_m.n > 0 ? 1 : 0);
+    E.last_launches = 1 + Exec::launches(plan->pack_u) + Exec::launches(plan->vjp_m);
   } else {
     PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
     PES_CUDA(E.run_pack(plan->pack_u, nullptr, nullptr, upstream, st));
     PES_CUDA(E.mark(1, st));
     PES_CUDA(E.run_dag(plan->vjp_fwd, 0, st));
-    E.last_launches = 7;
+    E.last_launches = 1 + Exec::launches(plan->pack) + Exec::launches(plan->pack_u) + Exec::launches(plan->vjp_fwd);
   }
+  E.last_launches += Exec::launches(plan->add_g) + Exec::launches(plan->vjp_corr) + Exec::launches(plan->unpack);
   PES_CUDA(E.run_add(plan->add_g, nullptr, nullptr, st));
   PES_CUDA(E.run_dag(plan->vjp_corr, 1, st));
   PES_CUDA(E.mark(2, st));
   if (plan->prog.system_P > 0) {
     PES_CUDA(E.run_add(plan->add_gi, grad_input, nullptr, st));  // sum over the polynomials
-    ++E.last_launches;
+    E.last_launches += Exec::launches(plan->add_gi);
   }
   PES_CUDA(E.mark(3, st));
   PES_CUDA(E.run_unpack(plan->unpack, grad_coeff, grad_input, st));
@@ -1271,7 +1299,8 @@ extern "C" pes_status pes_eval_grad_batch(pes_batch_t batch, const double* coeff
   PES_CUDA(cudaGraphLaunch(batch->gexec, st));
   if (batch->profile) PES_CUDA(cudaEventRecord(batch->ev[1], st));
   batch->last_launches = 0;
-  for (auto& G : batch->groups) batch->last_launches += 3 + (G->fwd.n > 0 ? 1 : 0);
+  for (auto& G : batch->groups)
+    batch->last_launches += 1 + Exec::launches(G->pack) + Exec::launches(G->fwd) + Exec::launches(G->add);
   return PES_OK;
 }
 
@@ -1540,24 +1569,30 @@ extern "C" pes_status pes_jobc_add_terms_system(int32_t P, const int32_t* poly_p
 
 extern "C" pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status) {
   if (timeout_ms <= 0 || timeout_ms > 60000) return fail(PES_EINVAL, "timeout_ms must be in (0, 60000]");
-  // one monomial x_0 of degree 0: a single job, made to wait on its own flag
+  // one monomial x_0 of degree 0: a single job, made to wait on its own flag,
+  // once in the whole-series kernel and once in the tiled kernel
   const int32_t ptr[2] = {0, 1}, idx[1] = {0};
-  pes_options o;
-  pes_default_options(&o);
-  o.with_vjp = 0;
-  o.timeout_ms = timeout_ms;
-  pes_plan_t P = nullptr;
-  pes_status s = pes_plan_ex(ptr, idx, 1, 1, 0, 1, &o, &P);
-  if (s != PES_OK) return s;
-  std::unique_ptr<pes_plan_s> guard(P);
-  std::vector<pes::ConvJob> jobs = P->prog.jobs;
-  jobs[0].dep1 = 0;  // the job waits for itself: the flag is never set
-  JobList L;
-  s = P->ex.make_joblist(L, jobs);
-  if (s != PES_OK) return s;
-  PES_CUDA(pes::launch_prologue(P->ex.ctrl, nullptr));
-  PES_CUDA(P->ex.run_dag(L, 0, nullptr));
-  pes_status st = P->ex.check(nullptr);
+  pes_status st = PES_OK;
+  for (int32_t tile : {0, 16}) {
+    pes_options o;
+    pes_default_options(&o);
+    o.with_vjp = 0;
+    o.timeout_ms = timeout_ms;
+    o.tile = tile;
+    pes_plan_t P = nullptr;
+    pes_status s = pes_plan_ex(ptr, idx, 1, 1, 0, 1, &o, &P);
+    if (s != PES_OK) return s;
+    std::unique_ptr<pes_plan_s> guard(P);
+    std::vector<pes::ConvJob> jobs = P->prog.jobs;
+    jobs[0].dep1 = 0;  // the job waits for itself: the flag is never set
+    JobList L;
+    s = P->ex.make_joblist(L, jobs);
+    if (s != PES_OK) return s;
+    PES_CUDA(pes::launch_prologue(P->ex.ctrl, nullptr));
+    PES_CUDA(P->ex.run_dag(L, 0, nullptr));
+    st = P->ex.check(nullptr);
+    if (st != PES_ETIMEOUT) break;
+  }
   if (device_status) *device_status = static_cast<int32_t>(st);
   return st == PES_ETIMEOUT ? PES_OK : fail(PES_EINTERNAL, "the wait did not report a timeout");
 }
