@@ -118,7 +118,24 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   const int32_t S = pes::series_stride(d);
   const int64_t D1 = d + 1;
 
-  const int arith = pes::ARITH_FP64;
+  // the integer pipe when the whole series of a job fit its staging (one lane
+  // per coefficient pair within the CTA cap, shared memory within the opt-in
+  // limit), else the FP64 pipe
+  int dev = 0, nsm = 0, optin = 0;
+  STATIC_CUDA(cudaGetDevice(&dev));
+  STATIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  STATIC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int arith = pes::ARITH_FP64;
+  int threads = 128;
+  {
+    const int pairs = (d + 2) / 2;
+    const int t = std::max((pairs + 31) / 32 * 32, std::min((2 * pairs + 31) / 32 * 32, pes::dag_max_threads(k)));
+    if (t <= pes::dag_max_threads(k) &&
+        pes::dag_smem_bytes(k, pes::ARITH_INT, S, d, 1) <= static_cast<size_t>(optin)) {
+      arith = pes::ARITH_INT;
+      threads = t;
+    }
+  }
   const int64_t sstride = pes::ws_slot_words(k, arith, S);
 
   // tables, in host memory first
@@ -163,11 +180,6 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   pes_status s = setup_device(&base);
   if (s != PES_OK) return s;
 
-  int dev = 0, nsm = 0, optin = 0;
-  STATIC_CUDA(cudaGetDevice(&dev));
-  STATIC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  STATIC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int threads = 128;
   const size_t smem = pes::dag_smem_bytes(k, arith, S, d, 1);
   if (smem > static_cast<size_t>(optin)) {
     set_error("degree too large for the shared-memory staging");
