@@ -87,10 +87,11 @@ typedef struct {
   int32_t tile;        /* 0 = automatic: the whole series of a job's operands are staged in shared memory
                           when they fit (integer / FP64 pipe: d <= 487 / 359 at k=10, 591 / 447 at k=8,
                           879 / 607 at k=5, 999 / 815 at k=4, 1159 / 919 at k=3, 1379 / 1231 at k=2,
-                          1535 / 1487 at k=1), else the tiled kernel with tiles of 128 coefficients.  > 0 (a multiple of 8 in [16, 1024]): always the
-                          tiled kernel with tiles of this many coefficients: every job is split into output
-                          tiles, each accumulated tile pair by tile pair from staged tiles of its operands
-                          (any degree up to 16383; the same bits as the whole-series kernel) */
+                          1535 / 1487 at k=1), else the tiled kernel with tiles of 128 coefficients.
+                          > 0 (a multiple of 8 in [16, 1024]): always the tiled kernel with tiles of this
+                          many coefficients: every job is split into output tiles, each accumulated tile
+                          pair by tile pair from staged tiles of its operands (any degree up to 16383; the
+                          same bits as the whole-series kernel) */
 } pes_options;
 
 /* Fill *opt with the defaults. */
