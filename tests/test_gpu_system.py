@@ -272,3 +272,23 @@ def test_system_of_constants(torch):
     assert np.array_equal(v.cpu().numpy(), np.concatenate(coeffs, axis=1))
     assert not J.any() and not gi.any()
     assert np.array_equal(gc, u)
+
+
+def test_system_tiled_bit_identical(torch):
+    """A system through the tiled kernel (forced tiles of 24 coefficients):
+    values, Jacobian in both layouts and the VJP give the whole-series bits."""
+    k, d = 4, 75
+    polys, exps, n, coeffs, inputs = case(k, d, 2000, powers=True)
+    u = random_md(np.random.default_rng(2001), k, (len(polys), d + 1))
+    C, Z, U = dev(torch, np.concatenate(coeffs, axis=1)), dev(torch, inputs), dev(torch, u)
+    out = []
+    for tile in (0, 24):
+        sysp = pes.System(polys, n, d, k, exponents=exps, tile=tile)
+        assert sysp.info()["tile"] == tile
+        v0, J0 = sysp.eval_system(C, Z, "series")
+        v1, J1 = sysp.eval_system(C, Z, "matrix")
+        gi, gc = sysp.vjp(C, Z, U, reuse_forward=True)
+        sysp.check()
+        out.append((v0, J0, v1, J1, gi, gc))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
