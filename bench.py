@@ -296,7 +296,8 @@ def make_workload(args, rank):
 def workload_config(prob, args):
     sizes = sorted({len(s) for s in prob.supports})
     shape = {"p2": "p2-like", "p1": "p1", "p3": "p3"}[args.workload]
-    return {"workload": f"{shape} polynomial n={prob.n} N={prob.N} monomials of {sizes[0] if len(sizes) == 1 else sizes} "
+    vars_ = sizes[0] if len(sizes) == 1 else sizes
+    return {"workload": f"{shape} polynomial n={prob.n} N={prob.N} monomials of {vars_} "
                         f"variables, d={prob.d}, k={prob.k}, value + full gradient per step",
             "autotune": not args.no_autotune and args.threads == 0,
             "global_batch": 1, "seq_len": prob.d + 1, "parallelism": f"replicas x{args.gpus}",

@@ -144,7 +144,8 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   for (int32_t m = 0; m < N; ++m) {
     acoef[static_cast<size_t>(m)] = A(m + 1);
     int32_t np = 0;
-    for (int32_t t = s.ptr[static_cast<size_t>(m)]; t < s.ptr[static_cast<size_t>(m) + 1]; ++t) np += s.exponent(t) >= 2;
+    for (int32_t t = s.ptr[static_cast<size_t>(m)]; t < s.ptr[static_cast<size_t>(m) + 1]; ++t)
+      np += s.exponent(t) >= 2;
     if (np == 0) continue;
     P.has_powers = true;
     for (int32_t c = 0; c + 1 < np; ++c) fchain[static_cast<size_t>(m)].push_back(next++);
@@ -204,7 +205,8 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   P.n_layers = max_layer;
   P.layer_ptr.assign(static_cast<size_t>(max_layer) + 1, 0);
   for (const ConvJob& j : P.jobs) P.layer_ptr[static_cast<size_t>(j.layer)]++;
-  for (int32_t L = 1; L <= max_layer; ++L) P.layer_ptr[static_cast<size_t>(L)] += P.layer_ptr[static_cast<size_t>(L) - 1];
+  for (int32_t L = 1; L <= max_layer; ++L)
+    P.layer_ptr[static_cast<size_t>(L)] += P.layer_ptr[static_cast<size_t>(L) - 1];
 
   // ---- addition stage: value and gradient contributions, monomial order ----
   // every monomial's terms (output, slot, integer factor): the factor of a
@@ -231,7 +233,8 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   std::vector<std::vector<std::pair<int32_t, int32_t>>> contrib(static_cast<size_t>(n) + 1);
   contrib[0].push_back({0, 1});  // a_0
   for (int32_t m = 0; m < N; ++m)
-    for (const auto& t : P.mono_terms[static_cast<size_t>(m)]) contrib[static_cast<size_t>(t[0])].push_back({t[1], t[2]});
+    for (const auto& t : P.mono_terms[static_cast<size_t>(m)])
+      contrib[static_cast<size_t>(t[0])].push_back({t[1], t[2]});
   P.add_ptr.assign(static_cast<size_t>(n) + 2, 0);
   for (size_t o = 0; o < contrib.size(); ++o) P.add_ptr[o + 1] = P.add_ptr[o] + static_cast<int32_t>(contrib[o].size());
   P.add_src.reserve(static_cast<size_t>(P.add_ptr.back()));
@@ -288,7 +291,8 @@ Program1 compile(const Supports& s, int32_t d, bool paper_layout, bool with_vjp)
   finalize(V.jobs, nx);
   P.vjp_fwd_jobs = static_cast<int32_t>(V.jobs.size());
   for (const ConvJob& j : V.jobs)  // the monomial products alone (their list resolves its own deps)
-    if (j.out >= P.slot_M0 && j.out < P.slot_g0) P.vjp_mjobs.push_back(ConvJob{j.in1, j.in2, j.out, -1, -1, 0, j.kind, j.layer});
+    if (j.out >= P.slot_M0 && j.out < P.slot_g0)
+      P.vjp_mjobs.push_back(ConvJob{j.in1, j.in2, j.out, -1, -1, 0, j.kind, j.layer});
   for (int32_t m = 0; m < N; ++m)
     V.jobs.push_back(ConvJob{P.slot_u, P.mslot[static_cast<size_t>(m)], P.slot_r0 + m, -1, -1, 0, JOB_CORR, 1});
   for (int32_t i = 0; i < n; ++i)
@@ -411,7 +415,8 @@ Program1 complexify(const Program1& R) {
   C.n_layers = max_layer;
   C.layer_ptr.assign(static_cast<size_t>(max_layer) + 1, 0);
   for (const ConvJob& j : C.jobs) C.layer_ptr[static_cast<size_t>(j.layer)]++;
-  for (int32_t L = 1; L <= max_layer; ++L) C.layer_ptr[static_cast<size_t>(L)] += C.layer_ptr[static_cast<size_t>(L) - 1];
+  for (int32_t L = 1; L <= max_layer; ++L)
+    C.layer_ptr[static_cast<size_t>(L)] += C.layer_ptr[static_cast<size_t>(L) - 1];
   const size_t nout = R.add_ptr.size() - 1;
   C.add_ptr.assign(2 * nout + 1, 0);
   for (size_t o = 0; o < nout; ++o) {
@@ -447,7 +452,8 @@ std::vector<int64_t> paper_add_levels(const Supports& s) {
   std::vector<int64_t> sizes;
   sizes.push_back(static_cast<int64_t>(s.N) + 1);  // value: a_0 and N forward products
   std::vector<int64_t> deg(static_cast<size_t>(s.n), 0);
-  for (int32_t t = 0; t < (s.N > 0 ? s.ptr[static_cast<size_t>(s.N)] : 0); ++t) deg[static_cast<size_t>(s.idx[static_cast<size_t>(t)])]++;
+  for (int32_t t = 0; t < (s.N > 0 ? s.ptr[static_cast<size_t>(s.N)] : 0); ++t)
+    deg[static_cast<size_t>(s.idx[static_cast<size_t>(t)])]++;
   for (int64_t g : deg) sizes.push_back(g);
   std::vector<int64_t> levels;
   for (;;) {

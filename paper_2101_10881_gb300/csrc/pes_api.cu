@@ -45,7 +45,8 @@ pes_status upload(T** dptr, const std::vector<T>& v) {
   *dptr = nullptr;
   if (v.empty()) return PES_OK;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), v.size() * sizeof(T));
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(PES_ENOMEM, "device tables") : cuda_fail(e, "cudaMalloc");
+  if (e != cudaSuccess)
+    return e == cudaErrorMemoryAllocation ? fail(PES_ENOMEM, "device tables") : cuda_fail(e, "cudaMalloc");
   e = cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
   return PES_OK;
@@ -171,7 +172,8 @@ struct Exec {
       PES_CUDA(cudaMemset(L.flags, 0, sizeof(int32_t) * nf));
     }
     long long cap = static_cast<long long>(blocks_per_sm) * nsm;
-    L.grid = static_cast<int32_t>(std::max<long long>(1, std::min<long long>(cap, static_cast<long long>(L.n) * split)));
+    L.grid = static_cast<int32_t>(
+        std::max<long long>(1, std::min<long long>(cap, static_cast<long long>(L.n) * split)));
     return PES_OK;
   }
 
@@ -820,7 +822,8 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
         urow.push_back({p * D1, np * D1, 2, 0, G.slot_up0 + p, 0});
         const int32_t m0 = (*poly_ptr)[static_cast<size_t>(p)], m1 = (*poly_ptr)[static_cast<size_t>(p) + 1];
         un.push_back({static_cast<int64_t>(m0 + p) * D1, cl, 0, 0, G.slot_up0 + p, 0});
-        for (int32_t m = m0; m < m1; ++m) un.push_back({static_cast<int64_t>(m + p + 1) * D1, cl, 0, 0, G.slot_r0 + m, 0});
+        for (int32_t m = m0; m < m1; ++m)
+          un.push_back({static_cast<int64_t>(m + p + 1) * D1, cl, 0, 0, G.slot_r0 + m, 0});
         for (int32_t i = 0; i < n; ++i) {
           const size_t o = static_cast<size_t>(np + p * n + i);
           if (G.add_ptr[o + 1] > G.add_ptr[o])
