@@ -1517,6 +1517,43 @@ extern "C" pes_status pes_jobc_jobs_powers(const int32_t* supp_ptr, const int32_
   return PES_OK;
 }
 
+extern "C" pes_status pes_jobc_program(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
+                                       int32_t N, int32_t n, int32_t complex_series, int32_t with_vjp,
+                                       int64_t* counts, int32_t* jobs, int32_t* add_ptr, int32_t* add_src,
+                                       int32_t* add_mult) {
+  if (!counts) return fail(PES_EINVAL, "counts is NULL");
+  pes::Supports sup;
+  pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup, supp_exp);
+  if (s != PES_OK) return s;
+  pes::Program1 G = pes::compile(sup, 0, false, with_vjp != 0);
+  if (complex_series) G = pes::complexify(G);
+  counts[0] = static_cast<int64_t>(G.jobs.size());
+  counts[1] = static_cast<int64_t>(G.add_ptr.size()) - 1;
+  counts[2] = static_cast<int64_t>(G.add_src.size());
+  counts[3] = with_vjp ? G.n_slots_vjp : G.n_slots;
+  counts[4] = static_cast<int64_t>(G.vjp_jobs.size());
+  counts[5] = G.vjp_fwd_jobs;
+  counts[6] = G.slot_u;
+  counts[7] = G.slot_g0;
+  counts[8] = G.slot_r0;
+  counts[9] = G.n_input_slots;
+  auto put_job = [&](size_t t, const pes::ConvJob& j) {
+    jobs[5 * t + 0] = j.in1;
+    jobs[5 * t + 1] = j.in2;
+    jobs[5 * t + 2] = j.out;
+    jobs[5 * t + 3] = j.layer;
+    jobs[5 * t + 4] = j.kind;
+  };
+  if (jobs) {
+    for (size_t t = 0; t < G.jobs.size(); ++t) put_job(t, G.jobs[t]);
+    for (size_t t = 0; t < G.vjp_jobs.size(); ++t) put_job(G.jobs.size() + t, G.vjp_jobs[t]);
+  }
+  if (add_ptr) std::memcpy(add_ptr, G.add_ptr.data(), G.add_ptr.size() * sizeof(int32_t));
+  if (add_src) std::memcpy(add_src, G.add_src.data(), G.add_src.size() * sizeof(int32_t));
+  if (add_mult) std::memcpy(add_mult, G.add_mult.data(), G.add_mult.size() * sizeof(int32_t));
+  return PES_OK;
+}
+
 extern "C" pes_status pes_jobc_add_levels(const int32_t* supp_ptr, const int32_t* supp_idx, int32_t N, int32_t n,
                                           int64_t* levels, int32_t cap, int32_t* nlevels) {
   pes::Supports sup;
