@@ -351,21 +351,25 @@ pes_status pes_jobc_add_terms_powers(const int32_t* supp_ptr, const int32_t* sup
                                      int32_t N, int32_t n, int32_t* add_ptr, int32_t* add_src, int32_t* add_mult,
                                      int64_t cap);
 /* The whole program of a plan (host tables, to inspect or interpret them):
- * complex_series 1 for pes_plan_complex, with_vjp 1 to include the VJP tables.
- *   counts[10]: [0] evaluation jobs, [1] addition outputs, [2] addition terms,
+ * complex_series 1 for pes_plan_complex; P > 0 with poly_ptr (as in
+ * pes_plan_system, poly_ptr[P] == N) for a system; with_vjp 1 to include the
+ * VJP tables.
+ *   counts[14]: [0] evaluation jobs, [1] addition outputs, [2] addition terms,
  *   [3] slots, [4] VJP jobs (the forward and monomial products, then the
  *   correlations and, for complex series, their add / subtract jobs), [5] VJP
  *   jobs before the correlations, [6] upstream slot, [7] first gradient slot,
  *   [8] first correlation slot (for complex series these three are numbered as
  *   in the real program, the parts living in 2s and 2s + 1), [9] input slots;
+ *   systems: [10] first constant slot, [11] first upstream slot, [12] first
+ *   Jacobian slot, [13] first slot of the Jacobian correlations (-1 otherwise);
  *   jobs: 5 ints per job (input 1, input 2, output, layer, kind: 0 convolution,
  *   1 correlation, 2 addition, 3 subtraction), the evaluation's jobs then the
  *   VJP's, counts[0] + counts[4] in all; add_ptr (counts[1] + 1), add_src and
  *   add_mult (counts[2]) as pes_jobc_add_terms_powers.
  * NULL arrays are not written (call once with NULL to size them). */
 pes_status pes_jobc_program(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp, int32_t N,
-                            int32_t n, int32_t complex_series, int32_t with_vjp, int64_t* counts, int32_t* jobs,
-                            int32_t* add_ptr, int32_t* add_src, int32_t* add_mult);
+                            int32_t n, int32_t complex_series, int32_t P, const int32_t* poly_ptr, int32_t with_vjp,
+                            int64_t* counts, int32_t* jobs, int32_t* add_ptr, int32_t* add_src, int32_t* add_mult);
 /* The same for a system (pes_plan_system): output p < P is the value of
  * polynomial p, output P + p*n + i the Jacobian entry d p / d x_i; *const0
  * receives the slot of the constant series of polynomial 0 (polynomial p's

@@ -1518,14 +1518,23 @@ extern "C" pes_status pes_jobc_jobs_powers(const int32_t* supp_ptr, const int32_
 }
 
 extern "C" pes_status pes_jobc_program(const int32_t* supp_ptr, const int32_t* supp_idx, const int32_t* supp_exp,
-                                       int32_t N, int32_t n, int32_t complex_series, int32_t with_vjp,
-                                       int64_t* counts, int32_t* jobs, int32_t* add_ptr, int32_t* add_src,
-                                       int32_t* add_mult) {
+                                       int32_t N, int32_t n, int32_t complex_series, int32_t P,
+                                       const int32_t* poly_ptr, int32_t with_vjp, int64_t* counts, int32_t* jobs,
+                                       int32_t* add_ptr, int32_t* add_src, int32_t* add_mult) {
   if (!counts) return fail(PES_EINVAL, "counts is NULL");
+  if (P > 0 && complex_series) return fail(PES_EINVAL, "systems are real");
+  if (P > 0) {
+    if (!poly_ptr || poly_ptr[0] != 0 || poly_ptr[P] != N) return fail(PES_EINVAL, "bad poly_ptr");
+    if (static_cast<int64_t>(P) * (n + 1) >= (1LL << 30)) return fail(PES_EINVAL, "too many outputs");
+    for (int32_t p = 0; p < P; ++p)
+      if (poly_ptr[p + 1] < poly_ptr[p]) return fail(PES_EINVAL, "poly_ptr must not decrease");
+  }
   pes::Supports sup;
   pes_status s = build_supports(supp_ptr, supp_idx, N, n, sup, supp_exp);
   if (s != PES_OK) return s;
-  pes::Program1 G = pes::compile(sup, 0, false, with_vjp != 0);
+  pes::Program1 G = P > 0 ? pes::compile_system(sup, std::vector<int32_t>(poly_ptr, poly_ptr + P + 1), 0,
+                                                with_vjp != 0)
+                          : pes::compile(sup, 0, false, with_vjp != 0);
   if (complex_series) G = pes::complexify(G);
   counts[0] = static_cast<int64_t>(G.jobs.size());
   counts[1] = static_cast<int64_t>(G.add_ptr.size()) - 1;
@@ -1537,6 +1546,10 @@ extern "C" pes_status pes_jobc_program(const int32_t* supp_ptr, const int32_t* s
   counts[7] = G.slot_g0;
   counts[8] = G.slot_r0;
   counts[9] = G.n_input_slots;
+  counts[10] = G.const0;
+  counts[11] = G.slot_up0;
+  counts[12] = G.slot_J0;
+  counts[13] = G.slot_rJ0;
   auto put_job = [&](size_t t, const pes::ConvJob& j) {
     jobs[5 * t + 0] = j.in1;
     jobs[5 * t + 1] = j.in2;

@@ -123,7 +123,8 @@ def lib():
                 "pes_jobc_add_terms_powers": (i32, [ip32, ip32, ip32, i32, i32, ip32, ip32, ip32, i64]),
                 "pes_jobc_add_terms_system": (i32, [i32, ip32, ip32, ip32, ip32, i32, ip32, ip32, ip32, ip32,
                                                     i64]),
-                "pes_jobc_program": (i32, [ip32, ip32, ip32, i32, i32, i32, i32, ip64, ip32, ip32, ip32, ip32]),
+                "pes_jobc_program": (i32, [ip32, ip32, ip32, i32, i32, i32, i32, ip32, i32, ip64, ip32, ip32, ip32,
+                                           ip32]),
                 "pes_jobc_add_levels": (i32, [ip32, ip32, i32, i32, ip64, i32, ip32]),
                 "pes_jobc_add_terms": (i32, [ip32, ip32, i32, i32, ip32, ip32, i64]),
                 "pes_selftest_timeout": (i32, [i64, ip32]),
@@ -551,29 +552,36 @@ def jobc_add_terms_system(polys, n, exponents=None):
     return const0.value, add_ptr, add_src[:nt], add_mult[:nt]
 
 
-def jobc_program(supports, n, exponents=None, complex_series=False, with_vjp=False):
+def jobc_program(supports, n, exponents=None, complex_series=False, with_vjp=False, polys=None):
     """The whole program of a plan as host tables (pes_jobc_program): a dict with
     jobs (rows of in1, in2, out, layer, kind; evaluation then VJP), the addition
-    tables, the slot counts and the VJP slot numbers."""
+    tables, the slot counts and the VJP slot numbers.  polys: for a system, the
+    number of monomials of each polynomial (supports in that order)."""
     ptr, idx = csr(supports)
     ex = exponent_array(exponents, supports) if exponents is not None else None
     exp_p = _ip32(ex) if ex is not None and ex.size else None
-    counts = np.zeros(10, dtype=np.int64)
-    args = (_ip32(ptr), _ip32(idx), exp_p, len(supports), int(n), int(bool(complex_series)), int(bool(with_vjp)))
-    _check(lib().pes_jobc_program(*args, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None, None, None,
-                                  None), "pes_jobc_program")
+    P = 0 if polys is None else len(polys)
+    poly_ptr = np.zeros(P + 1, dtype=np.int32)
+    if P:
+        poly_ptr[1:] = np.cumsum(polys)
+    counts = np.zeros(14, dtype=np.int64)
+    args = (_ip32(ptr), _ip32(idx), exp_p, len(supports), int(n), int(bool(complex_series)), P,
+            _ip32(poly_ptr) if P else None, int(bool(with_vjp)))
+    c64 = counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(lib().pes_jobc_program(*args, c64, None, None, None, None), "pes_jobc_program")
     nj = int(counts[0] + counts[4])
     jobs = np.zeros((max(nj, 1), 5), dtype=np.int32)
     add_ptr = np.zeros(int(counts[1]) + 1, dtype=np.int32)
     add_src = np.zeros(max(int(counts[2]), 1), dtype=np.int32)
     add_mult = np.zeros(max(int(counts[2]), 1), dtype=np.int32)
-    _check(lib().pes_jobc_program(*args, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ip32(jobs),
-                                  _ip32(add_ptr), _ip32(add_src), _ip32(add_mult)), "pes_jobc_program")
+    _check(lib().pes_jobc_program(*args, c64, _ip32(jobs), _ip32(add_ptr), _ip32(add_src), _ip32(add_mult)),
+           "pes_jobc_program")
     ne = int(counts[0])
     return {"jobs": jobs[:ne], "vjp_jobs": jobs[ne:nj], "vjp_fwd_jobs": int(counts[5]),
             "add_ptr": add_ptr, "add_src": add_src[: int(counts[2])], "add_mult": add_mult[: int(counts[2])],
             "slots": int(counts[3]), "slot_u": int(counts[6]), "slot_g0": int(counts[7]),
-            "slot_r0": int(counts[8]), "input_slots": int(counts[9])}
+            "slot_r0": int(counts[8]), "input_slots": int(counts[9]), "const0": int(counts[10]),
+            "slot_up0": int(counts[11]), "slot_J0": int(counts[12]), "slot_rJ0": int(counts[13])}
 
 
 def selftest_timeout(timeout_ms=500):

@@ -5,7 +5,8 @@ summed from the addition tables.  Without any rounding the results must equal
 the exact value, gradient and VJP, which pins the tables themselves: the real
 reverse mode with powers, the complex form (four real products and the add /
 subtract jobs of every complex product, correlations with the conjugate in the
-VJP) and the VJP tables.  No GPU needed."""
+VJP), systems (per-polynomial constants, Jacobian outputs, one upstream series
+per polynomial) and the VJP tables.  No GPU needed."""
 from fractions import Fraction
 
 import numpy as np
@@ -154,3 +155,70 @@ def test_complex_program_exact(seed, powers):
         assert (vs[2 * (r0 + m)], vs[2 * (r0 + m) + 1]) == ccorr_fr(u, conj(mono))
     for i in range(n):
         assert (vs[2 * (r0 + N + i)], vs[2 * (r0 + N + i) + 1]) == ccorr_fr(u, conj(grad[i]))
+
+
+@pytest.mark.parametrize("powers", [False, True])
+@pytest.mark.parametrize("seed", range(3))
+def test_system_program_exact(seed, powers):
+    """A system of P polynomials: one job table, the constant of polynomial p in
+    slot const0 + p, value outputs p < P and Jacobian outputs P + p n + i; the
+    VJP with one upstream series per polynomial: coefficient gradients from the
+    correlations of u_p with the monomial products, the input gradient the sum
+    over p of the correlations of u_p with the Jacobian series."""
+    rng = np.random.default_rng(3200 + seed)
+    n, S, P = 3, 4, 3
+    polys = [synth.random_supports(rng, n, int(rng.integers(0, 4)), 1, n) for _ in range(P)]
+    exps = [[[int(e) for e in rng.integers(1, 3, size=len(s_))] for s_ in p_] for p_ in polys] if powers else \
+        [[[1] * len(s_) for s_ in p_] for p_ in polys]
+    supp = [m for p_ in polys for m in p_]
+    flat_ex = [e for pe in exps for e in pe]
+    N = len(supp)
+    Pr = pes.jobc_program(supp, n, exponents=flat_ex if powers else None, with_vjp=True,
+                          polys=[len(p_) for p_ in polys])
+    consts = [rand_series(rng, S) for _ in range(P)]
+    mcoeff = [rand_series(rng, S) for _ in range(N)]
+    z = [rand_series(rng, S) for _ in range(n)]
+    u = [rand_series(rng, S) for _ in range(P)]
+
+    def inputs():
+        slots = {1 + m: mcoeff[m] for m in range(N)}
+        slots.update({1 + N + i: z[i] for i in range(n)})
+        slots.update({Pr["const0"] + p: consts[p] for p in range(P)})
+        return slots
+
+    slots = inputs()
+    run_jobs(slots, Pr["jobs"])
+    m0 = 0
+    refs = []
+    for p, p_ in enumerate(polys):
+        coeff = [consts[p]] + mcoeff[m0:m0 + len(p_)]
+        value, grad = eval_grad_pow_fr(p_, exps[p], n, coeff, z)
+        refs.append((coeff, grad))
+        assert output(Pr, slots, p, S) == value
+        for i in range(n):
+            assert output(Pr, slots, P + p * n + i, S) == grad[i]
+        m0 += len(p_)
+    # VJP
+    vs = inputs()
+    for p in range(P):
+        vs[Pr["slot_up0"] + p] = u[p]
+    run_jobs(vs, Pr["vjp_jobs"][: Pr["vjp_fwd_jobs"]])
+    for p in range(P):
+        for i in range(n):
+            o = P + p * n + i
+            if Pr["add_ptr"][o + 1] > Pr["add_ptr"][o]:
+                vs[Pr["slot_J0"] + p * n + i] = output(Pr, vs, o, S)
+    run_jobs(vs, Pr["vjp_jobs"][Pr["vjp_fwd_jobs"]:])
+    m0 = 0
+    for p, p_ in enumerate(polys):
+        coeff, _ = refs[p]
+        ri, rc = vjp_pow_fr(p_, exps[p], n, coeff, z, u[p])
+        for m in range(len(p_)):
+            assert vs[Pr["slot_r0"] + m0 + m] == rc[m + 1]
+        for i in range(n):  # the summands of the input gradient (the sum over p is an addition table)
+            o = P + p * n + i
+            if Pr["add_ptr"][o + 1] > Pr["add_ptr"][o]:
+                assert vs[Pr["slot_rJ0"] + p * n + i] == ri[i]
+            else:
+                assert all(x == 0 for x in ri[i])
+        m0 += len(p_)
