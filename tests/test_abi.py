@@ -46,6 +46,19 @@ def test_md_costs():
         pes.md_costs(6)
 
 
+def test_bench_cost_table_is_the_library_table():
+    """bench.py keeps its own copy of the double-operation costs so that its
+    oracle arm loads nothing of the CUDA library; the copy must be the
+    library's table."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for k in (1, 2, 3, 4, 5, 8, 10):
+        assert bench.md_costs(k) == pes.md_costs(k)
+
+
 def test_system_arguments_checked_on_host():
     """pes_plan_system rejects a bad poly_ptr (and bad supports) before it
     touches the device; pes_eval_system rejects a NULL plan."""
