@@ -397,15 +397,27 @@ pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status);
  * 64 MiB that is part of this library, so every GPU that loads the library
  * holds those 64 MiB until the process exits.  The paper has no counterpart.
  *
- * Arguments as pes_plan (supports, N, n, d, k) and pes_eval_grad (caller-owned
- * device buffers coeff, input, value, grad; asynchronous on `stream`).  The job
- * tables are compiled on the host at every call and copied into the array with
- * cudaMemcpyAsync; nothing calls cudaMalloc, cudaFree or an allocating library
- * routine.  Problems whose tables and workspace exceed 64 MiB are rejected
- * with PES_EUNSUPPORTED_SIZE (message in pes_last_error).
+ * Arguments as pes_plan (supports of monomials with exponents one, N, n, d, k)
+ * and pes_eval_grad (caller-owned device buffers coeff, input, value, grad;
+ * asynchronous on `stream`); the outputs are bit for bit those of pes_plan +
+ * pes_eval_grad.  The job tables are compiled on the host at every call and
+ * copied into the array with cudaMemcpyAsync; nothing calls cudaMalloc,
+ * cudaFree or an allocating library routine.  Limits, each rejected with
+ * PES_EUNSUPPORTED_SIZE (message in pes_last_error):
+ *   - d <= 1023, and the whole operand series of a job must fit one CTA's
+ *     shared memory (there is no tiled kernel here): d <= 487 at k=10, 591 at
+ *     k=8, 879 at k=5, 999 at k=4;
+ *   - tables and workspace within the 64 MiB: at d=152, k=10 a series takes
+ *     18,560 bytes of workspace (160 rows of 29 words), so about 3,600 series
+ *     fit; the workspace holds 3 n_m - 2 series per monomial of n_m >= 2
+ *     variables, a_0 and the n inputs.
+ * Negative d or a NULL buffer is PES_EINVAL, k outside the set
+ * PES_EUNSUPPORTED_K.
  *
  * The first call on a device takes the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
+ * cudaGetSymbolAddress (with that device current), and so does the first call
+ * in any other CUDA context of the device (a context the caller made current,
+ * or the new primary context after cudaDeviceReset); make that first call
  * before any stream capture.  Every call reuses the same array and rewrites
  * its tables, flags and control word, so calls that overlap on the GPU (on
  * different streams or threads) race and give wrong results; serialise them.

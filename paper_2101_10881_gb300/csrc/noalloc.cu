@@ -12,8 +12,13 @@
 // the process exits.
 //
 // In host code the array's name is only a host-side stand-in; its device
-// address is taken once per device with cudaGetSymbolAddress (on the first
-// call on that device, with that device current) and passed to the kernels.
+// address is taken with cudaGetSymbolAddress (on the first call on a device,
+// with that device current) and passed to the kernels.  The address belongs to
+// the CUDA context the module was loaded into, so it is kept per device
+// together with the identity of the context it was taken in: a call made in
+// another context of the same device (a caller-created context, or the new
+// primary context after cudaDeviceReset) takes the address again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,12 +34,18 @@
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
+// the whole-series kernel only (no tiles): its shared-memory staging bounds the
+// degree further at large k (487 at k=10, 591 at k=8, 879 at k=5, 999 at k=4)
+constexpr int32_t kMaxStaticDegree = 1023;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 256;
 std::mutex g_setup_mutex;
+// per device: the array's address and the id of the context it was taken in
+// (0: not taken yet, or the context could not be identified)
 unsigned char* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
 }  // namespace
 
@@ -48,6 +59,39 @@ void set_error(const std::string& msg) { pes::set_last_error(msg); }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Id of the current CUDA context (unique for the life of the process), 0 when
+// the driver cannot tell; looked up through the runtime's driver entry points,
+// so the library does not link the driver library itself.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // under g_setup_mutex
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of g_static_scratch in the current context of the current
+// device: taken with cudaGetSymbolAddress on the first call on that device
+// (and again whenever the current context is not the one it was taken in, or
+// the context cannot be identified).
 pes_status setup_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -60,14 +104,18 @@ pes_status setup_device(unsigned char** out) {
     return PES_EINVAL;
   }
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();  // 0 before the runtime made a context current
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess || ptr == nullptr) {
       set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_scratch_addr[dev] = nullptr;
+      g_scratch_ctx[dev] = 0;
       return PES_ECUDA;
     }
     g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+    g_scratch_ctx[dev] = current_context_id();  // the context the address was taken in
   }
   *out = g_scratch_addr[dev];
   return PES_OK;
@@ -96,9 +144,14 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
     set_error("k must be one of 1,2,3,4,5,8,10");
     return PES_EUNSUPPORTED_K;
   }
-  if (d < 0 || d > 1023 || !coeff || !input || !value || !grad) {
-    set_error("bad degree or NULL buffer");
+  if (d < 0 || !coeff || !input || !value || !grad) {
+    set_error("negative degree or NULL buffer");
     return PES_EINVAL;
+  }
+  if (d > kMaxStaticDegree) {
+    set_error("degree " + std::to_string(d) + " above " + std::to_string(kMaxStaticDegree) +
+              ", the largest the allocation-free entry point takes");
+    return PES_EUNSUPPORTED_SIZE;
   }
   std::string msg = pes::validate(supp_ptr, supp_idx, N, n);
   if (!msg.empty()) {
@@ -182,7 +235,8 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
 
   const size_t smem = pes::dag_smem_bytes(k, arith, S, d, 1);
   if (smem > static_cast<size_t>(optin)) {
-    set_error("degree too large for the shared-memory staging");
+    set_error("degree " + std::to_string(d) + " at k=" + std::to_string(k) +
+              " does not fit the shared-memory staging of whole series");
     return PES_EUNSUPPORTED_SIZE;
   }
   STATIC_CUDA(pes::dag_prepare(k, arith, smem));
