@@ -208,21 +208,5 @@ def config4(d: int, k: int, seed: int = 0, npoly: int = 64, n: int = 64, N: int 
     return SystemCase(n, d, k, avals, inputs, polys)
 
 
-def closed_form_value(supports, coeff_scalars, avals, d: int):
-    """Exact value series of sum_m c_m exp((sum_{i in S_m} a_i) t) + c_0.
-
-    coeff_scalars: list of Fractions c_0..c_N (degree-0 coefficients).
-    """
-    out = [Fraction(0)] * (d + 1)
-    out[0] += coeff_scalars[0]
-    for m, s in enumerate(supports):
-        sm = sum(Fraction(avals[i]) for i in s)
-        term = Fraction(1)
-        for j in range(d + 1):
-            out[j] += coeff_scalars[m + 1] * term
-            term = term * sm / (j + 1)
-    return out
-
-
 def binomial(n: int, r: int) -> int:
     return math.comb(n, r)

@@ -102,6 +102,76 @@ def normwise_err_fr(s, ref_fr) -> float:
 
 
 # ---------------------------------------------------------------------------
+# closed forms for exp-series inputs
+# ---------------------------------------------------------------------------
+
+def closed_form_value(supports, coeff_scalars, avals, d: int):
+    """Exact value series of c_0 + sum_m c_m exp((sum_{i in S_m} a_i) t), truncated
+    at degree d: with inputs z_i = exp(a_i t) and degree-0 coefficients c_m, the
+    monomial over S_m is exp((sum_{i in S_m} a_i) t), whose coefficient j is
+    (sum a_i)^j / j!.
+
+    coeff_scalars: list of Fractions c_0..c_N.
+    """
+    out = [Fraction(0)] * (d + 1)
+    out[0] += coeff_scalars[0]
+    for m, s in enumerate(supports):
+        sm = sum(Fraction(avals[i]) for i in s)
+        term = Fraction(1)
+        for j in range(d + 1):
+            out[j] += coeff_scalars[m + 1] * term
+            term = term * sm / (j + 1)
+    return out
+
+
+def exp_series_fixed(c: Fraction, P: int, e: int, d: int, F: int):
+    """Coefficients 0..d of c exp(sigma t), sigma = P / 2^e, as integers at scale
+    2^F: T_0 = c 2^F (exact: c's denominator must divide 2^F) and
+    T_j = floor(T_{j-1} P / (2^e j)).  Every floor loses less than one unit and
+    a lost unit is carried on multiplied by at most |sigma| / j, so no term is
+    off by more than exp(|sigma|) units of 2^-F."""
+    num = c.numerator << F
+    assert num % c.denominator == 0, "c 2^F is not an integer"
+    t = num // c.denominator
+    out = [t]
+    for j in range(1, d + 1):
+        q = t * P
+        den = j << e
+        t = q // den if q >= 0 else -((-q) // den)  # truncate toward zero: same bound
+        out.append(t)
+    return out
+
+
+def limbs_fixed(a, F: int):
+    """(k, ..., S) limb array -> object array (..., S) of exact integers at
+    scale 2^F (the sum of each coefficient's limbs times 2^F)."""
+    a = np.asarray(a, dtype=np.float64)
+    k = a.shape[0]
+    flat = a.reshape(k, -1)
+    out = np.empty(flat.shape[1], dtype=object)
+    for i in range(flat.shape[1]):
+        v = 0
+        for l in range(k):
+            x = float(flat[l, i])
+            if x != 0.0:
+                n_, d_ = x.as_integer_ratio()
+                n_ <<= F
+                assert n_ % d_ == 0, "limb below 2^-F"
+                v += n_ // d_
+        out[i] = v
+    return out.reshape(a.shape[1:])
+
+
+def normwise_err_ints(got, ref) -> float:
+    """max_j |got_j - ref_j| / max_j |ref_j| of two integer series at one scale."""
+    den = max(abs(int(r)) for r in ref)
+    num = max(abs(int(g) - int(r)) for g, r in zip(got, ref))
+    if den == 0:
+        return 0.0 if num == 0 else float("inf")
+    return num / den
+
+
+# ---------------------------------------------------------------------------
 # Fraction evaluator (tiny cases only)
 # ---------------------------------------------------------------------------
 

@@ -9,7 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_2101_10881_gb300 import pes, synth
 from paper_2101_10881_gb300.synth import KS, random_md
-from tests.exact import TOL, normwise_err
+from tests.exact import TOL, closed_form_value, normwise_err
 
 pytestmark = pytest.mark.gpu
 
@@ -167,7 +167,7 @@ def test_system_full_size_sampled(torch):
         for i in (0, 21, 63):
             assert normwise_err(J[:, : dd + 1, p, i], rg[:, i]) <= TOL[k]
         cs = [sum((Fraction(float(x)) for x in c[:, m, 0]), Fraction(0)) for m in range(c.shape[1])]
-        ref = synth.closed_form_value(supp, cs, sysc.avals, d)
+        ref = closed_form_value(supp, cs, sysc.avals, d)
         assert truncated_value_err(v[:, :, p], ref) <= TOL[k]
 
 

@@ -15,7 +15,7 @@ import pytest
 from oracle import oracle as O
 from paper_2101_10881_gb300 import synth
 from paper_2101_10881_gb300.synth import KS, random_md
-from tests.exact import (TOL, eval_grad_fr, normwise_err, normwise_err_fr, series_fractions,
+from tests.exact import (TOL, closed_form_value, eval_grad_fr, normwise_err, normwise_err_fr, series_fractions,
                          to_fraction, vjp_fr, conv_fr)
 
 
@@ -92,7 +92,7 @@ def test_closed_form_exp_inputs(k):
     coeff = synth.scalar_coeffs(rng, k, N, d)
     cs = [to_fraction(coeff[:, m, 0]) for m in range(N + 1)]
     v, g = O.eval_grad(supports, n, coeff, inputs)
-    vexact = synth.closed_form_value(supports, cs, avals, d)
+    vexact = closed_form_value(supports, cs, avals, d)
     assert normwise_err_fr(v, [vexact]) <= TOL[k]
     gexact = []
     for i in range(n):
