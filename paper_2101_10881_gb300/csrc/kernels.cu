@@ -103,13 +103,34 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
   }
 }
 
+// A 64-bit two's-complement accumulator of the integer pipe, kept as two
+// 32-bit words: a digit product x * y (a signed 64-bit value) is added as a
+// 32-bit multiply-add of its low word with carry-out, then a multiply-add of
+// its high word with carry-in.  The sum is the same 64-bit value a 64-bit
+// multiply-add gives; this form needs one heavy-pipe instruction per product
+// and no extra 64-bit addition on the ALU.
+struct Acc64 {
+  uint32_t lo;
+  int32_t hi;
+};
+
 // acc += x * y, exactly: 32x32 -> 64-bit integer multiply-add in place, or FP64 FMA
 // on digit products that are exact by construction.
-__device__ __forceinline__ void mac(int32_t x, int32_t y, long long& acc) {
-  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(x), "r"(y));
+__device__ __forceinline__ void mac(int32_t x, int32_t y, Acc64& acc) {
+  asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.s32 %1, %2, %3, %1;" : "+r"(acc.lo), "+r"(acc.hi) : "r"(x), "r"(y));
 }
 
 __device__ __forceinline__ void mac(double x, double y, double& acc) { acc = __fma_rn(x, y, acc); }
+
+__device__ __forceinline__ void acc_clear(Acc64& a) {
+  a.lo = 0u;
+  a.hi = 0;
+}
+__device__ __forceinline__ void acc_clear(double& a) { a = 0.0; }
+__device__ __forceinline__ long long acc_value(const Acc64& a) {
+  return static_cast<long long>((static_cast<unsigned long long>(static_cast<uint32_t>(a.hi)) << 32) | a.lo);
+}
+__device__ __forceinline__ long long acc_value(double a) { return __double2ll_rn(a); }
 
 __device__ __forceinline__ void set_error(Ctrl* ctrl, int code, long long d0, long long d1) {
   if (atomicCAS(&ctrl->status, 0, code) == 0) {
@@ -226,7 +247,7 @@ __device__ __forceinline__ long long corr_start(long long j, long long d) { retu
 template <int K, bool INTV>
 struct DigitMac {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
-  using AccT = typename std::conditional<INTV, long long, double>::type;
+  using AccT = typename std::conditional<INTV, Acc64, double>::type;
   static constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
   static constexpr int L = digits_for_k(K, B);
   static constexpr int XS = x_stride(L, INTV);
@@ -281,32 +302,53 @@ struct DigitMac {
     }
   }
 
-  // Add the accumulators into an exchange row (L + 1 words): A[t] belongs to
-  // word t+1 (word 0 is headroom above the grid's top digit).  One flush may
-  // carry up to 2^63 per accumulator, so the values are first carried in
-  // registers: word t+1 takes the low B bits of A[t] plus the part of A[t+1]
-  // above its low B bits, word 0 the part of A[0] above B bits.  No word then
-  // takes more than about 2^(64-B) per flush, and the words stay exact however
-  // many flushes they receive.
+  // Add the accumulators into an exchange row (L + 1 words of 8 bytes): A[t]
+  // belongs to word t+1 (word 0 is headroom above the grid's top digit).  One
+  // flush may carry up to 2^63 per accumulator, so the values are first carried
+  // in registers: word t+1 takes the low B bits of A[t] plus the part of A[t+1]
+  // above its low B bits, word 0 the part of A[0] above B bits, so no word takes
+  // more than 2^36 in magnitude per flush.  Each such contribution w is added as
+  // two 32-bit integers, w = h 2^18 + l with l in [-2^17, 2^17): h into the first
+  // half of the word and l into the second, with native 32-bit shared-memory
+  // atomic adds (a 64-bit shared-memory atomic add is a compare-and-swap loop,
+  // and the lanes of a coefficient group flush the same words at the same
+  // step).  Both halves stay exact for 2^13 flushes into one word, far more than
+  // any coefficient receives (its terms / R flushes plus two per lane); the
+  // word's value is h 2^18 + l (exch_word).
   __device__ __forceinline__ static void flush(unsigned long long* row, AccT (&A)[L]) {
+    int32_t* r32 = reinterpret_cast<int32_t*>(row);
     long long hi_next = 0;  // part of A[t+1] above its low B bits
 #pragma unroll
     for (int t = L - 1; t >= 0; --t) {
-      long long v;
-      if constexpr (INTV) v = A[t]; else v = __double2ll_rn(A[t]);
+      const long long v = acc_value(A[t]);
       const long long w = (v & ((1LL << B) - 1)) + hi_next;
       hi_next = v >> B;  // arithmetic shift: v = hi * 2^B + lo
-      if (w != 0) atomicAdd(row + t + 1, static_cast<unsigned long long>(w));
-      A[t] = 0;
+      add_split(r32 + 2 * (t + 1), w);
+      acc_clear(A[t]);
     }
-    if (hi_next != 0) atomicAdd(row, static_cast<unsigned long long>(hi_next));
+    add_split(r32, hi_next);
+  }
+
+  // row[0..1] += w as h 2^18 + l, l in [-2^17, 2^17)
+  __device__ __forceinline__ static void add_split(int32_t* row, long long w) {
+    if (w == 0) return;
+    const long long l = ((w + (1LL << 17)) & ((1LL << 18) - 1)) - (1LL << 17);
+    const long long h = (w - l) >> 18;
+    if (h != 0) atomicAdd(row, static_cast<int32_t>(h));
+    if (l != 0) atomicAdd(row + 1, static_cast<int32_t>(l));
   }
 };
+
+// Value of exchange-row word t (two 32-bit halves h, l: h 2^18 + l).
+__device__ __forceinline__ int64_t exch_word(const unsigned long long* row, int t) {
+  const int2 p = reinterpret_cast<const int2*>(row)[t];
+  return static_cast<int64_t>(p.x) * (1LL << 18) + p.y;
+}
 
 template <int K, bool INTV>
 __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1) dag_kernel(DagArgs a) {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
-  using AccT = typename std::conditional<INTV, long long, double>::type;
+  using AccT = typename DigitMac<K, INTV>::AccT;
   constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
   constexpr int L = digits_for_k(K, B);
   constexpr int XS = x_stride(L, INTV);
@@ -527,7 +569,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
         const bool conv = jb.kind == JOB_CONV;
         AccT A[L];
   #pragma unroll
-        for (int t = 0; t < L; ++t) A[t] = 0;
+        for (int t = 0; t < L; ++t) acc_clear(A[t]);
         auto flush = [&](int jj) { DigitMac<K, INTV>::flush(exch + jj * (L + 1), A); };
         // one term x_ix * y_iy of output coefficient j, delta digits below its grid
         auto term = [&](int ix, int iy, int delta) { DigitMac<K, INTV>::term(xdig, ydig, ix, iy, delta, A); };
@@ -661,7 +703,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
         } else {
           int64_t E[L + 1];
   #pragma unroll
-          for (int t = 0; t <= L; ++t) E[t] = static_cast<int64_t>(exch[j * (L + 1) + t]);
+          for (int t = 0; t <= L; ++t) E[t] = exch_word(exch + j * (L + 1), t);
           gz = sum_to_digits<L, B>(E, g, o);
         }
         int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j) * RW);
@@ -989,7 +1031,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
           const int p0 = min(q * H, tp), p1 = min(p0 + H, tp);
           AccT A[L];
 #pragma unroll
-          for (int t = 0; t < L; ++t) A[t] = 0;
+          for (int t = 0; t < L; ++t) acc_clear(A[t]);
           int jcur = p0 < na ? ca : cb;
           int left = R;
           for (int pos = p0; pos < p1; ++pos) {
@@ -1030,7 +1072,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
           } else {
             int64_t E[L + 1];
 #pragma unroll
-            for (int u = 0; u <= L; ++u) E[u] = static_cast<int64_t>(exch[t * (L + 1) + u]);
+            for (int u = 0; u <= L; ++u) E[u] = exch_word(exch + t * (L + 1), u);
             gz = sum_to_digits<L, B>(E, g, o);
           }
           int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j0 + t) * RW);
