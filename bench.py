@@ -79,7 +79,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-complex", action="store_true",
                     help="skip the measurement of the workload with complex series")
     ap.add_argument("--no-large-degree", action="store_true",
-                    help="skip the measurement of the tiled kernel (p2-like at d=1023, and d=487 with both kernels)")
+                    help="skip the measurement of the tiled kernel (p2-like at d=1023, and d=471 with both kernels)")
     ap.add_argument("--no-system", action="store_true",
                     help="skip the measurement of the 64 x 64 system (values and Jacobian in one plan)")
     ap.add_argument("--no-powers", action="store_true",
@@ -757,7 +757,7 @@ def system_measure(args, dev, flush, peak):
 def large_degree_measure(args, dev, flush, peak):
     """Degrees beyond the whole-series staging: the p2-like polynomial (n=128,
     128 monomials of 64 variables, k=10) at d=1023, where the tiled kernel
-    runs (tiles of 128 coefficients), and at d=487, the largest degree the
+    runs (tiles of 128 coefficients), and at d=471, the largest degree the
     whole-series kernel takes, once with each kernel; ms per eval+grad step
     with CUDA events and an L2 flush between steps."""
     import numpy as np
@@ -766,7 +766,7 @@ def large_degree_measure(args, dev, flush, peak):
     base = synth.config1(seed=args.seed)
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for name, d, tile in (("d1023_tiled", 1023, 0), ("d487_whole", 487, 0), ("d487_tiled", 487, 128)):
+    for name, d, tile in (("d1023_tiled", 1023, 0), ("d471_whole", 471, 0), ("d471_tiled", 471, 128)):
         rng = np.random.default_rng(args.seed + d)
         coeff = synth.random_md(rng, base.k, (base.N + 1, d + 1))
         inputs = synth.random_md(rng, base.k, (base.n, d + 1))
@@ -796,7 +796,7 @@ def large_degree_measure(args, dev, flush, peak):
                      "workspace_bytes": info["workspace_bytes"]}
         del plan, C, Z
     out["workload"] = "p2-like, n=128, 128 monomials of 64 variables, k=10, random series"
-    out["tiled_over_whole_at_d487"] = out["d487_tiled"]["ms_per_step"] / out["d487_whole"]["ms_per_step"]
+    out["tiled_over_whole_at_d471"] = out["d471_tiled"]["ms_per_step"] / out["d471_whole"]["ms_per_step"]
     return out
 
 

@@ -85,8 +85,8 @@ typedef struct {
                           job's dependants wait for all its parts; more parts shorten the chains of long
                           monomials; 0 = automatic (1, and 1 and 2 are tried when autotuning) */
   int32_t tile;        /* 0 = automatic: the whole series of a job's operands are staged in shared memory
-                          when they fit (integer / FP64 pipe: d <= 487 / 359 at k=10, 591 / 447 at k=8,
-                          879 / 607 at k=5, 999 / 815 at k=4, 1159 / 919 at k=3, 1379 / 1231 at k=2,
+                          when they fit (integer / FP64 pipe: d <= 471 / 359 at k=10, 543 / 447 at k=8,
+                          839 / 607 at k=5, 991 / 815 at k=4, 1075 / 919 at k=3, 1351 / 1231 at k=2,
                           1535 / 1487 at k=1), else the tiled kernel with tiles of 128 coefficients.
                           > 0 (a multiple of 8 in [16, 1024]): always the tiled kernel with tiles of this
                           many coefficients: every job is split into output tiles, each accumulated tile
@@ -405,8 +405,8 @@ pes_status pes_selftest_timeout(int64_t timeout_ms, int32_t* device_status);
  * cudaFree or an allocating library routine.  Limits, each rejected with
  * PES_EUNSUPPORTED_SIZE (message in pes_last_error):
  *   - d <= 1023, and the whole operand series of a job must fit one CTA's
- *     shared memory (there is no tiled kernel here): d <= 487 at k=10, 591 at
- *     k=8, 879 at k=5, 999 at k=4;
+ *     shared memory (there is no tiled kernel here): d <= 471 at k=10, 543 at
+ *     k=8, 839 at k=5, 991 at k=4;
  *   - tables and workspace within the 64 MiB: at d=152, k=10 a series takes
  *     18,560 bytes of workspace (160 rows of 29 words), so about 3,600 series
  *     fit; the workspace holds 3 n_m - 2 series per monomial of n_m >= 2

@@ -198,18 +198,31 @@ __host__ __device__ constexpr int y_stride(int L, bool intv) {
 // exchange rows (the limbs are converted to digits before the rows are
 // zeroed).  Depth 2: separate buffers, so that the next job's operands can be
 // staged while the exchange rows of the current one are still being rounded.
+//
+// Exchange rows of the integer variant: one private row per lane of the CTA
+// and one extra row per coefficient-pair group (for the one lane of a group
+// whose run crosses from the short to the long coefficient), each L + 1
+// 64-bit words at an odd stride in 8-byte units (private_row_stride), so that
+// every row has a single writer and no shared-memory atomics are needed.  The
+// FP64 variant keeps one row per output coefficient, updated atomically.
 // int32 words per workspace row of one coefficient: the integer variant's Y
 // row stride (so that a whole operand series lands as Y rows with one bulk
 // copy), else the digits rounded up to 16 bytes.
 __host__ __device__ constexpr int row_words(int L, bool intv) { return intv ? y_stride(L, true) : (L + 3) / 4 * 4; }
 
-__host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int smax, int dmax, int depth) {
+__host__ __device__ constexpr int private_row_stride(int L) { return (L + 1) | 1; }
+// coefficient-pair groups of a series of degree d: (d+1)/2 pairs (j, d-j),
+// j < d-j, and the middle coefficient d/2 alone when d+1 is odd
+__host__ __device__ constexpr int pair_groups(int d) { return (d + 2) / 2; }
+
+__host__ __device__ inline DagLayout dag_layout(int K, int L, bool intv, int smax, int dmax, int depth, int threads) {
   const int digit_bytes = intv ? 4 : 8;
   DagLayout o;
   // staged digit rows: X only (Y rows land in place) for the integer variant,
   // X and Y for the FP64 variant (converted to doubles)
   size_t raw_bytes = size_t(intv ? 1 : 2) * smax * row_words(L, intv) * sizeof(int32_t);
-  size_t exch_bytes = size_t(dmax + 1) * (L + 1) * sizeof(unsigned long long);
+  size_t exch_bytes = intv ? size_t(threads + pair_groups(dmax)) * private_row_stride(L) * sizeof(unsigned long long)
+                           : size_t(dmax + 1) * (L + 1) * sizeof(unsigned long long);
   size_t off = 0;
   o.raw = 0;
   if (depth >= 2) {
@@ -329,6 +342,23 @@ struct DigitMac {
     add_split(r32, hi_next);
   }
 
+  // The same carried contributions added into a row that only this thread
+  // writes (plain 64-bit loads and stores; each word takes at most 2^36 per
+  // flush, far inside 64 bits).
+  __device__ __forceinline__ static void flush_own(unsigned long long* row, AccT (&A)[L]) {
+    long long* r64 = reinterpret_cast<long long*>(row);
+    long long hi_next = 0;
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      const long long v = acc_value(A[t]);
+      const long long w = (v & ((1LL << B) - 1)) + hi_next;
+      hi_next = v >> B;
+      r64[t + 1] += w;
+      acc_clear(A[t]);
+    }
+    r64[0] += hi_next;
+  }
+
   // row[0..1] += w as h 2^18 + l, l in [-2^17, 2^17)
   __device__ __forceinline__ static void add_split(int32_t* row, long long w) {
     if (w == 0) return;
@@ -360,7 +390,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
   constexpr int R = INTV ? static_cast<int>((1LL << (63 - 2 * (B - 1))) / L) : 128 / L;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax, a.depth);
+  const DagLayout lay = dag_layout(K, L, INTV, a.smax, a.dmax, a.depth, blockDim.x);
   int32_t* raw = reinterpret_cast<int32_t*>(smem + lay.raw);
   unsigned long long* exch = reinterpret_cast<unsigned long long*>(smem + lay.exch);
   DigitT* xdig = reinterpret_cast<DigitT*>(smem + lay.xdig);
@@ -550,7 +580,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       __syncthreads();
 
       // ---- zero the exchange rows, reference grid of every output coefficient ----
-      const int rows = (d + 1) * (L + 1);
+      const int rows = INTV ? (T + g_hi - g_lo) * private_row_stride(L) : (d + 1) * (L + 1);
       for (int t = tid; t < rows; t += T) exch[t] = 0ull;
       for (int j = tid; j <= d; j += T) {
         if (!owned(j)) continue;
@@ -622,6 +652,14 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
           const int p1 = min(p0 + H, tp);
           int jcur = p0 < ns ? cs : cl;
           int left = R;  // terms the accumulators take before the next flush
+          // Exchange rows with one writer each: the lane's private row takes
+          // the coefficient it ends on; a lane whose run crosses from the short
+          // to the long coefficient puts its short partial sums into its
+          // group's extra row.
+          unsigned long long* prow = exch + static_cast<size_t>(tid) * private_row_stride(L);
+          unsigned long long* cur = prow;
+          if (grp < g_hi && p0 < ns && p1 > ns)
+            cur = exch + static_cast<size_t>(T + grp - g_lo) * private_row_stride(L);
           for (int pos = p0; pos < p1; ++pos) {
             int j, i;
             if (pos < ns) {
@@ -636,15 +674,17 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
             term(ix, iy, gs[j] - gx[ix] - gy[iy]);
             --left;
             if (pos == ns - 1 && pos + 1 < p1) {
-              flush(cs);  // this lane leaves the short coefficient
+              DigitMac<K, INTV>::flush_own(cur, A);  // this lane leaves the short coefficient
+              cur = prow;
               jcur = cl;
             }
             if (left == 0) {  // the same steps in every lane (not reset by the switch)
-              flush(jcur);
+              DigitMac<K, INTV>::flush_own(cur, A);
               left = R;
             }
           }
-          if (p1 > p0) flush(jcur);
+          if (p1 > p0) DigitMac<K, INTV>::flush_own(cur, A);
+          (void)jcur;
         } else {
           // Every thread runs the same number of consecutive terms of the
           // concatenated term sequence; partial sums of a coefficient split between
@@ -702,8 +742,42 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
           for (int p = 0; p < L; ++p) o[p] = 0;
         } else {
           int64_t E[L + 1];
-  #pragma unroll
-          for (int t = 0; t <= L; ++t) E[t] = exch_word(exch + j * (L + 1), t);
+          if constexpr (INTV) {
+            // the lanes of the coefficient's group that ran its terms: those of
+            // the short coefficient before the crossing lane, plus the extra row
+            // when a lane crosses; those of the long one from the crossing lane
+            // on; every lane for the middle coefficient
+            const int grp = min(j, d - j);
+            const int r = grp - g_lo, Gp = g_hi - g_lo;
+            const int Qb = T / Gp, extra = T - Qb * Gp;
+            const int Q = r < extra ? Qb + 1 : Qb;
+            const int l0 = r < extra ? r * (Qb + 1) : extra * (Qb + 1) + (r - extra) * Qb;
+            const bool mid = (d % 2 == 0) && j == d / 2;
+            const int tp = mid ? d / 2 + 1 : d + 2;
+            const int ns = mid ? tp : grp + 1;
+            const int H = (tp + Q - 1) / Q;
+            const int qb = ns / H;
+            const bool is_short = !mid && j == (jb.kind == JOB_CONV ? grp : d - grp);
+            const int lo = mid ? 0 : is_short ? 0 : qb;
+            const int hi = mid ? Q : is_short ? qb : Q;
+            constexpr int PS = private_row_stride(L);
+#pragma unroll
+            for (int t = 0; t <= L; ++t) E[t] = 0;
+#pragma unroll 1
+            for (int u = l0 + lo; u < l0 + hi; ++u) {
+              const long long* row = reinterpret_cast<const long long*>(exch) + static_cast<size_t>(u) * PS;
+#pragma unroll
+              for (int t = 0; t <= L; ++t) E[t] += row[t];
+            }
+            if (is_short && ns % H != 0) {
+              const long long* row = reinterpret_cast<const long long*>(exch) + static_cast<size_t>(T + r) * PS;
+#pragma unroll
+              for (int t = 0; t <= L; ++t) E[t] += row[t];
+            }
+          } else {
+#pragma unroll
+            for (int t = 0; t <= L; ++t) E[t] = exch_word(exch + j * (L + 1), t);
+          }
           gz = sum_to_digits<L, B>(E, g, o);
         }
         int4* dst = reinterpret_cast<int4*>(zrows + static_cast<long long>(j) * RW);
@@ -1385,8 +1459,8 @@ int digits_of_k(int k, int arith) { return digits_for_k(k, arith == ARITH_INT ? 
 
 int ws_row_words(int k, int arith) { return row_words(digits_of_k(k, arith), arith == ARITH_INT); }
 
-size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth) {
-  return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax, depth).total;
+size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth, int threads) {
+  return dag_layout(k, digits_of_k(k, arith), arith == ARITH_INT, smax, dmax, depth, threads).total;
 }
 
 size_t dag_tiled_smem_bytes(int k, int arith, int tile) {
@@ -1422,7 +1496,8 @@ cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid
   const bool tiled = a.tile > 0;
   void* fn = dag_kernel_ptr(k, arith, tiled);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = tiled ? dag_tiled_smem_bytes(k, arith, a.tile) : dag_smem_bytes(k, arith, a.smax, a.dmax, a.depth);
+  const size_t smem =
+      tiled ? dag_tiled_smem_bytes(k, arith, a.tile) : dag_smem_bytes(k, arith, a.smax, a.dmax, a.depth, threads);
   DagArgs copy = a;
   void* args[] = {&copy};
   return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, st);

@@ -76,8 +76,9 @@ __host__ __device__ constexpr int dag_min_ctas(int k) { return k >= 10 ? 2 : 1; 
 constexpr int kMaxSplit = 4;  // largest number of parts a convolution job is split into
 
 // Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax) at
-// staging depth 1 or 2.
-size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth);
+// staging depth 1 or 2 with `threads` threads per CTA (the integer variant
+// keeps one exchange row per thread).
+size_t dag_smem_bytes(int k, int arith, int smax, int dmax, int depth, int threads);
 // Shared-memory footprint of the tiled DAG kernel (degrees whose whole series
 // do not fit) for output tiles of `tile` coefficients, any degree.
 size_t dag_tiled_smem_bytes(int k, int arith, int tile);

@@ -35,7 +35,7 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
 // the whole-series kernel only (no tiles): its shared-memory staging bounds the
-// degree further at large k (487 at k=10, 591 at k=8, 879 at k=5, 999 at k=4)
+// degree further at large k (471 at k=10, 543 at k=8, 839 at k=5, 991 at k=4)
 constexpr int32_t kMaxStaticDegree = 1023;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -184,7 +184,7 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
     const int pairs = (d + 2) / 2;
     const int t = std::max((pairs + 31) / 32 * 32, std::min((2 * pairs + 31) / 32 * 32, pes::dag_max_threads(k)));
     if (t <= pes::dag_max_threads(k) &&
-        pes::dag_smem_bytes(k, pes::ARITH_INT, S, d, 1) <= static_cast<size_t>(optin)) {
+        pes::dag_smem_bytes(k, pes::ARITH_INT, S, d, 1, t) <= static_cast<size_t>(optin)) {
       arith = pes::ARITH_INT;
       threads = t;
     }
@@ -233,7 +233,7 @@ extern "C" pes_status pes_eval_grad_static(const int32_t* supp_ptr, const int32_
   pes_status s = setup_device(&base);
   if (s != PES_OK) return s;
 
-  const size_t smem = pes::dag_smem_bytes(k, arith, S, d, 1);
+  const size_t smem = pes::dag_smem_bytes(k, arith, S, d, 1, threads);
   if (smem > static_cast<size_t>(optin)) {
     set_error("degree " + std::to_string(d) + " at k=" + std::to_string(k) +
               " does not fit the shared-memory staging of whole series");

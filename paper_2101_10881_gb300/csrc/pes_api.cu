@@ -108,8 +108,8 @@ int32_t whole_series_threads(int32_t k, int32_t arith, int32_t dmax, int32_t req
 // The whole-series kernel runs degree dmax (lanes and shared memory at staging
 // depth 1); otherwise the tiled kernel takes it.
 bool whole_series_fits(int32_t k, int32_t arith, int32_t dmax, int32_t requested, int optin) {
-  return whole_series_threads(k, arith, dmax, requested) > 0 &&
-         pes::dag_smem_bytes(k, arith, pes::series_stride(dmax), dmax, 1) <= static_cast<size_t>(optin);
+  const int32_t t = whole_series_threads(k, arith, dmax, requested);
+  return t > 0 && pes::dag_smem_bytes(k, arith, pes::series_stride(dmax), dmax, 1, t) <= static_cast<size_t>(optin);
 }
 
 int device_optin() {
@@ -233,8 +233,10 @@ struct Exec {
       tile = 0;
       threads = whole_series_threads(k, arith, dmax, threads);
       split = (arith == pes::ARITH_INT && o.split > 0) ? o.split : 1;
-      depth = (staging == 2 && pes::dag_smem_bytes(k, arith, smax, dmax, 2) <= static_cast<size_t>(optin)) ? 2 : 1;
-      smem = pes::dag_smem_bytes(k, arith, smax, dmax, depth);
+      depth = (staging == 2 && pes::dag_smem_bytes(k, arith, smax, dmax, 2, threads) <= static_cast<size_t>(optin))
+                  ? 2
+                  : 1;
+      smem = pes::dag_smem_bytes(k, arith, smax, dmax, depth, threads);
     } else {
       // output tiles: at least one lane per pair of coefficients of a tile; by
       // default two per pair (integer variant) or 128 threads (FP64 variant)
@@ -272,10 +274,11 @@ struct Exec {
     return PES_OK;
   }
 
-  // shared memory of the convolution kernel at staging depth `dp`, or 0 if it does not fit
-  size_t smem_at(int32_t dp) const {
+  // shared memory of the convolution kernel at staging depth `dp` with `t`
+  // threads per CTA, or 0 if it does not fit
+  size_t smem_at(int32_t dp, int32_t t) const {
     if (tile > 0) return dp == 1 ? pes::dag_tiled_smem_bytes(k, arith, tile) : 0;
-    const size_t b = pes::dag_smem_bytes(k, arith, smax, dmax, dp);
+    const size_t b = pes::dag_smem_bytes(k, arith, smax, dmax, dp, t);
     return b <= static_cast<size_t>(optin) ? b : 0;
   }
 
@@ -283,7 +286,7 @@ struct Exec {
   // depth and the parts per job (integer variant only; the tiled kernel keeps
   // its tiles per job) for later launches
   pes_status configure(int32_t t, int32_t ctas_cap, int32_t dp, int32_t sp, JobList& L) {
-    const size_t b = smem_at(dp);
+    const size_t b = smem_at(dp, t);
     if (b == 0) return fail(PES_EUNSUPPORTED_SIZE, "staging depth does not fit in shared memory");
     if (tile > 0 && t < tile / 2) return fail(PES_EUNSUPPORTED_SIZE, "fewer lanes than pairs of a tile");
     PES_CUDA(pes::dag_prepare(k, arith, b, tile > 0));
@@ -534,10 +537,10 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
     float best = 1e30f;
     for (int32_t sp : splits) {
       for (int32_t dp : depths) {
-        const size_t b = E.smem_at(dp);
-        if (b == 0) continue;
-        PES_CUDA(pes::dag_prepare(E.k, E.arith, b));
         for (int32_t t : ts) {
+          const size_t b = E.smem_at(dp, t);
+          if (b == 0) continue;
+          PES_CUDA(pes::dag_prepare(E.k, E.arith, b));
           int occ = 0;
           PES_CUDA(pes::dag_occupancy(E.k, E.arith, t, b, &occ));
           for (int32_t c = std::max(1, occ); c >= std::max(1, occ - 1); --c) {
@@ -572,7 +575,7 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
 
 std::string tune_key(const Exec& E, int64_t njobs, uint64_t signature) {
   char key[200];
-  std::snprintf(key, sizeof(key), "v4_k%d_a%d_t%d_s%d_p%d_T%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads,
+  std::snprintf(key, sizeof(key), "v5_k%d_a%d_t%d_s%d_p%d_T%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads,
                 E.staging, E.split_req, E.tile, E.dmax,
                 static_cast<long long>(njobs), static_cast<unsigned long long>(signature));
   return key;

@@ -105,7 +105,7 @@ def test_ragged_degree_several_tiles(torch, threads):
     assert info["conv_jobs"] == 12 + 3 + 1 + 6 + 9
 
 
-@pytest.mark.parametrize("k,dmax", [(10, 487), (8, 591), (2, 1379)])
+@pytest.mark.parametrize("k,dmax", [(10, 471), (8, 543), (2, 1351)])
 def test_maximum_degree(torch, k, dmax):
     """The largest degree whose whole operand series one job stages in the
     integer variant (both series, their digits and the exchange rows in one

@@ -98,10 +98,10 @@ def test_static_entry_rejects_oversized_problem(torch):
     assert b"scratch" in pes.lib().pes_last_error()
 
 
-@pytest.mark.parametrize("k,d", [(2, 1024), (10, 488)])
+@pytest.mark.parametrize("k,d", [(2, 1024), (10, 472)])
 def test_static_entry_rejects_large_degrees(torch, k, d):
     """Above d = 1023, and above the degree whose whole series fit one CTA's
-    shared memory (487 at k = 10), the call is refused with
+    shared memory (471 at k = 10), the call is refused with
     PES_EUNSUPPORTED_SIZE before anything is enqueued."""
     rng = np.random.default_rng(d)
     prob = synth.Problem("big", 2, d, k, [[0, 1]], random_md(rng, k, (2, d + 1)), random_md(rng, k, (2, d + 1)))
