@@ -84,6 +84,9 @@ def parse_args(argv=None):
                     help="skip the measurement of the 64 x 64 system (values and Jacobian in one plan)")
     ap.add_argument("--no-powers", action="store_true",
                     help="skip the measurement of the workload with powers (monomials with exponents 1-3)")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1: also time one polynomial of the workload split over the N ranks by "
+                         "monomials (strong scaling; exact integer all-reduces of grids and digit sums)")
     ap.add_argument("--cpu-sample-vars", type=int, default=12,
                     help="variables of the monomial the oracle evaluates as the CPU sample")
     return ap.parse_args(argv)
@@ -519,6 +522,8 @@ def ours_arm(args, world, rank, local):
         out["large_degree"] = large_degree_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     if args.workload == "p2" and not args.no_system:
         out["system"] = system_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
+    if world > 1 and args.shard:
+        out["shard"] = shard_measure(args, dev, world, rank, prob, ops_step, flush)
     count = 256 if args.batch_count is None else args.batch_count
     if count > 0:
         out["batched"] = batch_measure(args, dev, count)
@@ -533,6 +538,41 @@ def ours_arm(args, world, rank, local):
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
+
+
+def shard_measure(args, dev, world, rank, prob, ops_step, flush):
+    """The workload's polynomial split over the ranks by monomials (contiguous
+    ranges balanced by convolution jobs): per step every rank runs its
+    convolutions, the ranks all-reduce the grids (maximum) and the exact digit
+    sums (sum) over NCCL, and every rank rounds the whole value and gradient
+    once.  Strong scaling: the whole polynomial per step, time of the slowest
+    rank."""
+    import torch
+    from paper_2101_10881_gb300.shard import ShardPlan
+    sp = ShardPlan(prob.supports, prob.n, prob.d, prob.k, world, rank, arith=args.arith)
+    C = sp.coeff_of(torch.from_numpy(prob.coeff).to(dev))
+    Z = torch.from_numpy(prob.inputs).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        sp.eval_grad(C, Z)
+    torch.cuda.synchronize(dev)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sp.eval_grad(C, Z)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    sp.plan.check()
+    ms = max_over_ranks(statistics.mean(times), world)
+    return {"workload": "the headline polynomial split over the ranks by monomials", "ranks": world,
+            "monomials_this_rank": sp.m_end - sp.m_begin, "ms_per_step": ms,
+            "value": ops_step / (ms * 1e-3) / 1e12, "unit": UNIT, "scaling": "strong",
+            "exchange": "all-reduce max of int32 grids, all-reduce sum of int64 digit sums"}
 
 
 def autograd_measure(args, dev, flush):

@@ -254,6 +254,61 @@ typedef struct {
 
 pes_status pes_get_plan_info(pes_plan_t plan, pes_plan_info* info);
 
+/* ---- one polynomial split over ranks ---------------------------------------------
+ *
+ * The monomials of a polynomial are independent through the convolution layers;
+ * only the addition jobs combine their contributions (Sec. 5).  So a polynomial
+ * can be split over R ranks (one GPU each) by monomials: rank r plans the
+ * polynomial of its own monomials (pes_plan / pes_plan_powers, the constant a_0
+ * on one rank only, zero on the others) and the ranks exchange two exact integer
+ * arrays.  With pes_partial_grids, an all-reduce (maximum) of the grids,
+ * pes_partial_sums, an all-reduce (sum) of the digit sums and pes_round_sums,
+ * every rank obtains the value and gradient that one plan of the whole polynomial
+ * computes, bit for bit: the addition stage sums the contributions of every
+ * output coefficient on the largest grid among them and rounds once, and both
+ * the maximum and the sum of integers are exact in any order.  (A sum of the
+ * ranks' rounded k-double limbs in floating point would not be.)
+ *
+ * Item o (d + 1) + j is coefficient j of the value (o = 0) or of d p / d x_i
+ * (o = 1 + i); L is pes_plan_info.digits. */
+
+/* The contiguous range [*m_begin, *m_end) of monomials (0-based, of supp_ptr's
+ * N monomials) that rank `rank` of `world` takes: cut where the running sum of
+ * the monomials' convolution jobs (3 n_m - 3, one for n_m = 1) crosses
+ * r W / world, W the total, so no rank holds more than W / world plus one
+ * monomial's jobs.  Host only.  PES_EINVAL for bad sizes or an empty monomial. */
+pes_status pes_shard_range(const int32_t* supp_ptr, int32_t N, int32_t world, int32_t rank, int32_t* m_begin,
+                           int32_t* m_end);
+
+/* Run the plan's convolutions (as pes_eval_grad does) and write, for every item,
+ * the largest grid of its contributions (a grid below -100000 when it has none).
+ *   grids: device, int32 [(n+1)(d+1)] (written).
+ * Real single-polynomial plans only (PES_EINVAL for complex or system plans).
+ * Asynchronous on `stream`. */
+pes_status pes_partial_grids(pes_plan_t plan, const double* coeff, const double* input, int32_t* grids,
+                             void* stream);
+
+/* Sum every item's contributions exactly on the grid `grids` gives it (the
+ * elementwise maximum over all ranks of pes_partial_grids), dropping the digits
+ * below its L digits as the addition stage does, and write the L digit sums
+ * unrounded: acc[item * L + p] weighs 2^(28 (g - 1 - p)) (24 bits for the FP64
+ * pipe), g = grids[item].  Uses the products of the last pes_partial_grids call
+ * on this plan (no other call in between).
+ *   grids: device, int32 [(n+1)(d+1)];  acc: device, int64 [(n+1)(d+1)][L] (written).
+ * Asynchronous on `stream`. */
+pes_status pes_partial_sums(pes_plan_t plan, const int32_t* grids, int64_t* acc, void* stream);
+
+/* Round digit sums (pes_partial_sums summed over the ranks) on their grids to k
+ * limbs, once per item, as the addition stage rounds: value [k][d+1] and grad
+ * [k][n][d+1] (device, written).  Asynchronous on `stream`. */
+pes_status pes_round_sums(pes_plan_t plan, const int32_t* grids, const int64_t* acc, double* value, double* grad,
+                          void* stream);
+
+/* The same rounding on the host (host buffers; no GPU needed), for k limbs and
+ * the digits of `arith` (PES_ARITH_INT or PES_ARITH_FP64), n variables, degree d. */
+pes_status pes_round_sums_host(int32_t k, int32_t arith, int32_t n, int32_t d, const int32_t* grids,
+                               const int64_t* acc, double* value, double* grad);
+
 /* ---- batches: many polynomials in one persistent launch (CUDA graph) ---------- */
 
 /* count instances; instance b has n[b] variables, N[b] monomials and degree

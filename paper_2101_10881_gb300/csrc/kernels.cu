@@ -1280,17 +1280,29 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
   const long long gofs = static_cast<long long>(in.S) * RW + j;  // grid of coefficient j within a slot
   const long long rofs = static_cast<long long>(j) * RW;         // row of coefficient j within a slot
 
-  // common grid: the largest grid of the contributions
+  // item index of a real single plan (value: output 0, d p / d x_i: output 1 + i)
+  const long long item =
+      (ao.dst_sel == 0 ? 0 : 1 + ao.dst_off / (in.d + 1)) * static_cast<long long>(in.d + 1) + j;
+
+  // common grid: the largest grid of the contributions (mode 2: the one given)
   int32_t gmax = 2 * GRID_ZERO;
-  if (valid)
-    for (int c = ao.cbeg + gl; c < ao.cend; c += G)
-      gmax = max(gmax, base[static_cast<long long>(a.contrib[c]) * in.ws_sstride + gofs]);
+  if (a.mode == 2) {
+    gmax = valid ? a.grid_io[item] : gmax;
+  } else {
+    if (valid)
+      for (int c = ao.cbeg + gl; c < ao.cend; c += G)
+        gmax = max(gmax, base[static_cast<long long>(a.contrib[c]) * in.ws_sstride + gofs]);
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  if constexpr (GROUPED) {
-    if (lane == 0) gm_s[warp] = gmax;
-    __syncthreads();
-    for (int t = 0; t < gw; ++t) gmax = max(gmax, gm_s[warp - sw + t]);
+    for (int o = 16; o >= 1; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    if constexpr (GROUPED) {
+      if (lane == 0) gm_s[warp] = gmax;
+      __syncthreads();
+      for (int t = 0; t < gw; ++t) gmax = max(gmax, gm_s[warp - sw + t]);
+    }
+    if (a.mode == 1) {
+      if (valid && gl == 0) a.grid_io[item] = gmax;
+      return;  // (every thread has passed the group's barrier)
+    }
   }
 
   // every lane sums its contributions' digits, shifted to the common grid
@@ -1327,6 +1339,11 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
         for (int p = 0; p < L; ++p) acc[p] += acc_s[warp + t][p];
   }
   if (!valid || gl != 0) return;
+  if (a.mode == 2) {
+#pragma unroll
+    for (int p = 0; p < L; ++p) a.acc_out[item * L + p] = acc[p];
+    return;
+  }
   // acc[p] weighs 2^(B (gmax - 1 - p)): word p + 1 of a sum on grid gmax + 1
   int64_t E[L + 1];
   E[0] = 0;
@@ -1360,6 +1377,40 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
 template <int K, bool INTV>
 __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
   add_body<K, INTV, false>(a, items);
+}
+
+// Digit sums on their grids (acc[p] weighs 2^(B (g - 1 - p)), g = grids[item])
+// rounded to k limbs, as the addition stage rounds its own sums: item
+// o (d + 1) + j is coefficient j of the value (o = 0) or of d p / d x_{o-1}.
+template <int K, bool INTV>
+__host__ __device__ void round_sum_item(const RoundArgs& a, long long item) {
+  constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
+  constexpr int L = digits_for_k(K, B);
+  const long long D1 = a.d + 1;
+  const long long o = item / D1, j = item - o * D1;
+  double* dst = o == 0 ? a.value + j : a.grad + (o - 1) * D1 + j;
+  const long long ls = o == 0 ? D1 : static_cast<long long>(a.n) * D1;
+  const int32_t g = a.grids[item];
+  if (g < -100000) {
+    for (int l = 0; l < K; ++l) dst[l * ls] = 0.0;
+    return;
+  }
+  int64_t E[L + 1];
+  E[0] = 0;
+  for (int p = 0; p < L; ++p) E[p + 1] = a.acc[item * L + p];
+  from_digits<K, L, B>(E, g + 1, dst, ls);
+}
+
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256) round_sums_kernel(RoundArgs a, long long items) {
+  const long long item = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (item < items) round_sum_item<K, INTV>(a, item);
+}
+
+template <int K, bool INTV>
+void round_sums_host_k(const RoundArgs& a) {
+  const long long items = static_cast<long long>(a.n + 1) * (a.d + 1);
+  for (long long item = 0; item < items; ++item) round_sum_item<K, INTV>(a, item);
 }
 
 template <int K, bool INTV>
@@ -1559,6 +1610,28 @@ cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaSt
   else
     PES_DISPATCH_K_ARITH(add_kernel, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
   return cudaGetLastError();
+}
+
+cudaError_t launch_round_sums(const RoundArgs& a, int k, int arith, cudaStream_t st) {
+  const long long items = static_cast<long long>(a.n + 1) * (a.d + 1);
+  if (items == 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((items + 255) / 256);
+  PES_DISPATCH_K_ARITH(round_sums_kernel, k, arith, grid, 256, st, a, items);
+  return cudaGetLastError();
+}
+
+int round_sums_host(int k, int arith, const RoundArgs& a) {
+  const bool iv = arith == ARITH_INT;
+  switch (k) {
+    case 1: iv ? round_sums_host_k<1, true>(a) : round_sums_host_k<1, false>(a); return 0;
+    case 2: iv ? round_sums_host_k<2, true>(a) : round_sums_host_k<2, false>(a); return 0;
+    case 3: iv ? round_sums_host_k<3, true>(a) : round_sums_host_k<3, false>(a); return 0;
+    case 4: iv ? round_sums_host_k<4, true>(a) : round_sums_host_k<4, false>(a); return 0;
+    case 5: iv ? round_sums_host_k<5, true>(a) : round_sums_host_k<5, false>(a); return 0;
+    case 8: iv ? round_sums_host_k<8, true>(a) : round_sums_host_k<8, false>(a); return 0;
+    case 10: iv ? round_sums_host_k<10, true>(a) : round_sums_host_k<10, false>(a); return 0;
+    default: return 1;
+  }
 }
 
 cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out, int64_t count,

@@ -55,6 +55,26 @@ struct AddArgs {
   int32_t* ws;
   double* dst[2];           // k-limb results: caller buffers by selector
   int32_t group_warps;      // warps that share one output coefficient (1, 2, 4 or 8)
+  // Partial sums of a polynomial split over ranks (real single plans; output o
+  // of the value is 0, of d p / d x_i is 1 + i, coefficient j of output o is
+  // item o (d + 1) + j):
+  //   mode 0: round every sum (or write it in digit form, to_ws);
+  //   mode 1: write the largest grid of each item's contributions to grid_io;
+  //   mode 2: sum each item's contributions on the grid grid_io gives (the
+  //           largest over all ranks) and write the L exact digit sums,
+  //           unrounded, to acc_out[item * L + p].
+  int32_t mode;
+  int32_t* grid_io;
+  long long* acc_out;
+};
+
+// Rounding of digit sums (mode 2 of the addition stage, summed over ranks).
+struct RoundArgs {
+  const int32_t* grids;     // [(n+1)(d+1)]
+  const long long* acc;     // [(n+1)(d+1)][L]
+  double* value;            // [k][d+1]
+  double* grad;             // [k][n][d+1]
+  int32_t n, d;
 };
 
 struct CopyArgs {
@@ -107,6 +127,9 @@ cudaError_t launch_pack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_unpack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st);
 cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaStream_t st);
+cudaError_t launch_round_sums(const RoundArgs& a, int k, int arith, cudaStream_t st);
+// The same rounding on the host (no GPU needed).
+int round_sums_host(int k, int arith, const RoundArgs& a);
 cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm, bool tiled = false);
 cudaError_t dag_prepare(int k, int arith, size_t smem, bool tiled = false);
 cudaError_t launch_md_binary(int op, int k, const double* x, const double* y, double* out,

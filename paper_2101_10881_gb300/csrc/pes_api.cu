@@ -328,10 +328,14 @@ struct Exec {
 
   // sums into caller buffers (rounded to k limbs), or, with dst0 == dst1 ==
   // nullptr, into workspace slots in digit form
-  cudaError_t run_add(const AddTable& A, double* dst0, double* dst1, cudaStream_t st) const {
+  cudaError_t run_add(const AddTable& A, double* dst0, double* dst1, cudaStream_t st, int32_t mode = 0,
+                      int32_t* grid_io = nullptr, long long* acc_out = nullptr) const {
     for (int b = 0; b < 2; ++b) {
       if (A.items[b] == 0) continue;
       pes::AddArgs a{};
+      a.mode = mode;
+      a.grid_io = grid_io;
+      a.acc_out = acc_out;
       a.outs = A.outs[b];
       a.nouts = A.nouts[b];
       a.to_ws = (dst0 == nullptr && dst1 == nullptr) ? 1 : 0;
@@ -894,6 +898,89 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
   PES_CUDA(E.mark(4, st));
   E.last_launches = 1 + Exec::launches(plan->pack) + Exec::launches(plan->fwd) + Exec::launches(plan->add);
   return PES_OK;
+}
+
+// ---- one polynomial split over ranks (Sec. 5: monomials are independent up to
+// the addition jobs; the exchange is exact integer arithmetic) ----------------
+
+extern "C" pes_status pes_shard_range(const int32_t* supp_ptr, int32_t N, int32_t world, int32_t rank,
+                                      int32_t* m_begin, int32_t* m_end) {
+  if (N < 0 || world < 1 || rank < 0 || rank >= world || !m_begin || !m_end || (N > 0 && !supp_ptr))
+    return fail(PES_EINVAL, "bad sizes, rank or NULL pointer");
+  // cost of monomial m: its convolution jobs, 3 n_m - 3 (one for n_m = 1)
+  std::vector<int64_t> pre(static_cast<size_t>(N) + 1, 0);
+  for (int32_t m = 0; m < N; ++m) {
+    const int64_t nm = supp_ptr[m + 1] - supp_ptr[m];
+    if (nm < 1) return fail(PES_EINVAL, "empty monomial " + std::to_string(m));
+    pre[static_cast<size_t>(m) + 1] = pre[static_cast<size_t>(m)] + (nm >= 2 ? 3 * nm - 3 : 1);
+  }
+  const int64_t W = pre.back();
+  // rank r takes the monomials whose cost prefix starts in [r W / world, (r+1) W / world)
+  auto bound = [&](int32_t r) -> int32_t {
+    if (r <= 0) return 0;
+    if (r >= world) return N;
+    int32_t m = 0;
+    while (m < N && pre[static_cast<size_t>(m)] * world < static_cast<int64_t>(r) * W) ++m;
+    return m;
+  };
+  *m_begin = bound(rank);
+  *m_end = bound(rank + 1);
+  return PES_OK;
+}
+
+namespace {
+pes_status check_shardable(pes_plan_t plan) {
+  if (!plan) return fail(PES_EINVAL, "plan is NULL");
+  if (plan->complex_series || plan->prog.system_P > 0)
+    return fail(PES_EINVAL, "partial sums take real single-polynomial plans (not complex, not systems)");
+  return PES_OK;
+}
+}  // namespace
+
+extern "C" pes_status pes_partial_grids(pes_plan_t plan, const double* coeff, const double* input, int32_t* grids,
+                                        void* stream) {
+  pes_status s = check_shardable(plan);
+  if (s != PES_OK) return s;
+  if (!coeff || !input || !grids) return fail(PES_EINVAL, "NULL buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Exec& E = plan->ex;
+  PES_CUDA(pes::launch_prologue(E.ctrl, st));
+  PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
+  PES_CUDA(E.run_dag(plan->fwd, 0, st));
+  PES_CUDA(E.run_add(plan->add, nullptr, nullptr, st, 1, grids, nullptr));
+  E.last_launches = 1 + Exec::launches(plan->pack) + Exec::launches(plan->fwd) + Exec::launches(plan->add);
+  return PES_OK;
+}
+
+extern "C" pes_status pes_partial_sums(pes_plan_t plan, const int32_t* grids, int64_t* acc, void* stream) {
+  pes_status s = check_shardable(plan);
+  if (s != PES_OK) return s;
+  if (!grids || !acc) return fail(PES_EINVAL, "NULL buffer");
+  Exec& E = plan->ex;
+  PES_CUDA(E.run_add(plan->add, nullptr, nullptr, static_cast<cudaStream_t>(stream), 2, const_cast<int32_t*>(grids),
+                     reinterpret_cast<long long*>(acc)));
+  E.last_launches = Exec::launches(plan->add);
+  return PES_OK;
+}
+
+extern "C" pes_status pes_round_sums(pes_plan_t plan, const int32_t* grids, const int64_t* acc, double* value,
+                                     double* grad, void* stream) {
+  pes_status s = check_shardable(plan);
+  if (s != PES_OK) return s;
+  if (!grids || !acc || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
+  pes::RoundArgs a{grids, reinterpret_cast<const long long*>(acc), value, grad, plan->prog.n, plan->prog.d};
+  PES_CUDA(pes::launch_round_sums(a, plan->ex.k, plan->ex.arith, static_cast<cudaStream_t>(stream)));
+  return PES_OK;
+}
+
+extern "C" pes_status pes_round_sums_host(int32_t k, int32_t arith, int32_t n, int32_t d, const int32_t* grids,
+                                          const int64_t* acc, double* value, double* grad) {
+  if (!valid_k(k)) return fail(PES_EUNSUPPORTED_K, "k must be one of 1,2,3,4,5,8,10");
+  if (arith != pes::ARITH_INT && arith != pes::ARITH_FP64) return fail(PES_EINVAL, "arith must be 0 or 1");
+  if (n < 1 || d < 0 || d > pes::kMaxDegree || !grids || !acc || !value || !grad)
+    return fail(PES_EINVAL, "bad sizes or NULL buffer");
+  pes::RoundArgs a{grids, reinterpret_cast<const long long*>(acc), value, grad, n, d};
+  return pes::round_sums_host(k, arith, a) == 0 ? PES_OK : fail(PES_EINTERNAL, "rounding");
 }
 
 extern "C" pes_status pes_eval_system(pes_plan_t plan, const double* coeff, const double* input, double* value,

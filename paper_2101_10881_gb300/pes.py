@@ -33,7 +33,8 @@ EXPORTS = ("pes_default_options", "pes_plan", "pes_plan_ex", "pes_plan_powers", 
            "pes_batch_offsets", "pes_eval_grad_batch", "pes_batch_check", "pes_get_batch_info",
            "pes_md_binary", "pes_md_costs", "pes_fp64_peak", "pes_int_peak", "pes_jobc_stats", "pes_jobc_jobs",
            "pes_jobc_add_levels", "pes_jobc_add_terms", "pes_selftest_timeout", "pes_eval_grad_static", "pes_status_string",
-           "pes_last_error")
+           "pes_last_error", "pes_shard_range", "pes_partial_grids", "pes_partial_sums", "pes_round_sums",
+           "pes_round_sums_host")
 
 
 class PesError(RuntimeError):
@@ -129,6 +130,11 @@ def lib():
                 "pes_jobc_add_terms": (i32, [ip32, ip32, i32, i32, ip32, ip32, i64]),
                 "pes_selftest_timeout": (i32, [i64, ip32]),
                 "pes_eval_grad_static": (i32, [ip32, ip32, i32, i32, i32, i32, vp, vp, vp, vp, vp, ip32]),
+                "pes_shard_range": (i32, [ip32, i32, i32, i32, ip32, ip32]),
+                "pes_partial_grids": (i32, [vp, vp, vp, vp, vp]),
+                "pes_partial_sums": (i32, [vp, vp, vp, vp]),
+                "pes_round_sums": (i32, [vp, vp, vp, vp, vp, vp]),
+                "pes_round_sums_host": (i32, [i32, i32, i32, i32, ip32, ip64, dp, dp]),
                 "pes_status_string": (ctypes.c_char_p, [i32]),
                 "pes_last_error": (ctypes.c_char_p, []),
             }
@@ -172,6 +178,38 @@ def _ptr(t, shape, name):
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _iptr(t, shape, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def shard_range(supports, world, rank):
+    """Monomials [begin, end) that rank `rank` of `world` takes (pes_shard_range)."""
+    ptr, _ = csr(supports)
+    b, e = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().pes_shard_range(_ip32(ptr), len(supports), int(world), int(rank), ctypes.byref(b), ctypes.byref(e)),
+           "pes_shard_range")
+    return b.value, e.value
+
+
+def round_sums_host(k, n, d, grids, acc, arith="int"):
+    """pes_round_sums_host on numpy arrays: grids int32 (n+1, d+1), acc int64
+    (n+1, d+1, L) -> value (k, d+1), grad (k, n, d+1)."""
+    g = np.ascontiguousarray(grids, dtype=np.int32)
+    a = np.ascontiguousarray(acc, dtype=np.int64)
+    value = np.empty((k, d + 1))
+    grad = np.empty((k, n, d + 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().pes_round_sums_host(int(k), ARITH[arith] if isinstance(arith, str) else int(arith), int(n), int(d),
+                                     _ip32(g), a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     value.ctypes.data_as(dp), grad.ctypes.data_as(dp)), "pes_round_sums_host")
+    return value, grad
 
 
 def make_options(arith="auto", threads=0, ctas_per_sm=0, with_vjp=True, timeout_ms=60000, profile=False,
@@ -285,6 +323,47 @@ class Plan:
                              _stream(stream)), "pes_vjp")
         self.generation += 1
         return grad_input, grad_coeff
+
+    # ---- partial sums of a polynomial split over ranks (pes_partial_*) ----
+
+    def partial_grids(self, coeff, inputs, grids=None, stream=None):
+        """Convolutions of this plan, then the largest grid of every output
+        coefficient's contributions: int32 (n+1, d+1), row 0 the value."""
+        import torch
+        sh = self.shapes()
+        if grids is None:
+            grids = torch.empty((self.n + 1, self.d + 1), dtype=torch.int32, device=coeff.device)
+        _check(lib().pes_partial_grids(self._h, _ptr(coeff, sh["coeff"], "coeff"), _ptr(inputs, sh["input"], "input"),
+                                       _iptr(grids, (self.n + 1, self.d + 1), torch.int32, "grids"),
+                                       _stream(stream)), "pes_partial_grids")
+        return grids
+
+    def partial_sums(self, grids, acc=None, stream=None):
+        """Exact digit sums of every output coefficient on the given grids:
+        int64 (n+1, d+1, L), unrounded."""
+        import torch
+        L = self.info()["digits"]
+        if acc is None:
+            acc = torch.empty((self.n + 1, self.d + 1, L), dtype=torch.int64, device=grids.device)
+        _check(lib().pes_partial_sums(self._h, _iptr(grids, (self.n + 1, self.d + 1), torch.int32, "grids"),
+                                      _iptr(acc, (self.n + 1, self.d + 1, L), torch.int64, "acc"),
+                                      _stream(stream)), "pes_partial_sums")
+        return acc
+
+    def round_sums(self, grids, acc, value=None, grad=None, stream=None):
+        """Digit sums (summed over the ranks) rounded once to k limbs."""
+        import torch
+        sh = self.shapes()
+        L = self.info()["digits"]
+        if value is None:
+            value = torch.empty(sh["value"], dtype=torch.float64, device=grids.device)
+        if grad is None:
+            grad = torch.empty(sh["grad"], dtype=torch.float64, device=grids.device)
+        _check(lib().pes_round_sums(self._h, _iptr(grids, (self.n + 1, self.d + 1), torch.int32, "grids"),
+                                    _iptr(acc, (self.n + 1, self.d + 1, L), torch.int64, "acc"),
+                                    _ptr(value, sh["value"], "value"), _ptr(grad, sh["grad"], "grad"),
+                                    _stream(stream)), "pes_round_sums")
+        return value, grad
 
     def workspace_io(self, buffer, to_buffer, stream=None):
         _check(lib().pes_workspace_io(self._h, ctypes.c_void_p(buffer.data_ptr()), int(bool(to_buffer)),
