@@ -13,14 +13,21 @@ double additions per addition job.
 
 Also reported: `e2e` (same metric through the Python API with pinned host
 buffers, copies inside the timed region), `roofline` of the convolution kernel
-against the measured FP64 FMA peak, the oracle as `cpu_baseline`, launch count
-and SM clocks sampled during the timed region.
+against the unit-count peak of the integer multiply-add pipe (and the measured
+microbenchmark peak), the oracle as `cpu_baseline`, launch count and SM clocks
+sampled during the timed region; beside the headline: p1 at d=8 in double
+double (`config0`), two cells of the 64 x 64 system sweep (`config4`), the
+whole batched recipe at k=2 and its first 512 instances at k=8 against plain
+calls (`batched`, `batched_k8`, with the ceiling any batched launch has),
+autograd, powers, complex series, large degrees and the system plan.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 (launched by torch.distributed.run, one rank per GPU) every rank
 evaluates its own polynomial of the same shape (weak scaling, no collective on
-the data path); rank 0 prints one JSON line.
+the data path); rank 0 prints one JSON line.  --shard also times the headline
+polynomial split over the ranks by monomials (strong scaling, exact integer
+all-reduces).
 """
 from __future__ import annotations
 
@@ -72,8 +79,8 @@ def parse_args(argv=None):
     ap.add_argument("--monomials", type=int, default=0,
                     help="use only the first M monomials of the workload (smaller case for profiling)")
     ap.add_argument("--batch-count", type=int, default=None,
-                    help="instances of the batched comparison (default: 256 in the default run, 2048 with "
-                         "--workload batch; 0 skips it in the default run)")
+                    help="instances of the batched comparison (default 2048: the whole recipe at k=2, and its "
+                         "first 512 instances at k=8; 0 skips it in the default run)")
     ap.add_argument("--batch-k", type=int, default=2)
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--no-complex", action="store_true",
@@ -84,6 +91,10 @@ def parse_args(argv=None):
                     help="skip the measurement of the 64 x 64 system (values and Jacobian in one plan)")
     ap.add_argument("--no-powers", action="store_true",
                     help="skip the measurement of the workload with powers (monomials with exponents 1-3)")
+    ap.add_argument("--no-config0", action="store_true",
+                    help="skip the p1 d=8 k=2 measurement (config0)")
+    ap.add_argument("--no-config4", action="store_true",
+                    help="skip the two cells of the 64 x 64 system sweep (config4)")
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1: also time one polynomial of the workload split over the N ranks by "
                          "monomials (strong scaling; exact integer all-reduces of grids and digit sums)")
@@ -524,9 +535,15 @@ def ours_arm(args, world, rank, local):
         out["system"] = system_measure(args, dev, flush, roofline["peak"] if arith == "int" else None)
     if world > 1 and args.shard:
         out["shard"] = shard_measure(args, dev, world, rank, prob, ops_step, flush)
-    count = 256 if args.batch_count is None else args.batch_count
+    int_peak_unit = roofline["peak"] if arith == "int" else None
+    if args.workload == "p2" and not args.no_config0:
+        out["config0"] = config0_measure(args, dev, flush)
+    if args.workload == "p2" and not args.no_config4:
+        out["config4"] = config4_measure(args, dev)
+    count = 2048 if args.batch_count is None else args.batch_count
     if count > 0:
-        out["batched"] = batch_measure(args, dev, count)
+        out["batched"] = batch_measure(args, dev, count, k=2, peak=int_peak_unit)
+        out["batched_k8"] = batch_measure(args, dev, min(count, 512), k=8, peak=int_peak_unit)
         out["batched_small"] = batch_measure(args, dev, 2048, small=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub = cpu_sample(prob, args.cpu_sample_vars)
@@ -538,6 +555,93 @@ def ours_arm(args, world, rank, local):
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
+
+
+def config0_measure(args, dev, flush):
+    """The paper's p1 at the smallest size of its tables: n=16, all 1820 products
+    of 4 distinct variables, d=8, double double (random series, seed 0).
+    Latency-bound: a few microseconds of digit work in 16,380 convolutions over
+    4 layers.  ms per eval+grad step (CUDA events, L2 flushed between steps),
+    kernels launched per step; the paper's V100 time for this shape (0.18 ms,
+    sum of its kernels) is context only."""
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    prob = synth.config0(seed=args.seed)
+    plan = pes.Plan(prob.supports, prob.n, prob.d, prob.k, with_vjp=False, profile=True, autotune=not args.no_autotune)
+    C = torch.from_numpy(prob.coeff).to(dev)
+    Z = torch.from_numpy(prob.inputs).to(dev)
+    V = torch.empty(plan.shapes()["value"], dtype=torch.float64, device=dev)
+    G = torch.empty(plan.shapes()["grad"], dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        plan.eval_grad(C, Z, V, G)
+    torch.cuda.synchronize(dev)
+    times, launches = [], 0
+    for _ in range(max(args.steps, 5)):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval_grad(C, Z, V, G)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        launches = plan.last_timing()["launches"]
+    plan.check()
+    info = plan.info()
+    ms = statistics.median(times)
+    return {"workload": "p1 n=16 N=1820 monomials of 4 variables, d=8, k=2 (random series)",
+            "ms_per_step": ms, "ms_min": min(times), "launches_per_step": launches,
+            "value": dp_equiv_ops(info["conv_jobs"], info["add_jobs"], prob.d, prob.k) / (ms * 1e-3) / 1e12,
+            "unit": UNIT, "conv_jobs": info["conv_jobs"], "threads_per_cta": info["threads"],
+            "paper_v100_ms": 0.18, "paper_v100_note": "sum of the paper's kernel times on a V100 (context)"}
+
+
+def config4_measure(args, dev):
+    """64 polynomials in 64 variables, 512 monomials of 4-16 variables each,
+    degree-0 random coefficients, inputs z_i = exp(a_i t): two cells of the
+    k x d sweep (k=10 and k=2 at d=152), the 64 polynomials as one system plan:
+    forward (values) and the autograd backward of L = sum_p sum_j v_pj^2, with
+    the normwise error of two polynomials' values against the exact closed form.
+    The whole 7 x 7 sweep: bench.py --workload sweep."""
+    import numpy as np
+    import torch
+    from paper_2101_10881_gb300 import pes, synth
+    from paper_2101_10881_gb300.autograd import poly_eval
+    stream = torch.cuda.current_stream(dev)
+    tol = {1: 1e-13, 2: 1e-29, 3: 1e-44, 4: 1e-60, 5: 1e-76, 8: 1e-123, 10: 1e-150}
+    cells = {}
+    for k, d in ((10, 152), (2, 152)):
+        sysc = synth.config4(d, k, seed=args.seed)
+        sysp = pes.System([supp for supp, _ in sysc.polys], sysc.n, d, k)
+        C = torch.from_numpy(np.concatenate([c for _, c in sysc.polys], axis=1)).to(dev)
+        Z = torch.from_numpy(sysc.inputs).to(dev)
+        fb = []
+        for it in range(3):
+            Cg, Zg = C.clone().requires_grad_(True), Z.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            v = poly_eval(Cg, Zg, sysp)
+            e1.record(stream)
+            v.backward(2 * v.detach())
+            e2.record(stream)
+            e2.synchronize()
+            if it >= 1:
+                fb.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        sysp.check()
+        vals = v.detach().cpu().numpy()
+        errs = [closed_form_err(supp, c, sysc.avals, vals[:, q], 53 * k + 64)
+                for q, (supp, c) in enumerate(sysc.polys[:2])]
+        info = sysp.info()
+        f = statistics.mean(t[0] for t in fb)
+        b = statistics.mean(t[1] for t in fb)
+        cells[f"k{k}_d{d}"] = {"k": k, "d": d, "forward_ms": f, "backward_ms": b, "backward_over_forward": b / f,
+                               "forward_value": dp_equiv_ops(info["conv_jobs"], info["add_jobs"], d, k) / (f * 1e-3)
+                               / 1e12, "unit": UNIT, "conv_jobs": info["conv_jobs"],
+                               "closed_form_err": max(errs), "tol": tol[k], "within_tol": max(errs) <= tol[k]}
+        del sysp, C, Z, Cg, Zg, v
+    return {"workload": "system of 64 polynomials in 64 variables, 512 monomials of 4-16 variables, inputs "
+                        "exp(a_i t), one system plan, forward + autograd backward of sum_p sum_j v_pj^2",
+            "cells": cells}
 
 
 def shard_measure(args, dev, world, rank, prob, ops_step, flush):
@@ -840,7 +944,7 @@ def large_degree_measure(args, dev, flush, peak):
     return out
 
 
-def batch_measure(args, dev, count, small=False):
+def batch_measure(args, dev, count, small=False, k=None, peak=None):
     """Config 3 recipe (random sparse polynomials: n 8-128, m 16-2048 monomials of
     2-8 variables, d in {15,31,63,127,152}), first `count` instances, k=2 (or,
     with `small`, the small instances of synth.small_batch_shapes): one
@@ -850,7 +954,7 @@ def batch_measure(args, dev, count, small=False):
     import numpy as np
     import torch
     from paper_2101_10881_gb300 import pes, synth
-    k = args.batch_k
+    k = args.batch_k if k is None else k
     shapes = (synth.small_batch_shapes if small else synth.config3_shapes)(seed=args.seed, count=count)
     rng = np.random.default_rng(args.seed + 7)
     probs = []
@@ -901,12 +1005,25 @@ def batch_measure(args, dev, count, small=False):
     info = B.info()
     what = ("small instances (n 4-16, 4-32 monomials of 2-4 variables, d in {7,15,31})" if small
             else "instances of the batched recipe")
-    return {"workload": f"first {count} {what} (seed {args.seed}), k={k}",
-            "instances": count, "conv_jobs": info["conv_jobs"], "groups": info["grid"],
-            "batched_ms_per_instance": res["batched"] / count, "plain_ms_per_instance": res["plain"] / count,
-            "plain_over_batched": res["plain"] / res["batched"],
-            "batched_equals_plain_bitwise": same, "launches_plain_per_call": 4 * count,
-            "graph": "one CUDA graph: per group pack + persistent convolution + addition, groups on forked streams"}
+    # digit multiply-adds of the whole batch, and what the unit-count peak of
+    # the integer pipe would make of them: the ceiling of any batched launch
+    L = info["digits"]
+    macs = sum(pl.info()["conv_jobs"] * (p.d + 1) * (p.d + 2) // 2 for pl, p in zip(plans, probs)) * (L * (L + 1) // 2)
+    out = {"workload": f"first {count} {what} (seed {args.seed}), k={k}",
+           "instances": count, "k": k, "conv_jobs": info["conv_jobs"], "groups": info["grid"],
+           "batched_ms_per_instance": res["batched"] / count, "plain_ms_per_instance": res["plain"] / count,
+           "plain_over_batched": res["plain"] / res["batched"],
+           "batched_equals_plain_bitwise": same, "launches_plain_per_call": 4 * count,
+           "digit_mads": macs,
+           "graph": "one CUDA graph: per group pack + persistent convolution + addition, groups on forked streams"}
+    if peak:
+        at_peak_ms = macs / (peak * 1e12) * 1e3
+        out.update({"batched_frac_of_int_peak": at_peak_ms / res["batched"],
+                    "plain_frac_of_int_peak": at_peak_ms / res["plain"],
+                    "ceiling_plain_over_batched": res["plain"] / at_peak_ms,
+                    "ceiling_rule": "plain time over the time of the batch's digit multiply-adds at the integer "
+                                    "pipe's unit-count peak (no batched launch can be faster)"})
+    return out
 
 
 def limbs_to_fraction(limbs):

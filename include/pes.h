@@ -65,8 +65,8 @@ typedef struct {
   int32_t arith;       /* PES_ARITH_AUTO (default), PES_ARITH_FP64 or PES_ARITH_INT */
   int32_t threads;     /* threads per CTA of the convolution kernel (a multiple of 32), 0 = automatic.
                           Integer pipe: the lanes are spread evenly over the coefficient pairs (j, d-j),
-                          automatic = two lanes per pair (one per output coefficient), at least one lane
-                          per pair; FP64 pipe: automatic = 128 */
+                          automatic = two lanes per pair (one per output coefficient; three at k = 10),
+                          at least one lane per pair; FP64 pipe: automatic = 128 */
   int32_t ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit */
   int32_t with_vjp;    /* 1: also build the tables of pes_vjp (default 1) */
   int64_t timeout_ms;  /* bound on every device-side wait; 0 = default (60000) */

@@ -95,10 +95,14 @@ int32_t whole_series_threads(int32_t k, int32_t arith, int32_t dmax, int32_t req
   int32_t t = requested;
   if (arith == pes::ARITH_INT) {
     // by default two lanes per coefficient pair (one per output coefficient),
+    // three at k = 10 (whose CTAs are capped at 256 threads and two per SM:
+    // the wider CTA keeps 16 warps per SM where its exchange rows allow two),
     // whole warps; at least one lane per pair
     const int32_t pairs = (dmax + 2) / 2;
     const int32_t least = (pairs + 31) / 32 * 32;
-    t = t == 0 ? std::max(least, std::min((2 * pairs + 31) / 32 * 32, pes::dag_max_threads(k))) : std::max(t, least);
+    const int32_t per_pair = k >= 10 ? 3 : 2;
+    t = t == 0 ? std::max(least, std::min((per_pair * pairs + 31) / 32 * 32, pes::dag_max_threads(k)))
+               : std::max(t, least);
   } else if (t == 0) {
     t = 128;  // FP64 variant: 128 threads share the terms evenly
   }
