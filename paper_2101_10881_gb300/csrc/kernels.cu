@@ -71,6 +71,17 @@ __device__ __forceinline__ void fence_proxy_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Mark a sub-job done.  Every thread of the CTA stored its output rows before
+// the block barrier that precedes this call, and the barrier makes those
+// stores visible to the calling thread; the release store is cumulative over
+// them, so a CTA that reads the flag with an acquire load sees the rows.  The
+// proxy fence orders the rows (written through the generic proxy) before the
+// bulk copies a consumer issues after it has seen the flag.
+__device__ __forceinline__ void publish_flag(int32_t* flag, int epoch) {
+  fence_proxy_async_global();
+  st_release(flag, epoch);
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
@@ -789,11 +800,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      fence_proxy_async_global();
-      st_release(a.flags + sj, epoch);
-    }
+    if (tid == 0) publish_flag(a.flags + sj, epoch);
     claimed = ahead;
   }
 }
@@ -1159,11 +1166,7 @@ __global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      fence_proxy_async_global();
-      st_release(a.flags + sj, epoch);
-    }
+    if (tid == 0) publish_flag(a.flags + sj, epoch);
   }
 }
 
@@ -1247,7 +1250,7 @@ __global__ void prologue_kernel(Ctrl* ctrl) {
 // GROUPED: group_warps warps per output coefficient (block barriers combine
 // them); else one warp per output coefficient and no barrier.
 template <int K, bool INTV, bool GROUPED>
-__device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
+__device__ __forceinline__ void add_body(const AddArgs& a, long long items, long long blk) {
   constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
   constexpr int L = digits_for_k(K, B);
   constexpr int RW = row_words(L, INTV);
@@ -1261,7 +1264,7 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
   const int G = gw * 32;
   const int sw = warp % gw;                  // warp within the group
   const int gl = sw * 32 + lane;             // lane within the group
-  const long long w = static_cast<long long>(blockIdx.x) * (8 / gw) + warp / gw;
+  const long long w = blk * (8 / gw) + warp / gw;
   const bool valid = w < items;
   AddOut ao{};
   int j = 0;
@@ -1289,9 +1292,11 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
   if (a.mode == 2) {
     gmax = valid ? a.grid_io[item] : gmax;
   } else {
-    if (valid)
+    if (valid) {
+#pragma unroll 4
       for (int c = ao.cbeg + gl; c < ao.cend; c += G)
         gmax = max(gmax, base[static_cast<long long>(a.contrib[c]) * in.ws_sstride + gofs]);
+    }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     if constexpr (GROUPED) {
@@ -1310,6 +1315,7 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
 #pragma unroll
   for (int p = 0; p < L; ++p) acc[p] = 0;
   if (valid && gmax >= -100000) {
+#pragma unroll 2
     for (int c = ao.cbeg + gl; c < ao.cend; c += G) {
       const int32_t* slot = base + static_cast<long long>(a.contrib[c]) * in.ws_sstride;
       const int sh = gmax - slot[gofs];  // digits below the common grid's top
@@ -1376,7 +1382,7 @@ __device__ __forceinline__ void add_body(const AddArgs& a, long long items) {
 
 template <int K, bool INTV>
 __global__ void __launch_bounds__(256) add_kernel(AddArgs a, long long items) {
-  add_body<K, INTV, false>(a, items);
+  add_body<K, INTV, false>(a, items, blockIdx.x);
 }
 
 // Digit sums on their grids (acc[p] weighs 2^(B (g - 1 - p)), g = grids[item])
@@ -1415,7 +1421,19 @@ void round_sums_host_k(const RoundArgs& a) {
 
 template <int K, bool INTV>
 __global__ void __launch_bounds__(256) add_kernel_grouped(AddArgs a, long long items) {
-  add_body<K, INTV, true>(a, items);
+  add_body<K, INTV, true>(a, items, blockIdx.x);
+}
+
+// Both parts of an addition stage whose outputs are all summed by groups of
+// warps, in one launch: the first nb0 blocks take part 0, the rest part 1 (the
+// branch is uniform over a block, so the group barriers hold).
+template <int K, bool INTV>
+__global__ void __launch_bounds__(256) add_kernel_pair(AddArgs a0, long long items0, AddArgs a1, long long items1,
+                                                       unsigned nb0) {
+  if (blockIdx.x < nb0)
+    add_body<K, INTV, true>(a0, items0, blockIdx.x);
+  else
+    add_body<K, INTV, true>(a1, items1, blockIdx.x - nb0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1609,6 +1627,19 @@ cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaSt
     PES_DISPATCH_K_ARITH(add_kernel_grouped, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
   else
     PES_DISPATCH_K_ARITH(add_kernel, k, arith, grid, warps * 32, st, a, static_cast<long long>(items));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_pair(const AddArgs& a0, int64_t items0, const AddArgs& a1, int64_t items1, int k,
+                            int arith, cudaStream_t st) {
+  const auto grouped = [](int gw) { return gw == 2 || gw == 4 || gw == 8; };
+  if (!grouped(a0.group_warps) || !grouped(a1.group_warps)) return cudaErrorInvalidValue;
+  const int warps = 8;
+  const long long pb0 = warps / a0.group_warps, pb1 = warps / a1.group_warps;
+  const unsigned nb0 = static_cast<unsigned>((items0 + pb0 - 1) / pb0);
+  const unsigned grid = nb0 + static_cast<unsigned>((items1 + pb1 - 1) / pb1);
+  PES_DISPATCH_K_ARITH(add_kernel_pair, k, arith, grid, warps * 32, st, a0, static_cast<long long>(items0), a1,
+                       static_cast<long long>(items1), nb0);
   return cudaGetLastError();
 }
 

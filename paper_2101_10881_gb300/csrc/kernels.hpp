@@ -120,6 +120,16 @@ inline int64_t ws_slot_words(int k, int arith, int32_t S) {
 inline int32_t add_group_warps(int64_t max_contrib) {
   return max_contrib > 4096 ? 8 : max_contrib > 2048 ? 4 : max_contrib > 1024 ? 2 : 1;
 }
+// The same for a launch of `items` output coefficients on `nsm` SMs: a table
+// too small to fill the GPU with one group per coefficient (a few hundred
+// coefficients, each a sum of hundreds of contributions) is latency-bound on
+// its longest sum, so its groups are widened while the launch stays within 16
+// warps per SM and every lane keeps at least two contributions.
+inline int32_t add_group_warps(int64_t max_contrib, int64_t items, int32_t nsm) {
+  int32_t gw = add_group_warps(max_contrib);
+  while (gw < 8 && items * gw * 2 <= 16LL * nsm && max_contrib > 64LL * gw) gw *= 2;
+  return gw;
+}
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_prologue(Ctrl* ctrl, cudaStream_t st);
@@ -127,6 +137,10 @@ cudaError_t launch_pack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_unpack(const CopyArgs& a, int k, int arith, cudaStream_t st);
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st);
 cudaError_t launch_add(const AddArgs& a, int k, int arith, int64_t items, cudaStream_t st);
+// Two parts of one addition stage, both with groups of 2, 4 or 8 warps per
+// output coefficient, in one launch.
+cudaError_t launch_add_pair(const AddArgs& a0, int64_t items0, const AddArgs& a1, int64_t items1, int k,
+                            int arith, cudaStream_t st);
 cudaError_t launch_round_sums(const RoundArgs& a, int k, int arith, cudaStream_t st);
 // The same rounding on the host (no GPU needed).
 int round_sums_host(int k, int arith, const RoundArgs& a);

@@ -195,11 +195,11 @@ struct Exec {
     pes_status s = PES_OK;
     for (int b = 0; b < 2 && s == PES_OK; ++b) {
       A.nouts[b] = static_cast<int32_t>(part[b].size());
-      A.group_warps[b] = pes::add_group_warps(maxc[b]);
       std::vector<int64_t> ip(part[b].size() + 1, 0);
       for (size_t o = 0; o < part[b].size(); ++o)
         ip[o + 1] = ip[o] + insts[static_cast<size_t>(part[b][o].inst)].d + 1;
       A.items[b] = ip.back();
+      A.group_warps[b] = pes::add_group_warps(maxc[b], A.items[b], nsm > 0 ? nsm : 1);
       if (!part[b].empty()) {
         s = put(&A.outs[b], part[b]);
         if (s == PES_OK) s = put(&A.item_ptr[b], ip);
@@ -334,9 +334,10 @@ struct Exec {
   // nullptr, into workspace slots in digit form
   cudaError_t run_add(const AddTable& A, double* dst0, double* dst1, cudaStream_t st, int32_t mode = 0,
                       int32_t* grid_io = nullptr, long long* acc_out = nullptr) const {
+    pes::AddArgs args[2]{};
     for (int b = 0; b < 2; ++b) {
       if (A.items[b] == 0) continue;
-      pes::AddArgs a{};
+      pes::AddArgs& a = args[b];
       a.mode = mode;
       a.grid_io = grid_io;
       a.acc_out = acc_out;
@@ -351,14 +352,23 @@ struct Exec {
       a.dst[0] = dst0;
       a.dst[1] = dst1;
       a.group_warps = A.group_warps[b];
-      cudaError_t e = pes::launch_add(a, k, arith, A.items[b], st);
+    }
+    if (paired(A)) return pes::launch_add_pair(args[0], A.items[0], args[1], A.items[1], k, arith, st);
+    for (int b = 0; b < 2; ++b) {
+      if (A.items[b] == 0) continue;
+      cudaError_t e = pes::launch_add(args[b], k, arith, A.items[b], st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
 
+  // both parts of an addition stage in one launch (both summed by warp groups)
+  static bool paired(const AddTable& A) {
+    return A.items[0] > 0 && A.items[1] > 0 && A.group_warps[0] > 1 && A.group_warps[1] > 1;
+  }
+
   // kernels a run_add / run_dag / run_pack / run_unpack call launches
-  static int32_t launches(const AddTable& A) { return (A.items[0] > 0) + (A.items[1] > 0); }
+  static int32_t launches(const AddTable& A) { return paired(A) ? 1 : (A.items[0] > 0) + (A.items[1] > 0); }
   static int32_t launches(const JobList& L) { return L.n > 0 ? 1 : 0; }
   static int32_t launches(const CopyTable& C) { return C.n > 0 ? 1 : 0; }
 
