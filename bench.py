@@ -159,7 +159,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu_index), "-lms", "200"],
+                 "-i", str(self.gpu_index), "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -393,15 +393,23 @@ def ours_arm(args, world, rank, local):
     ops_step = dp_equiv_ops(info["conv_jobs"], info["add_jobs"], prob.d, prob.k)
     digit_flops = digit_fma_flops(info["conv_jobs"], prob.d, info["digits"])
 
-    def timed(p, steps):
+    def timed(p, steps, min_warm_s=0.0):
         """Device-resident steps with an L2 flush between them; per-step and
-        convolution-kernel milliseconds from CUDA events on the launching stream."""
-        for _ in range(max(args.warmup, 3)):
+        convolution-kernel milliseconds from CUDA events on the launching stream.
+        The untimed warm-up runs at least `warmup` steps and at least
+        min_warm_s seconds (so that the clock sampler, started before it, has
+        samples under load before the timed steps begin)."""
+        t0 = time.perf_counter()
+        done = 0
+        while done < max(args.warmup, 3) or time.perf_counter() - t0 < min_warm_s:
             p.eval_grad(C, Z, V, G)
+            torch.cuda.synchronize(dev)
+            done += 1
         torch.cuda.synchronize(dev)
         p.check()
         barrier(world)
         torch.cuda.synchronize(dev)
+        wall_box[0] = time.perf_counter()
         sms, cms, nl = [], [], 0
         for _ in range(steps):
             flush.fill_(1)
@@ -417,14 +425,15 @@ def ours_arm(args, world, rank, local):
             nl += t["launches"]
         torch.cuda.synchronize(dev)
         barrier(world)
+        wall_box[1] = time.perf_counter()
         p.check()
         return sms, cms, nl
 
+    wall_box = [0.0, 0.0]  # wall clock around the timed steps of the last timed() call
     clocks = ClockSampler(local)
     clocks.start()
-    t_wall0 = time.perf_counter()
-    step_ms, conv_ms, launches = timed(plan, args.steps)
-    wall = time.perf_counter() - t_wall0
+    step_ms, conv_ms, launches = timed(plan, args.steps, min_warm_s=0.5)
+    wall = wall_box[1] - wall_box[0]
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), world)
 
