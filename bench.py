@@ -64,7 +64,7 @@ def parse_args(argv=None):
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: one lane per coefficient)")
     ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
                     help="staging depth of the convolution kernel (0: automatic / autotuned)")
-    ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4],
+    ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4, 8, 16],
                     help="parts per convolution job (0: automatic / autotuned)")
     ap.add_argument("--tile", type=int, default=0,
                     help="coefficients per output tile of the tiled kernel (0: whole series where they fit)")

@@ -80,10 +80,14 @@ typedef struct {
                           job's operands are complete, stages them while rounding the current one
                           (a separate staging buffer: more shared memory); 0 = automatic (1, and both
                           are tried when autotuning) */
-  int32_t split;       /* parts per convolution job (integer pipe): 1, 2 or 4; each part computes the
-                          output coefficients of a contiguous range of coefficient pairs (j, d-j), so a
+  int32_t split;       /* parts per convolution job (integer pipe): 1, 2, 4, 8 or 16; each part computes
+                          the output coefficients of a contiguous range of coefficient pairs (j, d-j), so a
                           job's dependants wait for all its parts; more parts shorten the chains of long
-                          monomials; 0 = automatic (1, and 1 and 2 are tried when autotuning) */
+                          monomials; 0 = automatic: the parts double while the table's average layer, times
+                          the parts, holds fewer jobs than the launch has CTAs and every part keeps at
+                          least 8 coefficient pairs (the p2-like workload at d=152, k=10: 1 for its 128
+                          monomials, 2 for 64 of them, 4 for 32, 8 for 16 or fewer; p3: 1); when
+                          autotuning, 1, 2 and the automatic choice, half and twice it, are tried */
   int32_t tile;        /* 0 = automatic: the whole series of a job's operands are staged in shared memory
                           when they fit (integer / FP64 pipe: d <= 471 / 359 at k=10, 543 / 447 at k=8,
                           839 / 607 at k=5, 991 / 815 at k=4, 1075 / 919 at k=3, 1351 / 1231 at k=2,

@@ -93,7 +93,7 @@ struct CopyArgs {
 // accumulators and a digit row in registers).
 __host__ __device__ constexpr int dag_max_threads(int k) { return k >= 10 ? 256 : k >= 8 ? 384 : k >= 4 ? 512 : 768; }
 __host__ __device__ constexpr int dag_min_ctas(int k) { return k >= 10 ? 2 : 1; }
-constexpr int kMaxSplit = 4;  // largest number of parts a convolution job is split into
+constexpr int kMaxSplit = 16;  // largest number of parts a convolution job is split into
 
 // Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax) at
 // staging depth 1 or 2 with `threads` threads per CTA (the integer variant

@@ -58,6 +58,7 @@ struct JobList {
   int32_t* flags = nullptr;
   int32_t n = 0;
   int32_t grid = 0;
+  int32_t fparts = 1;  // parts per job the flags cover
 };
 
 // The outputs of an addition stage in two parts: those with at most 1,024
@@ -161,15 +162,47 @@ struct Exec {
     return s;
   }
 
+  // Parts per job when the caller left it automatic (integer pipe, whole
+  // series): a table whose layers hold few jobs for the CTAs of the launch
+  // (one polynomial of few long monomials, one rank's share of a polynomial)
+  // runs its dependency chains faster with every job split over several CTAs.
+  // The parts double while the average layer, times the parts, holds fewer
+  // sub-jobs than the launch has CTAs and every part keeps at least 8
+  // coefficient pairs (measured on the p2-like polynomial at d=152, k=10:
+  // within 10 % of the best split for 1 to 128 monomials).
+  void choose_split(const std::vector<pes::ConvJob>& jobs) {
+    if (split_req != 0 || arith != pes::ARITH_INT || tile != 0 || jobs.empty()) return;
+    int32_t lo = jobs.front().layer, hi = jobs.front().layer;
+    for (const auto& j : jobs) {
+      lo = std::min(lo, j.layer);
+      hi = std::max(hi, j.layer);
+    }
+    const double width = static_cast<double>(jobs.size()) / (hi - lo + 1);
+    const double ctas = static_cast<double>(blocks_per_sm) * nsm;
+    const int32_t most = std::max(1, (dmax + 2) / 2 / 8);
+    int32_t sp = 1;
+    while (sp < pes::kMaxSplit && 2 * sp <= most && width * sp < ctas) sp *= 2;
+    split = sp;
+  }
+
+  // Parts per job the flags of a job list must cover: the split in use, and,
+  // when the split is automatic, every split the autotuner may try (1, 2 and
+  // half to twice the automatic choice); the tiled kernel flags every tile.
+  int32_t flag_parts() const {
+    if (tile > 0 || split_req != 0 || arith != pes::ARITH_INT) return std::max(split, 1);
+    return std::max(2, std::min(pes::kMaxSplit, 2 * split));
+  }
+
   pes_status make_joblist(JobList& L, const std::vector<pes::ConvJob>& jobs) {
     L.n = static_cast<int32_t>(jobs.size());
     pes_status s = put(&L.jobs, jobs);
     if (s != PES_OK) return s;
     if (L.n > 0) {
-      // one flag per part of every job, for the largest split (tiled kernel: per tile)
-      if (static_cast<int64_t>(L.n) * std::max(split, pes::kMaxSplit) >= (1LL << 31))
+      // one flag per part of every job (tiled kernel: per tile)
+      if (static_cast<int64_t>(L.n) * flag_parts() >= (1LL << 31))
         return fail(PES_EUNSUPPORTED_SIZE, "jobs x tiles per job exceed 2^31");
-      const size_t nf = static_cast<size_t>(L.n) * std::max(split, pes::kMaxSplit);
+      L.fparts = flag_parts();
+      const size_t nf = static_cast<size_t>(L.n) * L.fparts;
       cudaError_t e = cudaMalloc(&L.flags, sizeof(int32_t) * nf);
       if (e != cudaSuccess) return fail(PES_ENOMEM, "job flags");
       owned.push_back(L.flags);
@@ -293,6 +326,8 @@ struct Exec {
     const size_t b = smem_at(dp, t);
     if (b == 0) return fail(PES_EUNSUPPORTED_SIZE, "staging depth does not fit in shared memory");
     if (tile > 0 && t < tile / 2) return fail(PES_EUNSUPPORTED_SIZE, "fewer lanes than pairs of a tile");
+    if (tile == 0 && arith == pes::ARITH_INT && L.n > 0 && std::max(1, sp) > L.fparts)
+      return fail(PES_EINTERNAL, "parts per job beyond the job flags");
     PES_CUDA(pes::dag_prepare(k, arith, b, tile > 0));
     int bps = 0;
     PES_CUDA(pes::dag_occupancy(k, arith, t, b, &bps, tile > 0));
@@ -435,8 +470,8 @@ pes_status parse_options(const pes_options* opt, pes_options& o) {
     return fail(PES_EINVAL, "threads must be 0 (automatic) or a multiple of 32 up to 1024");
   if (o.ctas_per_sm < 0) return fail(PES_EINVAL, "ctas_per_sm must be >= 0");
   if (o.staging < 0 || o.staging > 2) return fail(PES_EINVAL, "staging must be 0, 1 or 2");
-  if (!(o.split == 0 || o.split == 1 || o.split == 2 || o.split == 4))
-    return fail(PES_EINVAL, "split must be 0, 1, 2 or 4");
+  if (!(o.split == 0 || o.split == 1 || o.split == 2 || o.split == 4 || o.split == 8 || o.split == 16))
+    return fail(PES_EINVAL, "split must be 0, 1, 2, 4, 8 or 16");
   if (o.tile != 0 && (o.tile < 16 || o.tile > 1024 || o.tile % 8 != 0))
     return fail(PES_EINVAL, "tile must be 0 (automatic) or a multiple of 8 in [16, 1024]");
   return PES_OK;
@@ -548,7 +583,13 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
     std::vector<int32_t> depths{E.depth};
     if (E.staging == 0) depths = {1, 2};
     std::vector<int32_t> splits{E.split};
-    if (E.split_req == 0 && E.arith == pes::ARITH_INT && E.tile == 0) splits = {1, 2};
+    if (E.split_req == 0 && E.arith == pes::ARITH_INT && E.tile == 0) {
+      // the automatic choice (E.split), half and twice it, and 1 and 2
+      splits = {1, 2};
+      for (int32_t sp : {E.split / 2, E.split, E.split * 2})
+        if (sp >= 1 && sp <= pes::kMaxSplit && std::find(splits.begin(), splits.end(), sp) == splits.end())
+          splits.push_back(sp);
+    }
     cudaEvent_t e0, e1;
     PES_CUDA(cudaEventCreate(&e0));
     PES_CUDA(cudaEventCreate(&e1));
@@ -593,7 +634,7 @@ pes_status tune_launch(Exec& E, JobList& L, const std::string& key, Run run, cud
 
 std::string tune_key(const Exec& E, int64_t njobs, uint64_t signature) {
   char key[200];
-  std::snprintf(key, sizeof(key), "v5_k%d_a%d_t%d_s%d_p%d_T%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads,
+  std::snprintf(key, sizeof(key), "v6_k%d_a%d_t%d_s%d_p%d_T%d_d%d_j%lld_%016llx", E.k, E.arith, E.threads,
                 E.staging, E.split_req, E.tile, E.dmax,
                 static_cast<long long>(njobs), static_cast<unsigned long long>(signature));
   return key;
@@ -713,6 +754,7 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
   P->ws_bytes = static_cast<int64_t>(P->ex.ws_words * sizeof(int32_t));
 
   // forward jobs
+  P->ex.choose_split(G.jobs);
   s = P->ex.make_joblist(P->fwd, G.jobs);
   if (s != PES_OK) return s;
   P->autotune = o.autotune != 0;
@@ -1281,6 +1323,7 @@ extern "C" pes_status pes_plan_batch_powers(int32_t count, const int32_t* n, con
     }
     G->conv_jobs = static_cast<int64_t>(jobs.size());
     B->conv_jobs += G->conv_jobs;
+    G->ex.choose_split(jobs);
     s = G->ex.make_joblist(G->fwd, jobs);
     if (s != PES_OK) return s;
 

@@ -145,7 +145,7 @@ def test_staging_depths_agree(torch, threads):
     assert normwise_err(g2, rg) <= TOL[k]
 
 
-@pytest.mark.parametrize("split", [2, 4])
+@pytest.mark.parametrize("split", [2, 4, 8, 16])
 def test_split_jobs_agree(torch, split):
     """Jobs split into parts over ranges of coefficient pairs (each part with a
     flag of its own, dependants waiting for all parts) give the same bits as
@@ -416,4 +416,8 @@ def test_invalid_arguments(torch):
     for bad in (12, 20, 2048):
         with pytest.raises(pes.PesError) as e:
             pes.Plan([[0, 1]], 2, 40, 2, tile=bad)
+        assert e.value.code == 1
+    for bad in (3, 32, -1):
+        with pytest.raises(pes.PesError) as e:
+            pes.Plan([[0, 1]], 2, 40, 2, split=bad)
         assert e.value.code == 1
