@@ -920,14 +920,32 @@ pes_status plan_impl(const int32_t* supp_ptr, const int32_t* supp_idx, const int
 
 extern "C" void pes_plan_destroy(pes_plan_t plan) { delete plan; }
 
+// First call of a plan built with `autotune`: tune its convolution launch by
+// running `run` (the call's own work on the caller's buffers), then give the
+// VJP job lists the same launch shape.
+template <class Run>
+static pes_status tune_plan(pes_plan_t plan, Run run, cudaStream_t st) {
+  if (!plan->autotune || plan->tuned) return PES_OK;
+  plan->tuned = true;
+  Exec& E = plan->ex;
+  pes_status ts = tune_launch(E, plan->fwd, tune_key(E, plan->fwd.n, plan->signature), run, st);
+  if (ts != PES_OK) return ts;
+  plan->vjp_fwd.grid = plan->vjp_m.grid = plan->vjp_corr.grid = 0;
+  for (JobList* L : {&plan->vjp_fwd, &plan->vjp_m, &plan->vjp_corr}) {
+    if (L->n == 0) continue;
+    ts = E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, *L);
+    if (ts != PES_OK) return ts;
+  }
+  return PES_OK;
+}
+
 extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const double* input, double* value,
                                     double* grad, void* stream) {
   if (!plan) return fail(PES_EINVAL, "plan is NULL");
   if (!coeff || !input || !value || !grad) return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Exec& E = plan->ex;
-  if (plan->autotune && !plan->tuned) {
-    plan->tuned = true;
+  {
     auto run = [&](cudaStream_t s2) -> pes_status {
       PES_CUDA(pes::launch_prologue(E.ctrl, s2));
       PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, s2));
@@ -935,13 +953,8 @@ extern "C" pes_status pes_eval_grad(pes_plan_t plan, const double* coeff, const 
       PES_CUDA(E.run_add(plan->add, value, grad, s2));
       return PES_OK;
     };
-    pes_status ts = tune_launch(E, plan->fwd, tune_key(E, plan->fwd.n, plan->signature), run, st);
+    pes_status ts = tune_plan(plan, run, st);
     if (ts != PES_OK) return ts;
-    // the VJP job lists share the launch shape
-    plan->vjp_fwd.grid = plan->vjp_m.grid = plan->vjp_corr.grid = 0;
-    E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, plan->vjp_fwd);
-    E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, plan->vjp_m);
-    E.configure(E.threads, E.blocks_per_sm, E.depth, E.split, plan->vjp_corr);
   }
   PES_CUDA(E.mark(0, st));
   PES_CUDA(pes::launch_prologue(E.ctrl, st));
@@ -1000,10 +1013,17 @@ extern "C" pes_status pes_partial_grids(pes_plan_t plan, const double* coeff, co
   if (!coeff || !input || !grids) return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Exec& E = plan->ex;
-  PES_CUDA(pes::launch_prologue(E.ctrl, st));
-  PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, st));
-  PES_CUDA(E.run_dag(plan->fwd, 0, st));
-  PES_CUDA(E.run_add(plan->add, nullptr, nullptr, st, 1, grids, nullptr));
+  auto run = [&](cudaStream_t s2) -> pes_status {
+    PES_CUDA(pes::launch_prologue(E.ctrl, s2));
+    PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, s2));
+    PES_CUDA(E.run_dag(plan->fwd, 0, s2));
+    PES_CUDA(E.run_add(plan->add, nullptr, nullptr, s2, 1, grids, nullptr));
+    return PES_OK;
+  };
+  s = tune_plan(plan, run, st);
+  if (s != PES_OK) return s;
+  s = run(st);
+  if (s != PES_OK) return s;
   E.last_launches = 1 + Exec::launches(plan->pack) + Exec::launches(plan->fwd) + Exec::launches(plan->add);
   return PES_OK;
 }
@@ -1048,9 +1068,8 @@ extern "C" pes_status pes_eval_system(pes_plan_t plan, const double* coeff, cons
   if (!coeff || !input || !value || !jac) return fail(PES_EINVAL, "NULL buffer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Exec& E = plan->ex;
-  if (plan->autotune && !plan->tuned) {
-    // tune on the series layout; both layouts share the job list
-    plan->tuned = true;
+  {
+    // both layouts share the job list and its launch shape
     auto run = [&](cudaStream_t s2) -> pes_status {
       PES_CUDA(pes::launch_prologue(E.ctrl, s2));
       PES_CUDA(E.run_pack(plan->pack, coeff, input, nullptr, s2));
@@ -1058,7 +1077,7 @@ extern "C" pes_status pes_eval_system(pes_plan_t plan, const double* coeff, cons
       PES_CUDA(E.run_add(plan->add_mat, value, jac, s2));
       return PES_OK;
     };
-    pes_status ts = tune_launch(E, plan->fwd, tune_key(E, plan->fwd.n, plan->signature), run, st);
+    pes_status ts = tune_plan(plan, run, st);
     if (ts != PES_OK) return ts;
   }
   PES_CUDA(E.mark(0, st));
