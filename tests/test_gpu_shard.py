@@ -77,3 +77,25 @@ def test_partial_calls_reject_complex_plans(torch):
     rc = pes.lib().pes_partial_grids(plan.handle, ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(Z.data_ptr()),
                                      ctypes.c_void_p(grids.data_ptr()), None)
     assert rc == 1
+
+
+def test_autotuned_shards_equal_one_plan(torch):
+    """Rank plans built with autotune tune their launch shape (parts per job
+    included) on the first pes_partial_grids call; the exchanged result is
+    still one plan's bits."""
+    supports = synth.supports_p2(n=32, N=8, m=16, seed=9)
+    n, d, k, world = 32, 152, 10, 2
+    rng = np.random.default_rng(77)
+    C = torch.from_numpy(random_md(rng, k, (len(supports) + 1, d + 1))).cuda()
+    Z = torch.from_numpy(random_md(rng, k, (n, d + 1))).cuda()
+    whole = pes.Plan(supports, n, d, k, with_vjp=False)
+    v0, g0 = whole.eval_grad(C, Z)
+    shards = [ShardPlan(supports, n, d, k, world, r, autotune=True) for r in range(world)]
+    grids = [s.plan.partial_grids(s.coeff_of(C), Z).clone() for s in shards]
+    common = torch.maximum(grids[0], grids[1])
+    total = sum((s.plan.partial_sums(common).clone() for s in shards[1:]), shards[0].plan.partial_sums(common).clone())
+    for s in shards:
+        v, g = s.plan.round_sums(common, total)
+        s.plan.check()
+        assert torch.equal(v, v0) and torch.equal(g, g0)
+        assert s.plan.info()["split"] in (1, 2, 4, 8, 16)
