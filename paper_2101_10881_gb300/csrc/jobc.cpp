@@ -65,9 +65,19 @@ struct Builder {
 };
 
 // Stable sort by layer, then resolve producer jobs of every operand slot.
+// Within a layer, the jobs whose output another job reads come first, so that
+// the dependency chains advance as early as the dispatch order allows and the
+// leaves (products only the addition stage reads) fill in behind them.
 void finalize(std::vector<ConvJob>& jobs, int32_t n_slots) {
-  std::stable_sort(jobs.begin(), jobs.end(),
-                   [](const ConvJob& a, const ConvJob& b) { return a.layer < b.layer; });
+  std::vector<char> read(static_cast<size_t>(n_slots), 0);
+  for (const ConvJob& j : jobs) {
+    read[static_cast<size_t>(j.in1)] = 1;
+    read[static_cast<size_t>(j.in2)] = 1;
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [&read](const ConvJob& a, const ConvJob& b) {
+    if (a.layer != b.layer) return a.layer < b.layer;
+    return read[static_cast<size_t>(a.out)] > read[static_cast<size_t>(b.out)];
+  });
   std::vector<int32_t> producer(static_cast<size_t>(n_slots), -1);
   for (size_t j = 0; j < jobs.size(); ++j) {
     ConvJob& jb = jobs[j];
