@@ -37,7 +37,7 @@ struct DagArgs {
   int32_t smax;             // largest padded stride of the instances
   int32_t dmax;             // largest degree
   int32_t depth;            // staging depth: 1, or 2 (next job staged while this one is rounded)
-  int32_t split;            // parts per job (integer variant: 1, 2 or 4): part p of job j is
+  int32_t split;            // parts per job (integer variant: 1 to 16, a power of two): part p of job j is
                             // dispatched, flagged and waited for as j * split + p
   long long timeout_ns;     // bound on every wait
   int32_t tile;             // > 0: the tiled kernel, output tiles of `tile` coefficients, `split`
