@@ -86,6 +86,30 @@ def test_small_random_polynomials(torch, k, d):
     assert normalised(v) and normalised(g)
 
 
+@pytest.mark.parametrize("k", [2, 3])
+def test_degenerate_single_plans(torch, k):
+    """A polynomial with no monomial: the value is a_0 limb for limb and the
+    gradient is exactly zero; a variable that no monomial holds has an exactly
+    zero gradient series; a polynomial of one variable and one monomial of it
+    matches the oracle."""
+    rng = np.random.default_rng(500 + k)
+    d, n = 20, 4
+    a0 = random_md(rng, k, (1, d + 1))
+    empty = synth.Problem("empty", n, d, k, [], a0, random_md(rng, k, (n, d + 1)))
+    v, g, _ = run(torch, empty)
+    assert np.array_equal(v, a0[:, 0]) and not g.any()
+    supp = [[0, 2], [2]]  # variables 1 and 3 appear in no monomial
+    prob = synth.Problem("holes", n, d, k, supp, random_md(rng, k, (3, d + 1)), random_md(rng, k, (n, d + 1)))
+    v, g, _ = run(torch, prob)
+    assert not g[:, 1].any() and not g[:, 3].any()
+    rv, rg = O.eval_grad(supp, n, prob.coeff, prob.inputs)
+    assert normwise_err(v, rv) <= TOL[k] and normwise_err(g, rg) <= TOL[k]
+    one = synth.Problem("one", 1, d, k, [[0]], random_md(rng, k, (2, d + 1)), random_md(rng, k, (1, d + 1)))
+    v, g, _ = run(torch, one)
+    rv, rg = O.eval_grad([[0]], 1, one.coeff, one.inputs)
+    assert normwise_err(v, rv) <= TOL[k] and normwise_err(g, rg) <= TOL[k]
+
+
 @pytest.mark.parametrize("threads", [0, 96, 256, 320])
 def test_ragged_degree_several_tiles(torch, threads):
     """d = 152: 153 coefficients (a ragged last warp), k = 4, monomials of up to
