@@ -386,8 +386,10 @@ __device__ __forceinline__ int64_t exch_word(const unsigned long long* row, int 
   return static_cast<int64_t>(p.x) * (1LL << 18) + p.y;
 }
 
-template <int K, bool INTV>
-__global__ void __launch_bounds__(dag_max_threads(K), INTV ? dag_min_ctas(K) : 1) dag_kernel(DagArgs a) {
+template <int K, bool INTV, bool NARROW = false>
+__global__ void __launch_bounds__(NARROW ? kNarrowThreads : dag_max_threads(K),
+                                  NARROW ? kNarrowCtas : (INTV ? dag_min_ctas(K) : 1))
+    __maxnreg__(NARROW ? 255 : dag_max_regs(K, INTV)) dag_kernel(DagArgs a) {
   using DigitT = typename std::conditional<INTV, int32_t, double>::type;
   using AccT = typename DigitMac<K, INTV>::AccT;
   constexpr int B = INTV ? DIGIT_BITS_INT : DIGIT_BITS;
@@ -1503,24 +1505,33 @@ __global__ void __launch_bounds__(256) int_peak_kernel(long long* sink, int iter
   if (s == 12345) sink[blockIdx.x] = s;
 }
 
+// The kernel a launch uses: the tiled kernel, the narrow whole-series
+// instantiation (k <= 2, integer pipe, at most kNarrowThreads threads) or the
+// general one.
 template <int K, bool INTV>
-void* dag_fn(bool tiled) {
-  return tiled ? reinterpret_cast<void*>(&dag_tiled_kernel<K, INTV>) : reinterpret_cast<void*>(&dag_kernel<K, INTV>);
+void* dag_fn(bool tiled, bool narrow) {
+  if (tiled) return reinterpret_cast<void*>(&dag_tiled_kernel<K, INTV>);
+  if constexpr (dag_has_narrow(K, INTV)) {
+    if (narrow) return reinterpret_cast<void*>(&dag_kernel<K, INTV, true>);
+  }
+  return reinterpret_cast<void*>(&dag_kernel<K, INTV>);
 }
 
-void* dag_kernel_ptr(int k, int arith, bool tiled) {
+void* dag_kernel_ptr(int k, int arith, bool tiled, bool narrow) {
   const bool iv = arith == ARITH_INT;
   switch (k) {
-    case 1: return iv ? dag_fn<1, true>(tiled) : dag_fn<1, false>(tiled);
-    case 2: return iv ? dag_fn<2, true>(tiled) : dag_fn<2, false>(tiled);
-    case 3: return iv ? dag_fn<3, true>(tiled) : dag_fn<3, false>(tiled);
-    case 4: return iv ? dag_fn<4, true>(tiled) : dag_fn<4, false>(tiled);
-    case 5: return iv ? dag_fn<5, true>(tiled) : dag_fn<5, false>(tiled);
-    case 8: return iv ? dag_fn<8, true>(tiled) : dag_fn<8, false>(tiled);
-    case 10: return iv ? dag_fn<10, true>(tiled) : dag_fn<10, false>(tiled);
+    case 1: return iv ? dag_fn<1, true>(tiled, narrow) : dag_fn<1, false>(tiled, narrow);
+    case 2: return iv ? dag_fn<2, true>(tiled, narrow) : dag_fn<2, false>(tiled, narrow);
+    case 3: return iv ? dag_fn<3, true>(tiled, narrow) : dag_fn<3, false>(tiled, narrow);
+    case 4: return iv ? dag_fn<4, true>(tiled, narrow) : dag_fn<4, false>(tiled, narrow);
+    case 5: return iv ? dag_fn<5, true>(tiled, narrow) : dag_fn<5, false>(tiled, narrow);
+    case 8: return iv ? dag_fn<8, true>(tiled, narrow) : dag_fn<8, false>(tiled, narrow);
+    case 10: return iv ? dag_fn<10, true>(tiled, narrow) : dag_fn<10, false>(tiled, narrow);
     default: return nullptr;
   }
 }
+
+bool narrow_launch(int threads) { return threads > 0 && threads <= kNarrowThreads; }
 
 }  // namespace
 
@@ -1540,8 +1551,9 @@ size_t dag_tiled_smem_bytes(int k, int arith, int tile) {
 // device, shared by every plan: raise it, never lower it, so that a plan built
 // later for a smaller degree cannot break the launches of an earlier one.
 cudaError_t dag_prepare(int k, int arith, size_t smem, bool tiled) {
-  void* fn = dag_kernel_ptr(k, arith, tiled);
-  if (!fn) return cudaErrorInvalidValue;
+  void* fn = dag_kernel_ptr(k, arith, tiled, false);
+  void* fn_narrow = dag_kernel_ptr(k, arith, tiled, true);  // the same kernel unless k <= 2 whole-series integer
+  if (!fn || !fn_narrow) return cudaErrorInvalidValue;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1551,19 +1563,21 @@ cudaError_t dag_prepare(int k, int arith, size_t smem, bool tiled) {
   size_t& cur = granted[std::make_tuple(dev, k, arith, tiled)];
   if (smem <= cur) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e == cudaSuccess && fn_narrow != fn)
+    e = cudaFuncSetAttribute(fn_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e == cudaSuccess) cur = smem;
   return e;
 }
 
 cudaError_t dag_occupancy(int k, int arith, int threads, size_t smem, int* blocks_per_sm, bool tiled) {
-  void* fn = dag_kernel_ptr(k, arith, tiled);
+  void* fn = dag_kernel_ptr(k, arith, tiled, narrow_launch(threads));
   if (!fn) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
 cudaError_t launch_dag(const DagArgs& a, int k, int arith, int threads, int grid, cudaStream_t st) {
   const bool tiled = a.tile > 0;
-  void* fn = dag_kernel_ptr(k, arith, tiled);
+  void* fn = dag_kernel_ptr(k, arith, tiled, narrow_launch(threads));
   if (!fn) return cudaErrorInvalidValue;
   const size_t smem =
       tiled ? dag_tiled_smem_bytes(k, arith, a.tile) : dag_smem_bytes(k, arith, a.smax, a.dmax, a.depth, threads);

@@ -93,6 +93,20 @@ struct CopyArgs {
 // accumulators and a digit row in registers).
 __host__ __device__ constexpr int dag_max_threads(int k) { return k >= 10 ? 256 : k >= 8 ? 384 : k >= 4 ? 512 : 768; }
 __host__ __device__ constexpr int dag_min_ctas(int k) { return k >= 10 ? 2 : 1; }
+// More CTAs per SM at low k keep more jobs in flight while others stage or
+// round.  The whole-series kernel's integer variant caps its registers at 64
+// for k = 3 (four CTAs of 256 threads per SM) and at 80 for k = 4, 5 (three);
+// at k <= 2 a second instantiation for CTAs of at most 256 threads declares
+// four CTAs per SM in its launch bounds (measured faster at k <= 2 than the
+// same register count reached through a cap), and CTAs wider than that (large
+// degrees) take the uncapped kernel.  The accumulators of L <= 12 digits fit
+// without spilling.
+__host__ __device__ constexpr int dag_max_regs(int k, bool intv) {
+  return !intv ? 255 : k <= 2 ? 255 : k <= 3 ? 64 : k <= 5 ? 80 : 255;
+}
+__host__ __device__ constexpr bool dag_has_narrow(int k, bool intv) { return intv && k <= 2; }
+constexpr int kNarrowThreads = 256;  // widest CTA of the narrow instantiation
+constexpr int kNarrowCtas = 4;       // CTAs per SM its launch bounds declare
 constexpr int kMaxSplit = 16;  // largest number of parts a convolution job is split into
 
 // Shared-memory footprint of the DAG kernel for (k, arith, smax, dmax) at
