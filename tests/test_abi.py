@@ -75,3 +75,25 @@ def test_system_arguments_checked_on_host():
                                2, None, ctypes.byref(h))
         assert rc == 1, (P, list(pp))
     assert L.pes_eval_system(None, None, None, None, None, 0, None) == 1
+
+
+def test_kernel_source_hash_follows_code_not_comments(tmp_path, monkeypatch):
+    """The DRAM traffic of the committed ncu capture stays valid while the
+    kernel code is unchanged: the hash ignores comments and white space and
+    changes with any code token."""
+    import shutil
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "paper_2101_10881_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("kernels.cu", "digits.cuh", "kernels.hpp"):
+        shutil.copy(os.path.join(ROOT, "paper_2101_10881_gb300", "csrc", f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    with open(csrc / "kernels.hpp", "a") as fh:
+        fh.write("\n// a comment\n/* and a\n   block comment */\n\n")
+    assert bench.kernel_source_hash() == h0
+    with open(csrc / "kernels.hpp", "a") as fh:
+        fh.write("constexpr int kUnusedForTheTest = 1;\n")
+    assert bench.kernel_source_hash() != h0
